@@ -1,0 +1,207 @@
+"""FP64 CPU oracle for relaxation gauge fixing (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+package.  The CUDA library neither imports nor links it, and it shares no code
+with the library: the C source ``lgt_oracle.c`` restates the paper's Sections 2
+and 3 on its own (see its header for every reading of the text it takes).
+
+Every function takes and returns links as complex128 arrays of shape
+``(N_t, N_3, N_2, N_1, 4, 3, 3)`` (direction 0 = t, 1..3 = x1..x3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lgt_oracle.c")
+_LIB = os.path.join(_HERE, "liblgt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LANDAU, COULOMB = 0, 1
+OR, SR = 0, 1
+
+_dp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, FP64, no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+             _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.orc_measure.argtypes = [_i32p, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            L.orc_half_sweep.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_int, _dp, _dp]
+            L.orc_sweeps.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_site_new_links.argtypes = [_i32p, _dp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_int, _dp]
+            L.orc_local_update.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           _dp, _dp, _dp, _dp]
+            L.orc_local_update.restype = None
+            L.orc_gather_K.argtypes = [_i32p, _dp, ctypes.c_int64, ctypes.c_int, _dp]
+            L.orc_su2_maximum.argtypes = [_dp, _dp]
+            L.orc_su2_maximum.restype = None
+            L.orc_philox4x32_10.argtypes = [_dp, _dp, _dp]
+            L.orc_philox4x32_10.restype = None
+            L.orc_sr_draws.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _dp]
+            L.orc_sr_draws.restype = None
+            L.orc_fix.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_uint64, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  _dp, _dp]
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = None
+            L.orc_max_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _dims_of(links: np.ndarray):
+    if links.dtype != np.complex128 or links.ndim != 7 or links.shape[4:] != (4, 3, 3):
+        raise ValueError("links must be complex128 of shape (N_t, N_3, N_2, N_1, 4, 3, 3)")
+    if not links.flags.c_contiguous:
+        raise ValueError("links must be C-contiguous")
+    return (ctypes.c_int32 * 4)(*links.shape[:4])
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise RuntimeError(f"{what} failed ({rc})")
+    return rc
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def measure(links: np.ndarray, gauge: int = LANDAU):
+    """Exact F, theta, plaquette (and per-timeslice F_t, theta_t)."""
+    d = _dims_of(links)
+    nt = links.shape[0]
+    F = ctypes.c_double()
+    th = ctypes.c_double()
+    pl = ctypes.c_double()
+    ft = np.zeros(nt)
+    tt = np.zeros(nt)
+    _check(_load().orc_measure(d, links.ctypes.data, gauge, ctypes.addressof(F), ctypes.addressof(th),
+                               ctypes.addressof(pl), ft.ctypes.data, tt.ctypes.data), "orc_measure")
+    return dict(F=F.value, theta=th.value, plaq=pl.value, F_t=ft, theta_t=tt)
+
+
+def half_sweep(links, parity, gauge=LANDAU, algo=OR, omega=1.0, p=0.0, seed=0, sweep=0,
+               transform_temporal=1, active=None, order=None):
+    """In-place half-sweep over one parity."""
+    d = _dims_of(links)
+    act = None
+    if active is not None:
+        act = np.ascontiguousarray(active, dtype=np.uint8)
+    od = None
+    if order is not None:
+        od = np.ascontiguousarray(order, dtype=np.int64)
+        assert od.size == links[..., 0, 0, 0].size // 2
+    _check(_load().orc_half_sweep(d, links.ctypes.data, gauge, parity, algo, omega, p, seed, sweep,
+                                  transform_temporal, None if act is None else act.ctypes.data,
+                                  None if od is None else od.ctypes.data), "orc_half_sweep")
+    return links
+
+
+def sweeps(links, n, gauge=LANDAU, algo=OR, omega=1.0, p=0.0, seed=0, sweep0=0,
+           transform_temporal=1, active=None):
+    """In-place n full sweeps (even half, then odd half)."""
+    d = _dims_of(links)
+    act = None
+    if active is not None:
+        act = np.ascontiguousarray(active, dtype=np.uint8)
+    _check(_load().orc_sweeps(d, links.ctypes.data, gauge, algo, omega, p, seed, sweep0, n,
+                              transform_temporal, None if act is None else act.ctypes.data),
+           "orc_sweeps")
+    return links
+
+
+def site_new_links(links, site, gauge=LANDAU, algo=OR, omega=1.0, p=0.0, seed=0, sweep=0,
+                   transform_temporal=1):
+    """(fwd[4,3,3], bwd[4,3,3]) that one site update would write."""
+    d = _dims_of(links)
+    out = np.empty((8, 3, 3), dtype=np.complex128)
+    _check(_load().orc_site_new_links(d, links.ctypes.data, int(site), gauge, algo, omega, p, seed,
+                                      sweep, transform_temporal, out.ctypes.data), "orc_site_new_links")
+    return out[:4], out[4:]
+
+
+def local_update(K: np.ndarray, algo=OR, omega=1.0, p=0.0, draws=(0, 0, 0)):
+    """g, W[3], R[3] of one Cabibbo-Marinari update of K (3x3 complex)."""
+    K = np.ascontiguousarray(K, dtype=np.complex128)
+    g = np.empty((3, 3), np.complex128)
+    W = np.empty((3, 3, 3), np.complex128)
+    R = np.empty((3, 3, 3), np.complex128)
+    dr = np.ascontiguousarray(draws, dtype=np.uint32)
+    _load().orc_local_update(K.ctypes.data, algo, omega, p, dr.ctypes.data, g.ctypes.data,
+                             W.ctypes.data, R.ctypes.data)
+    return g, W, R
+
+
+def gather_K(links, site, gauge=LANDAU):
+    d = _dims_of(links)
+    K = np.empty((3, 3), np.complex128)
+    _check(_load().orc_gather_K(d, links.ctypes.data, int(site), gauge, K.ctypes.data), "orc_gather_K")
+    return K
+
+
+def su2_maximum(M: np.ndarray):
+    M = np.ascontiguousarray(M, dtype=np.complex128)
+    r = np.empty(4)
+    _load().orc_su2_maximum(M.ctypes.data, r.ctypes.data)
+    return r
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.empty(4, np.uint32)
+    _load().orc_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return tuple(int(v) for v in o)
+
+
+def sr_draws(seed, sweep, site):
+    o = np.empty(3, np.uint32)
+    _load().orc_sr_draws(seed, sweep, site, o.ctypes.data)
+    return o
+
+
+def fix(links, gauge=LANDAU, algo=OR, omega=1.7, p=0.0, seed=0, tol=1e-14, max_sweeps=1000,
+        check_every=10, transform_temporal=1):
+    """In-place gauge fixing to theta < tol.  Returns dict(converged, sweeps, F, theta)."""
+    d = _dims_of(links)
+    sw = ctypes.c_int()
+    F = ctypes.c_double()
+    th = ctypes.c_double()
+    rc = _check(_load().orc_fix(d, links.ctypes.data, gauge, algo, omega, p, seed, tol, max_sweeps,
+                                check_every, transform_temporal, ctypes.byref(sw), ctypes.addressof(F),
+                                ctypes.addressof(th)), "orc_fix")
+    return dict(converged=(rc == 0), sweeps=sw.value, F=F.value, theta=th.value)
