@@ -1,0 +1,232 @@
+/*
+ * lgt.h -- C ABI of liblgt: SU(3) lattice gauge fixing (Landau gauge, and
+ * Coulomb gauge one timeslice at a time) by checkerboard relaxation on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of Schroeck & Vogt, "Gauge fixing in lattice QCD with
+ * multi-GPUs" (Excited QCD 2013):
+ *   - Sec. 2 defines the gauge functional F, the transformation
+ *     U^g_mu(x) = g(x) U_mu(x) g(x+mu)^dagger, the violation Delta(x) and the
+ *     precision theta = 1/(N_c V) sum_x tr[Delta Delta^dagger];
+ *   - Sec. 3 the relaxation: for all sites of one parity at once maximise
+ *     Re tr[g(x) K(x)] with K(x) built from the 8 adjacent links, through the
+ *     three SU(2) subgroups (Cabibbo-Marinari) and the closed-form SU(2)
+ *     maximum g = K^dagger / sqrt(det K^dagger);
+ *   - Sec. 3.1 overrelaxation (g -> g^omega to first order, omega in [1,2));
+ *   - Sec. 3.2 stochastic relaxation (g -> g^2 with probability p);
+ *   - Sec. 4 the driver: both parities in turn until theta reaches the
+ *     requested precision.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Lattice: dims = {N_t, N_3, N_2, N_1} (slowest to fastest), each even and
+ *   >= 2, periodic.  Site index x1 + N1*(x2 + N2*(x3 + N3*t)).  Direction
+ *   mu = 0 is t (the paper's U_0), mu = 1, 2, 3 are x1, x2, x3.  Parity of a
+ *   site is (x1+x2+x3+t) mod 2; the even sites are updated first.
+ * Links (public layout): complex128 interleaved (re, im), array-of-structs
+ *   links[((site*4 + mu)*9 + 3*row + col)*2 + {0: re, 1: im}],
+ *   i.e. a C array double[N_t][N_3][N_2][N_1][4][3][3][2].  Each link must be
+ *   in SU(3) (checked on input to 1e-10).
+ * A_mu(x) (left undefined by the paper) is the traceless part of
+ *   (U_mu(x) - U_mu(x)^dagger) / (2i); theta is quoted in that normalisation.
+ * Coulomb gauge: per timeslice t, spatial directions only (N_d = 3, V -> V_s);
+ *   F_t and theta_t per slice; the result's F is the mean of F_t and its
+ *   theta the maximum of theta_t.  By default g(x) is also applied to the
+ *   temporal links so the output remains a gauge transform of the input.
+ * Ownership: the library copies what it is given and never frees caller
+ *   memory.  It owns all device state of a context until lgt_destroy.
+ * Errors: every call returns an lgt_status; no exception crosses the ABI.
+ *   lgt_last_error() returns a message for the calling thread's last error.
+ *   Calls on one context are not thread-safe; a server is.
+ * Streams: a context runs on the CUDA stream given at creation (NULL = the
+ *   legacy default stream); every call that returns data synchronises it.
+ */
+#ifndef LGT_H
+#define LGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LGT_API __attribute__((visibility("default")))
+#else
+#define LGT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgt_ctx lgt_ctx;       /* one gauge-fixing job on one lattice */
+typedef struct lgt_server lgt_server; /* continuous-batching job server */
+
+typedef enum {
+  LGT_OK = 0,
+  LGT_EINVAL = 1,     /* bad argument (dims, params, non-SU(3) or non-finite input) */
+  LGT_ENOMEM = 2,     /* device or host allocation failed / over budget */
+  LGT_ECUDA = 3,      /* CUDA runtime error (message in lgt_last_error) */
+  LGT_ENOTCONV = 4,   /* max_sweeps reached before theta < theta_tol (state kept) */
+  LGT_EAGAIN = 5,     /* job still queued or running */
+  LGT_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LGT_EBUSY = 7,      /* resource in use */
+  LGT_ECANCELLED = 8, /* job cancelled */
+  LGT_ENOTFOUND = 9   /* unknown job id */
+} lgt_status;
+
+typedef enum { LGT_LANDAU = 0, LGT_COULOMB = 1 } lgt_gauge;
+typedef enum { LGT_OR = 0, LGT_SR = 1 } lgt_algo; /* Sec. 3.1 / Sec. 3.2 */
+typedef enum {
+  LGT_FP64 = 0,    /* all sweeps in FP64 */
+  LGT_FP32_18 = 1, /* bulk sweeps on FP32 links (18 reals), then FP64 polish */
+  LGT_FP32_12 = 2  /* bulk sweeps on FP32 links stored as rows 0,1 (12 reals) */
+} lgt_prec;
+
+typedef struct {
+  int32_t dims[4];            /* N_t, N_3, N_2, N_1 */
+  int32_t gauge;              /* lgt_gauge */
+  int32_t algo;               /* lgt_algo */
+  int32_t bulk;               /* lgt_prec of the bulk sweeps */
+  int32_t transform_temporal; /* Coulomb: also transform U_0 (default 1) */
+  double omega;               /* overrelaxation parameter, [1, 2) (OR only) */
+  double p;                   /* stochastic relaxation probability, [0, 1] (SR only) */
+  uint64_t seed;              /* key of the SR random stream */
+  uint64_t sweep_offset;      /* index of the first sweep (RNG counter; resume) */
+  double theta_tol;           /* requested precision, e.g. 1e-14 */
+  double theta_switch;        /* bulk FP32 -> FP64 switch threshold (ignored for FP64) */
+  int32_t max_sweeps;         /* cap on sweeps of one lgt_fix call (all phases) */
+  int32_t check_every;        /* exact theta check every k sweeps */
+  int32_t reunit_every;       /* reunitarise FP32 links / G every n sweeps (0: never) */
+  int32_t block_size;         /* threads per block of the sweep kernel (0: autotuned) */
+} lgt_params;
+
+typedef struct {
+  double F;             /* final F (Landau) or mean F_t (Coulomb), exact FP64 measurement */
+  double theta;         /* final theta (Landau) or max theta_t (Coulomb) */
+  double plaquette;     /* average plaquette Re tr U_P / 3 (gauge invariant) */
+  double seconds;       /* wall time of the call */
+  int64_t sweeps_bulk;  /* sweeps run in the bulk FP32 precision */
+  int64_t sweeps_fp64;  /* sweeps run in FP64 */
+  int32_t status;       /* lgt_status of the job */
+  int32_t reserved;
+} lgt_result;
+
+/* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
+ * theta_switch 1e-11, max_sweeps 10000, check_every 10, reunit_every 50,
+ * transform_temporal 1, block_size 0.  dims are zeroed.  Never fails for p != NULL. */
+LGT_API lgt_status lgt_params_default(lgt_params *p);
+
+/* Create a context for one lattice (Sec. 2 problem statement).
+ * links: the field in the public layout above, either host memory
+ *   (links_on_device = 0) or device memory of the current device
+ *   (links_on_device = 1); copied, never retained.
+ * cuda_stream: cudaStream_t to run on (NULL: default stream).
+ * *out receives the context on LGT_OK, NULL otherwise.
+ * Errors: LGT_EINVAL for odd/too-small dims, bad params, non-SU(3) or
+ * non-finite links; LGT_ENOMEM when device memory is short; LGT_ECUDA. */
+LGT_API lgt_status lgt_create(const lgt_params *params, const double *links, int links_on_device, void *cuda_stream,
+                      lgt_ctx **out);
+
+/* Run n full sweeps (even half then odd half, Sec. 3 and Sec. 4) in the
+ * context's current phase (bulk precision until promoted, FP64 after), with no
+ * convergence test.  Coulomb: every slice is updated.  n >= 0. */
+LGT_API lgt_status lgt_sweep(lgt_ctx *ctx, int32_t n);
+
+/* Exact measurement of the current working field, FP64 arithmetic and
+ * fixed-order FP64 sums (Sec. 2: F and theta; plus the average plaquette).
+ * In the bulk phase the working field is the FP32 links (widened).
+ * Any output pointer may be NULL. */
+LGT_API lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double *plaquette);
+
+/* Per-timeslice F_t and theta_t of the current working field (Coulomb
+ * normalisation: spatial directions, N_d = 3, V_s).  Host arrays of N_t. */
+LGT_API lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *theta_t);
+
+/* Gauge-fix to theta < theta_tol (Sec. 4 driver) through the precision
+ * ladder: bulk FP32 sweeps until the exact working-field theta drops below
+ * theta_switch, then promotion (the accumulated gauge transformation G,
+ * reunitarised in FP64, applied to the retained FP64 input), then FP64
+ * sweeps, checking the exact theta every check_every sweeps.  Coulomb: a
+ * slice stops being updated once its theta_t is below the phase's target.
+ * res (nullable) receives the outcome.  Returns LGT_OK when converged,
+ * LGT_ENOTCONV after max_sweeps (state kept, may be continued). */
+LGT_API lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res);
+
+/* Leave the bulk phase now: G (reunitarised in FP64) is applied to the FP64
+ * input, U <- G(x) U(x) G(x+mu)^dagger, and later sweeps run in FP64.
+ * No-op in the FP64 phase. */
+LGT_API lgt_status lgt_promote(lgt_ctx *ctx);
+
+/* The current field in the public layout, FP64.  In the bulk phase this is
+ * G U G^dagger of the FP64 input (the phase is not changed).  out: host
+ * (out_on_device = 0) or device memory of V*4*9*2 doubles. */
+LGT_API lgt_status lgt_get_links(lgt_ctx *ctx, double *out, int out_on_device);
+
+/* The working links as stored (bulk phase: FP32 widened to FP64, 12-real
+ * storage with its third row rebuilt; FP64 phase: as lgt_get_links). */
+LGT_API lgt_status lgt_get_working_links(lgt_ctx *ctx, double *out, int out_on_device);
+
+/* Sweeps run so far in each precision and the phase (0 bulk, 1 FP64). */
+LGT_API lgt_status lgt_get_progress(lgt_ctx *ctx, int64_t *sweeps_bulk, int64_t *sweeps_fp64, int32_t *phase);
+
+/* Replace the context's field with new links (same dims and params) and
+ * restart: bulk phase (or FP64 for LGT_FP64), G = 1, sweep counters zero,
+ * RNG counter back to sweep_offset, every slice active.  Reuses the
+ * context's device memory (host links are staged through a device buffer
+ * allocated on first use and kept).  Errors as lgt_create. */
+LGT_API lgt_status lgt_load(lgt_ctx *ctx, const double *links, int links_on_device);
+
+typedef struct {
+  double sweep_ms[2];        /* device time of the sweep kernels: [0] bulk FP32, [1] FP64 */
+  int64_t sweep_launches[2]; /* half-sweep kernel launches in each precision */
+  int64_t site_updates[2];   /* site updates done in each precision */
+  int64_t launches;          /* every kernel launch of this context */
+  double measure_ms;         /* device time of exact measurements */
+  int64_t measure_launches;
+} lgt_stats;
+
+/* Counters since creation (or the last lgt_load).  Sweep-kernel times come
+ * from CUDA events recorded on the context's stream around each batch of
+ * consecutive half-sweep launches (nothing else runs inside a batch). */
+LGT_API lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out);
+
+/* Release every resource of the context.  NULL is ignored. */
+LGT_API void lgt_destroy(lgt_ctx *ctx);
+
+/* ---------------------------------------------------------------- serving */
+/* A continuous-batching server: jobs are admitted while the device memory
+ * they need fits hbm_budget_bytes, their lattices stay resident, and one
+ * worker thread advances every live job through the sweep kernels, checking
+ * each job's exact theta every check_every sweeps and retiring it when
+ * converged (Sec. 4 driver, per job).  device: CUDA device ordinal. */
+LGT_API lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt_server **out);
+
+/* Queue a job; links (host, public layout) are copied before return.
+ * *job_id receives its id.  LGT_EINVAL for bad params/links, LGT_ENOMEM when
+ * the job alone exceeds the budget. */
+LGT_API lgt_status lgt_submit(lgt_server *s, const lgt_params *params, const double *links, uint64_t *job_id);
+
+/* Job state: LGT_EAGAIN while queued or running; otherwise the job's final
+ * status, with *res filled and, if links_out != NULL, the fixed field written
+ * there (host, public layout).  A finished job is released by this call. */
+LGT_API lgt_status lgt_poll(lgt_server *s, uint64_t job_id, lgt_result *res, double *links_out);
+
+/* Cancel a queued or running job (it finishes with LGT_ECANCELLED). */
+LGT_API lgt_status lgt_cancel(lgt_server *s, uint64_t job_id);
+
+/* Server counters: jobs done, jobs live, device bytes in use. */
+LGT_API lgt_status lgt_server_stats(lgt_server *s, uint64_t *jobs_done, uint64_t *jobs_live, size_t *bytes_in_use);
+
+/* Stop the worker (queued jobs are cancelled) and release everything. */
+LGT_API void lgt_server_destroy(lgt_server *s);
+
+/* Message of the calling thread's most recent error ("" if none). */
+LGT_API const char *lgt_last_error(void);
+
+/* Library version string. */
+LGT_API const char *lgt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LGT_H */

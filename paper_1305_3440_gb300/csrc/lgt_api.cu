@@ -1,0 +1,622 @@
+// lgt_api.cu -- the C ABI (include/lgt.h): contexts, the precision ladder and
+// the driver loop of Sec. 4 (sweep both parities until theta < tol).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lgt.h"
+#include "lgt_api_internal.h"
+#include "lgt_internal.h"
+
+using namespace lgt;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void lgt_set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+extern "C" const char *lgt_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *lgt_version(void) { return "liblgt 0.1 (sm_103a)"; }
+
+#define LGT_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      lgt_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? LGT_ENOMEM : LGT_ECUDA;                      \
+    }                                                                                       \
+  } while (0)
+
+// ------------------------------------------------------------------ params
+extern "C" lgt_status lgt_params_default(lgt_params *p) {
+  if (!p) {
+    lgt_set_error("lgt_params_default: NULL");
+    return LGT_EINVAL;
+  }
+  memset(p, 0, sizeof *p);
+  p->gauge = LGT_LANDAU;
+  p->algo = LGT_OR;
+  p->bulk = LGT_FP64;
+  p->transform_temporal = 1;
+  p->omega = 1.7;
+  p->p = 0.0;
+  p->seed = 0;
+  p->sweep_offset = 0;
+  p->theta_tol = 1e-14;
+  p->theta_switch = 1e-11;
+  p->max_sweeps = 10000;
+  p->check_every = 10;
+  p->reunit_every = 50;
+  p->block_size = 0;
+  return LGT_OK;
+}
+
+lgt_status lgt_validate_params(const lgt_params *p) {
+  if (!p) {
+    lgt_set_error("params is NULL");
+    return LGT_EINVAL;
+  }
+  for (int d = 0; d < 4; d++)
+    if (p->dims[d] < 2 || (p->dims[d] & 1)) {
+      lgt_set_error("dims[%d] = %d: every extent must be even and >= 2", d, p->dims[d]);
+      return LGT_EINVAL;
+    }
+  const double vol = (double)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
+  if (vol / 2 > 2.0e9) {
+    lgt_set_error("lattice too large (V/2 must fit in 32 bits)");
+    return LGT_EINVAL;
+  }
+  if (p->gauge != LGT_LANDAU && p->gauge != LGT_COULOMB) {
+    lgt_set_error("gauge %d unknown", p->gauge);
+    return LGT_EINVAL;
+  }
+  if (p->algo != LGT_OR && p->algo != LGT_SR) {
+    lgt_set_error("algo %d unknown", p->algo);
+    return LGT_EINVAL;
+  }
+  if (p->bulk != LGT_FP64 && p->bulk != LGT_FP32_18 && p->bulk != LGT_FP32_12) {
+    lgt_set_error("bulk precision %d unknown", p->bulk);
+    return LGT_EINVAL;
+  }
+  if (p->algo == LGT_OR && !(p->omega >= 1.0 && p->omega < 2.0)) {
+    lgt_set_error("omega = %g outside [1, 2)", p->omega);
+    return LGT_EINVAL;
+  }
+  if (p->algo == LGT_SR && !(p->p >= 0.0 && p->p <= 1.0)) {
+    lgt_set_error("p = %g outside [0, 1]", p->p);
+    return LGT_EINVAL;
+  }
+  if (!(p->theta_tol > 0.0) || !(p->theta_switch >= 0.0)) {
+    lgt_set_error("theta_tol must be > 0 and theta_switch >= 0");
+    return LGT_EINVAL;
+  }
+  if (p->max_sweeps < 0 || p->check_every < 1 || p->reunit_every < 0) {
+    lgt_set_error("max_sweeps >= 0, check_every >= 1, reunit_every >= 0 required");
+    return LGT_EINVAL;
+  }
+  if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) {
+    lgt_set_error("block_size must be 0, 64, 128 or 256");
+    return LGT_EINVAL;
+  }
+  return LGT_OK;
+}
+
+Geom lgt_make_geom(const int32_t dims[4]) {
+  Geom g;
+  g.nt = dims[0];
+  g.n3 = dims[1];
+  g.n2 = dims[2];
+  g.n1 = dims[3];
+  g.half1 = g.n1 / 2;
+  g.vs_half = g.n1 * g.n2 * g.n3 / 2;
+  g.vh = g.vs_half * g.nt;
+  return g;
+}
+
+static unsigned long long sr_threshold(double p) {
+  if (!(p > 0.0)) return 0ull;
+  if (p >= 1.0) return 1ull << 32;
+  return (unsigned long long)floor(p * 4294967296.0);
+}
+
+static int fmt_of(int32_t prec) { return prec == LGT_FP32_18 ? FMT_F32_18 : (prec == LGT_FP32_12 ? FMT_F32_12 : FMT_F64); }
+
+size_t lgt_ctx_device_bytes(const lgt_params *p) {
+  const Geom g = lgt_make_geom(p->dims);
+  size_t b = field_bytes(FMT_F64, g.vh) + workspace_bytes(g, 64) + 4096;
+  if (p->bulk != LGT_FP64) b += field_bytes(fmt_of(p->bulk), g.vh) + g_bytes(g.vh);
+  return b;
+}
+
+// ------------------------------------------------------------------ context
+struct lgt_ctx {
+  lgt_params prm;
+  Geom g;
+  cudaStream_t stream;
+  int phase;      // 0 bulk (FP32), 1 FP64
+  int bulk_fmt;   // FMT_* of the bulk phase
+  void *u64;      // FP64 links (the input while in the bulk phase)
+  void *u32;      // bulk working links
+  void *G;        // accumulated transformation of the bulk phase
+  void *ws_base;  // workspace allocation
+  Workspace ws;
+  double *host;   // pinned readback buffer
+  int block;
+  int64_t sweeps_bulk, sweeps_fp64;
+  uint64_t sweep_index;  // number of the next sweep (RNG counter)
+  SweepCfg cfg;
+  double *stage;  // device staging buffer for host links (AoS), lazily allocated
+  // timing: event pairs around batches of kernel launches, resolved at sync points
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;  // 0 bulk sweeps, 1 FP64 sweeps, 2 measurement
+  };
+  std::vector<Pending> *pending;
+  std::vector<cudaEvent_t> *event_pool;
+  lgt_stats stats;
+};
+
+static void resolve_events(lgt_ctx *c);
+
+static void ctx_free(lgt_ctx *c) {
+  if (!c) return;
+  if (c->pending) {
+    for (auto &pe : *c->pending) {
+      cudaEventDestroy(pe.a);
+      cudaEventDestroy(pe.b);
+    }
+    delete c->pending;
+  }
+  if (c->event_pool) {
+    for (auto e : *c->event_pool) cudaEventDestroy(e);
+    delete c->event_pool;
+  }
+  if (c->stage) cudaFree(c->stage);
+  if (c->u64) cudaFree(c->u64);
+  if (c->u32) cudaFree(c->u32);
+  if (c->G) cudaFree(c->G);
+  if (c->ws_base) cudaFree(c->ws_base);
+  if (c->host) cudaFreeHost(c->host);
+  delete c;
+}
+
+static cudaEvent_t take_event(lgt_ctx *c) {
+  if (!c->event_pool->empty()) {
+    cudaEvent_t e = c->event_pool->back();
+    c->event_pool->pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// open a timed batch on the context's stream; returns its index or -1
+static int batch_begin(lgt_ctx *c, int kind) {
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return -1;
+  if (cudaEventRecord(a, c->stream) != cudaSuccess) return -1;
+  c->pending->push_back({a, b, kind});
+  return (int)c->pending->size() - 1;
+}
+
+static void batch_end(lgt_ctx *c, int idx) {
+  if (idx >= 0) cudaEventRecord((*c->pending)[idx].b, c->stream);
+}
+
+// after a stream synchronisation: fold finished batches into the counters
+static void resolve_events(lgt_ctx *c) {
+  for (auto &pe : *c->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      if (pe.kind < 2) c->stats.sweep_ms[pe.kind] += ms;
+      else c->stats.measure_ms += ms;
+    }
+    c->event_pool->push_back(pe.a);
+    c->event_pool->push_back(pe.b);
+  }
+  c->pending->clear();
+}
+
+static lgt_status sync_stream(lgt_ctx *c) {
+  LGT_CUDA(cudaStreamSynchronize(c->stream));
+  resolve_events(c);
+  return LGT_OK;
+}
+
+static lgt_status read_back(lgt_ctx *c, const void *dev, size_t bytes) {
+  LGT_CUDA(cudaMemcpyAsync(c->host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return sync_stream(c);
+}
+
+int lgt_pick_block(const lgt_params *p) {
+  if (p->block_size) return p->block_size;
+  return lgt_autotuned_block(p);
+}
+
+// (re)load a field: ingest into FP64 (and the bulk format), G = 1, reset counters
+static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_device) {
+  if (!links) {
+    lgt_set_error("links is NULL");
+    return LGT_EINVAL;
+  }
+  const Geom &g = c->g;
+  const size_t aos_bytes = (size_t)g.vh * 2 * 4 * 18 * sizeof(double);
+  const double *src = links;
+  if (!links_on_device) {
+    if (!c->stage) LGT_CUDA(cudaMalloc(&c->stage, aos_bytes));
+    LGT_CUDA(cudaMemcpyAsync(c->stage, links, aos_bytes, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage;
+  }
+  LGT_CUDA(cudaMemsetAsync(c->ws.err, 0, sizeof(int), c->stream));
+  LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)g.nt, c->stream));
+  LGT_CUDA(launch_ingest(FMT_F64, g, src, c->u64, c->ws.err, c->stream));
+  c->stats.launches++;
+  if (c->u32) {
+    LGT_CUDA(launch_ingest(c->bulk_fmt, g, src, c->u32, c->ws.err, c->stream));
+    LGT_CUDA(launch_g_identity(g, c->G, c->stream));
+    c->stats.launches += 2;
+  }
+  lgt_status st = read_back(c, c->ws.err, sizeof(int));
+  if (st != LGT_OK) return st;
+  if (*(int *)c->host != 0) {
+    lgt_set_error("input links are not all finite SU(3) matrices (|U^dag U - 1| or |det U - 1| >= 1e-10)");
+    return LGT_EINVAL;
+  }
+  c->phase = c->prm.bulk == LGT_FP64 ? 1 : 0;
+  c->sweeps_bulk = c->sweeps_fp64 = 0;
+  c->sweep_index = c->prm.sweep_offset;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, int links_on_device,
+                                 void *cuda_stream, lgt_ctx **out) {
+  if (!out) {
+    lgt_set_error("out is NULL");
+    return LGT_EINVAL;
+  }
+  *out = nullptr;
+  lgt_status st = lgt_validate_params(params);
+  if (st != LGT_OK) return st;
+  if (!links) {
+    lgt_set_error("links is NULL");
+    return LGT_EINVAL;
+  }
+  lgt_ctx *c = new lgt_ctx();
+  memset((void *)c, 0, sizeof *c);
+  c->pending = new std::vector<lgt_ctx::Pending>();
+  c->event_pool = new std::vector<cudaEvent_t>();
+  c->prm = *params;
+  c->g = lgt_make_geom(params->dims);
+  c->stream = (cudaStream_t)cuda_stream;
+  c->bulk_fmt = fmt_of(params->bulk);
+  c->block = lgt_pick_block(params);
+  c->cfg.gauge = params->gauge == LGT_COULOMB ? GAUGE_COULOMB : GAUGE_LANDAU;
+  c->cfg.algo = params->algo == LGT_SR ? ALGO_SR : ALGO_OR;
+  c->cfg.omega = params->omega;
+  c->cfg.sr_thr = sr_threshold(params->p);
+  c->cfg.seed = params->seed;
+  c->cfg.transform_temporal = params->transform_temporal ? 1 : 0;
+  const Geom &g = c->g;
+#define CTX_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      lgt_set_error("%s failed: %s", #call, cudaGetErrorString(e_));                           \
+      ctx_free(c);                                                                             \
+      return e_ == cudaErrorMemoryAllocation ? LGT_ENOMEM : LGT_ECUDA;                         \
+    }                                                                                          \
+  } while (0)
+  CTX_CUDA(cudaMalloc(&c->u64, field_bytes(FMT_F64, g.vh)));
+  if (params->bulk != LGT_FP64) {
+    CTX_CUDA(cudaMalloc(&c->u32, field_bytes(c->bulk_fmt, g.vh)));
+    CTX_CUDA(cudaMalloc(&c->G, g_bytes(g.vh)));
+  }
+  const size_t wsb = workspace_bytes(g, 64);
+  CTX_CUDA(cudaMalloc(&c->ws_base, wsb));
+  CTX_CUDA(cudaMemsetAsync(c->ws_base, 0, wsb, c->stream));
+  workspace_carve(c->ws_base, g, 64, &c->ws);
+  CTX_CUDA(cudaMallocHost(&c->host, 4096 + sizeof(double) * 2 * (size_t)g.nt));
+#undef CTX_CUDA
+  st = load_field(c, links, links_on_device);
+  if (st != LGT_OK) {
+    ctx_free(c);
+    return st;
+  }
+  *out = c;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_load(lgt_ctx *ctx, const double *links, int links_on_device) {
+  if (!ctx) {
+    lgt_set_error("lgt_load: NULL context");
+    return LGT_EINVAL;
+  }
+  memset(&ctx->stats, 0, sizeof ctx->stats);
+  return load_field(ctx, links, links_on_device);
+}
+
+extern "C" lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out) {
+  if (!ctx || !out) {
+    lgt_set_error("lgt_get_stats: bad arguments");
+    return LGT_EINVAL;
+  }
+  lgt_status st = sync_stream(ctx);
+  if (st != LGT_OK) return st;
+  *out = ctx->stats;
+  return LGT_OK;
+}
+
+extern "C" void lgt_destroy(lgt_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  ctx_free(ctx);
+}
+
+// ------------------------------------------------------------------ sweeps
+static lgt_status run_sweeps(lgt_ctx *c, int n, int use_mask) {
+  const int fmt = c->phase == 0 ? c->bulk_fmt : FMT_F64;
+  void *links = c->phase == 0 ? c->u32 : c->u64;
+  void *G = c->phase == 0 ? c->G : nullptr;
+  const int kind = c->phase == 0 ? 0 : 1;
+  if (n <= 0) return LGT_OK;
+  const int bt = batch_begin(c, kind);
+  for (int s = 0; s < n; s++) {
+    int reunit = 0;
+    if (c->phase == 0 && c->prm.reunit_every > 0) reunit = ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
+    for (int parity = 0; parity < 2; parity++)
+      LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask,
+                                 c->block, c->stream));
+    c->sweep_index++;
+    if (c->phase == 0) c->sweeps_bulk++;
+    else c->sweeps_fp64++;
+  }
+  batch_end(c, bt);
+  c->stats.sweep_launches[kind] += 2 * (int64_t)n;
+  c->stats.launches += 2 * (int64_t)n;
+  c->stats.site_updates[kind] += (int64_t)n * 2 * (int64_t)c->g.vh;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_sweep(lgt_ctx *ctx, int32_t n) {
+  if (!ctx || n < 0) {
+    lgt_set_error("lgt_sweep: bad arguments");
+    return LGT_EINVAL;
+  }
+  lgt_status st = run_sweeps(ctx, n, 0);
+  if (st != LGT_OK) return st;
+  return sync_stream(ctx);
+}
+
+// ------------------------------------------------------------ measurement
+struct Meas {
+  double F, theta, plaq, theta_mean;
+  int active;
+};
+
+// exact measurement of the working field; coulomb_target >= 0 updates masks
+static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas *m) {
+  const int fmt = c->phase == 0 ? c->bulk_fmt : FMT_F64;
+  const void *links = c->phase == 0 ? c->u32 : c->u64;
+  const int bt = batch_begin(c, 2);
+  LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream));
+  batch_end(c, bt);
+  c->stats.measure_launches++;
+  c->stats.launches++;
+  lgt_status st = read_back(c, c->ws.totals, sizeof(double) * TOT_N);
+  if (st != LGT_OK) return st;
+  const double *t = c->host;
+  if (c->prm.gauge == LGT_COULOMB) {
+    m->F = t[TOT_F_COULOMB];
+    m->theta = t[TOT_THETA_COULOMB_MAX];
+    m->theta_mean = t[TOT_THETA_COULOMB_MEAN];
+  } else {
+    m->F = t[TOT_F_LANDAU];
+    m->theta = t[TOT_THETA_LANDAU];
+    m->theta_mean = m->theta;
+  }
+  m->plaq = t[TOT_PLAQ];
+  m->active = (int)t[TOT_ACTIVE_SLICES];
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double *plaq) {
+  if (!ctx) {
+    lgt_set_error("lgt_measure: NULL context");
+    return LGT_EINVAL;
+  }
+  Meas m;
+  lgt_status st = measure(ctx, plaq != nullptr, -1.0, &m);
+  if (st != LGT_OK) return st;
+  if (F) *F = m.F;
+  if (theta) *theta = m.theta;
+  if (plaq) *plaq = m.plaq;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *theta_t) {
+  if (!ctx) {
+    lgt_set_error("lgt_measure_slices: NULL context");
+    return LGT_EINVAL;
+  }
+  Meas m;
+  lgt_status st = measure(ctx, 0, -1.0, &m);
+  if (st != LGT_OK) return st;
+  const size_t nb = sizeof(double) * (size_t)ctx->g.nt;
+  if (F_t) {
+    LGT_CUDA(cudaMemcpyAsync(F_t, ctx->ws.slice_F, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (theta_t) {
+    LGT_CUDA(cudaMemcpyAsync(theta_t, ctx->ws.slice_theta, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return sync_stream(ctx);
+}
+
+// --------------------------------------------------------------- promotion
+static lgt_status promote(lgt_ctx *c) {
+  if (c->phase == 1) return LGT_OK;
+  const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
+  LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_t, c->stream));
+  c->stats.launches++;
+  c->phase = 1;
+  return sync_stream(c);
+}
+
+extern "C" lgt_status lgt_promote(lgt_ctx *ctx) {
+  if (!ctx) {
+    lgt_set_error("lgt_promote: NULL context");
+    return LGT_EINVAL;
+  }
+  return promote(ctx);
+}
+
+// ------------------------------------------------------------- the driver
+extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
+  if (!ctx) {
+    lgt_set_error("lgt_fix: NULL context");
+    return LGT_EINVAL;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  lgt_ctx *c = ctx;
+  const bool coulomb = c->prm.gauge == LGT_COULOMB;
+  int64_t remaining = c->prm.max_sweeps;
+  const int k = c->prm.check_every;
+  const int64_t bulk0 = c->sweeps_bulk, fp640 = c->sweeps_fp64;
+  Meas m;
+  lgt_status st;
+  if (c->phase == 0) {
+    // bulk FP32 phase: until the working field's theta drops below theta_switch
+    // or stops improving (the FP32 rounding floor)
+    const double target = c->prm.theta_switch;
+    st = measure(c, 0, coulomb ? target : -1.0, &m);
+    if (st != LGT_OK) return st;
+    double best = m.theta;
+    int stall = 0;
+    while (m.theta >= target && remaining > 0 && stall < 3) {
+      const int n = (int)(remaining < k ? remaining : k);
+      st = run_sweeps(c, n, coulomb ? 1 : 0);
+      if (st != LGT_OK) return st;
+      remaining -= n;
+      st = measure(c, 0, coulomb ? target : -1.0, &m);
+      if (st != LGT_OK) return st;
+      if (m.theta < best) {
+        best = m.theta;
+        stall = 0;
+      } else {
+        stall++;
+      }
+    }
+    st = promote(c);
+    if (st != LGT_OK) return st;
+  }
+  // FP64 phase to theta < tol
+  const double tol = c->prm.theta_tol;
+  st = measure(c, 0, coulomb ? tol : -1.0, &m);
+  if (st != LGT_OK) return st;
+  while (m.theta >= tol && remaining > 0) {
+    const int n = (int)(remaining < k ? remaining : k);
+    st = run_sweeps(c, n, coulomb ? 1 : 0);
+    if (st != LGT_OK) return st;
+    remaining -= n;
+    st = measure(c, 0, coulomb ? tol : -1.0, &m);
+    if (st != LGT_OK) return st;
+  }
+  // all slices active again for later calls
+  LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)c->g.nt, c->stream));
+  Meas fin;
+  st = measure(c, 1, -1.0, &fin);
+  if (st != LGT_OK) return st;
+  const bool conv = m.theta < tol;
+  if (res) {
+    res->F = fin.F;
+    res->theta = fin.theta;
+    res->plaquette = fin.plaq;
+    res->sweeps_bulk = c->sweeps_bulk - bulk0;
+    res->sweeps_fp64 = c->sweeps_fp64 - fp640;
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    res->status = conv ? LGT_OK : LGT_ENOTCONV;
+    res->reserved = 0;
+  }
+  if (!conv) {
+    lgt_set_error("not converged: theta = %.3e after %d sweeps", m.theta, c->prm.max_sweeps);
+    return LGT_ENOTCONV;
+  }
+  return LGT_OK;
+}
+
+// ------------------------------------------------------------- egress
+static lgt_status to_output(lgt_ctx *c, double *out, int out_on_device, int working) {
+  const Geom &g = c->g;
+  const size_t aos_bytes = (size_t)g.vh * 2 * 4 * 18 * sizeof(double);
+  double *dst = out;
+  double *tmp = nullptr;
+  if (!out_on_device) {
+    if (!c->stage) {
+      cudaError_t e = cudaMalloc(&c->stage, aos_bytes);
+      if (e != cudaSuccess) {
+        lgt_set_error("cudaMalloc of the staging buffer failed: %s", cudaGetErrorString(e));
+        return LGT_ENOMEM;
+      }
+    }
+    tmp = c->stage;
+    dst = tmp;
+  }
+  cudaError_t e;
+  if (c->phase == 1) e = launch_egress(FMT_F64, g, c->u64, dst, c->stream);
+  else if (working) e = launch_egress(c->bulk_fmt, g, c->u32, dst, c->stream);
+  else {
+    const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
+    e = launch_apply_G(g, c->G, c->u64, nullptr, dst, skip_t, c->stream);
+  }
+  c->stats.launches++;
+  if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, aos_bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  resolve_events(c);
+  if (e != cudaSuccess) {
+    lgt_set_error("link egress failed: %s", cudaGetErrorString(e));
+    return LGT_ECUDA;
+  }
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_get_links(lgt_ctx *ctx, double *out, int out_on_device) {
+  if (!ctx || !out) {
+    lgt_set_error("lgt_get_links: bad arguments");
+    return LGT_EINVAL;
+  }
+  return to_output(ctx, out, out_on_device, 0);
+}
+
+extern "C" lgt_status lgt_get_working_links(lgt_ctx *ctx, double *out, int out_on_device) {
+  if (!ctx || !out) {
+    lgt_set_error("lgt_get_working_links: bad arguments");
+    return LGT_EINVAL;
+  }
+  return to_output(ctx, out, out_on_device, 1);
+}
+
+extern "C" lgt_status lgt_get_progress(lgt_ctx *ctx, int64_t *sweeps_bulk, int64_t *sweeps_fp64, int32_t *phase) {
+  if (!ctx) {
+    lgt_set_error("lgt_get_progress: NULL context");
+    return LGT_EINVAL;
+  }
+  if (sweeps_bulk) *sweeps_bulk = ctx->sweeps_bulk;
+  if (sweeps_fp64) *sweeps_fp64 = ctx->sweeps_fp64;
+  if (phase) *phase = ctx->phase;
+  return LGT_OK;
+}

@@ -1,0 +1,647 @@
+// lgt_kernels.cu -- the sweep, measurement and layout kernels for sm_103a.
+//
+// Half-sweep (Sec. 3 and Sec. 4 of Schroeck & Vogt): one thread per site of
+// the active parity.  The thread gathers K(x) from the 4 forward links of its
+// site and the 4 backward links U_mu(x-mu) (which belong to sites of the other
+// parity), runs the Cabibbo-Marinari local update, and writes g U_mu(x) and
+// U_mu(x-mu) g^dagger back in place.  Sites of one parity touch disjoint links,
+// so the launch is race-free.  While K(x) is in registers the thread also
+// adds Re tr K and tr[Delta Delta^dagger] to a deterministic per-slice sum
+// (the fused estimate of F and theta).
+//
+// FP32 formats keep all 8 links in registers between the gather and the
+// write-back (each link is read once and written once per half-sweep, no
+// reuse).  FP64 links are 2x larger and FP64 arithmetic is the bottleneck on
+// this part, so the FP64 kernel gathers K streaming and re-reads each link
+// for the write-back (an L2 hit).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lgt_device.cuh"
+#include "lgt_internal.h"
+
+namespace lgt {
+
+static inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+size_t workspace_bytes(const Geom &g, int min_block) {
+  const int gx = ceil_div(g.vs_half, min_block);
+  size_t b = 0;
+  b += sizeof(double) * (size_t)g.nt * gx * 2;             // sweep_partial
+  b += sizeof(double) * 2 * (size_t)g.nt * 2;              // fused
+  b += sizeof(double) * (size_t)g.nt * 2 * gx * MEAS_NV;   // meas_partial
+  b += sizeof(double) * (size_t)g.nt * MEAS_NV;            // slice_sum
+  b += sizeof(double) * (size_t)g.nt * 2;                  // slice_F, slice_theta
+  b += sizeof(double) * TOT_N;                             // totals
+  b += sizeof(unsigned) * ((size_t)g.nt * 2 + 1);          // counters
+  b += (size_t)g.nt + sizeof(int);                         // active, err
+  return b + 16 * 16;                                      // alignment slack
+}
+
+static char *align16(char *p) { return (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15); }
+
+void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
+  const int gx = ceil_div(g.vs_half, min_block);
+  char *p = align16((char *)base);
+  w->sweep_partial = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt * gx * 2);
+  w->fused = (double *)p;
+  p = align16(p + sizeof(double) * 2 * (size_t)g.nt * 2);
+  w->meas_partial = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt * 2 * gx * MEAS_NV);
+  w->slice_sum = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt * MEAS_NV);
+  w->slice_F = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt);
+  w->slice_theta = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt);
+  w->totals = (double *)p;
+  p = align16(p + sizeof(double) * TOT_N);
+  w->sweep_counter = (unsigned *)p;
+  p = align16(p + sizeof(unsigned) * (size_t)g.nt);
+  w->meas_counter = (unsigned *)p;
+  p = align16(p + sizeof(unsigned) * (size_t)g.nt);
+  w->glob_counter = (unsigned *)p;
+  p = align16(p + sizeof(unsigned));
+  w->err = (int *)p;
+  p = align16(p + sizeof(int));
+  w->active = (uint8_t *)p;
+}
+
+// ----------------------------------------------------------------- sweeps
+struct SweepArgs {
+  Geom g;
+  void *links;
+  void *G;
+  const uint8_t *active;
+  double *partial;    // [nt][gridDim.x][2]
+  unsigned *counter;  // [nt]
+  double *fused;      // [2][nt][2]
+  double omega;
+  unsigned long long sr_thr;
+  unsigned long long seed;
+  unsigned long long sweep;
+  int transform_temporal;
+  int reunit;
+};
+
+// Fixed-order per-slice sum of the block partials by the slice's last block.
+template <typename T>
+__device__ __forceinline__ void fused_reduce(const SweepArgs &a, int p, int t, T acc[2]) {
+  __shared__ double tot[2];
+  __shared__ int am_last;
+  block_sum<2, T>(acc, tot);
+  if (threadIdx.x == 0) {
+    double *dst = a.partial + ((size_t)t * gridDim.x + blockIdx.x) * 2;
+    dst[0] = tot[0];
+    dst[1] = tot[1];
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.counter[t], 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double v[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double *src = a.partial + ((size_t)t * gridDim.x + b) * 2;
+    v[0] += __ldcg(src);
+    v[1] += __ldcg(src + 1);
+  }
+  block_sum<2, double>(v, tot);
+  if (threadIdx.x == 0) {
+    a.fused[((size_t)p * a.g.nt + t) * 2] = tot[0];
+    a.fused[((size_t)p * a.g.nt + t) * 2 + 1] = tot[1];
+    a.counter[t] = 0u;
+  }
+}
+
+__device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
+  const unsigned long long lex =
+      (unsigned long long)c.x1 +
+      (unsigned long long)a.g.n1 * ((unsigned long long)c.x2 +
+                                    (unsigned long long)a.g.n2 * ((unsigned long long)c.x3 +
+                                                                  (unsigned long long)a.g.n3 * (unsigned long long)c.t));
+  const uint4 ctr = make_uint4((uint32_t)lex, (uint32_t)(lex >> 32), (uint32_t)a.sweep, LGT_SR_TAG);
+  const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+  return philox4x32_10(ctr, key);
+}
+
+// FP32 link formats: all links of the site in registers.  12-real links stay
+// compressed (rows 0, 1) and row 2 is rebuilt where it is needed.
+template <int FMT, int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_f32(SweepArgs a, int p) {
+  typedef LinkIO<FMT> IO;
+  const int t = blockIdx.y;
+  if (a.active && !a.active[t]) return;  // whole block belongs to one slice
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[2] = {0.0f, 0.0f};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    float uf[4][18], ub[4][18];
+    int nb[4];
+#pragma unroll
+    for (int mu = MU0; mu < 4; mu++) {
+      nb[mu] = cb_shift(a.g, c, mu, -1);
+      IO::load_raw(a.links, a.g.vh, p, mu, i, uf[mu]);
+      IO::load_raw(a.links, a.g.vh, q, mu, nb[mu], ub[mu]);
+    }
+    float W[18];
+    mat_zero(W);
+#pragma unroll
+    for (int mu = MU0; mu < 4; mu++) {
+      if (IO::kCompressed) {
+        float full[18];
+#pragma unroll
+        for (int e = 0; e < 18; e++) full[e] = uf[mu][e];
+        rebuild_row2(full);
+        acc_add(W, full);
+#pragma unroll
+        for (int e = 0; e < 18; e++) full[e] = ub[mu][e];
+        rebuild_row2(full);
+        acc_add_dag(W, full);
+      } else {
+        acc_add(W, uf[mu]);
+        acc_add_dag(W, ub[mu]);
+      }
+    }
+    violation_of_K(W, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    float gm[18];
+    local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+#pragma unroll
+    for (int mu = MU0; mu < 4; mu++) {
+      float r[18];
+      if (IO::kCompressed) rebuild_row2(uf[mu]);  // g U needs row 2 of U
+      mat_mul(gm, uf[mu], r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, p, mu, i, r);
+      mat_mul_dag(ub[mu], gm, r);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, q, mu, nb[mu], r);
+    }
+    if (GAUGE == GAUGE_COULOMB && a.transform_temporal) {
+      const int nb0 = cb_shift(a.g, c, 0, -1);
+      float u[18], r[18];
+      IO::load(a.links, a.g.vh, p, 0, i, u);
+      mat_mul(gm, u, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, p, 0, i, r);
+      IO::load(a.links, a.g.vh, q, 0, nb0, u);
+      mat_mul_dag(u, gm, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, q, 0, nb0, r);
+    }
+    if (a.G) {
+      float gx[18], r[18];
+      GIO::load(a.G, a.g.vh, p, i, gx);
+      mat_mul(gm, gx, r);
+      if (a.reunit) reunitarise(r);
+      GIO::store(a.G, a.g.vh, p, i, r);
+    }
+  }
+  fused_reduce<float>(a, p, t, acc);
+}
+
+// FP64: K gathered streaming, links re-read for the write-back.
+template <int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
+  typedef LinkIO<FMT_F64> IO;
+  const int t = blockIdx.y;
+  if (a.active && !a.active[t]) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    int nb[4];
+    double W[18];
+    mat_zero(W);
+#pragma unroll
+    for (int mu = MU0; mu < 4; mu++) {
+      double u[18];
+      nb[mu] = cb_shift(a.g, c, mu, -1);
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      acc_add(W, u);
+      IO::load(a.links, a.g.vh, q, mu, nb[mu], u);
+      acc_add_dag(W, u);
+    }
+    violation_of_K(W, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    double gm[18];
+    local_update<double, ALGO>(W, gm, a.omega, a.sr_thr, draws);
+    const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
+    for (int mu = mu_lo; mu < 4; mu++) {
+      const int nbm = mu < MU0 ? cb_shift(a.g, c, 0, -1) : nb[mu];
+      double u[18], r[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      mat_mul(gm, u, r);
+      IO::store(a.links, a.g.vh, p, mu, i, r);
+      IO::load(a.links, a.g.vh, q, mu, nbm, u);
+      mat_mul_dag(u, gm, r);
+      IO::store(a.links, a.g.vh, q, mu, nbm, r);
+    }
+  }
+  fused_reduce<double>(a, p, t, acc);
+}
+
+typedef void (*sweep_fn)(SweepArgs, int);
+
+static sweep_fn pick_sweep(int fmt, int gauge, int algo) {
+#define LGT_PICK(F, G, A) \
+  if (fmt == F && gauge == G && algo == A) return (F == FMT_F64) ? (sweep_fn)k_sweep_f64<G, A> : (sweep_fn)k_sweep_f32<(F == FMT_F64 ? FMT_F32_18 : F), G, A>;
+  LGT_PICK(FMT_F64, GAUGE_LANDAU, ALGO_OR)
+  LGT_PICK(FMT_F64, GAUGE_LANDAU, ALGO_SR)
+  LGT_PICK(FMT_F64, GAUGE_COULOMB, ALGO_OR)
+  LGT_PICK(FMT_F64, GAUGE_COULOMB, ALGO_SR)
+  LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_OR)
+  LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_SR)
+  LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_OR)
+  LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_SR)
+  LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_OR)
+  LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_SR)
+  LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_OR)
+  LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_SR)
+#undef LGT_PICK
+  return nullptr;
+}
+
+cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                              int parity, unsigned long long sweep, int reunit, int use_mask, int block,
+                              cudaStream_t st) {
+  sweep_fn fn = pick_sweep(fmt, c.gauge, c.algo);
+  if (!fn) return cudaErrorInvalidValue;
+  SweepArgs a;
+  a.g = g;
+  a.links = links;
+  a.G = G;
+  a.active = use_mask ? w.active : nullptr;
+  a.partial = w.sweep_partial;
+  a.counter = w.sweep_counter;
+  a.fused = w.fused;
+  a.omega = c.omega;
+  a.sr_thr = c.sr_thr;
+  a.seed = c.seed;
+  a.sweep = sweep;
+  a.transform_temporal = c.transform_temporal;
+  a.reunit = reunit;
+  dim3 grid(ceil_div(g.vs_half, block), g.nt);
+  fn<<<grid, block, 0, st>>>(a, parity & 1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ measurement
+struct MeasArgs {
+  Geom g;
+  const void *links;
+  double *partial;      // [nt][2][gridDim.x][MEAS_NV]
+  unsigned *counter;    // [nt]
+  unsigned *glob;       // [1]
+  double *slice_sum;    // [nt][MEAS_NV]
+  double *slice_F;      // [nt]
+  double *slice_theta;  // [nt]
+  double *totals;       // [TOT_N]
+  uint8_t *active;      // [nt]
+  double coulomb_target;
+  int with_plaq;
+};
+
+template <int FMT>
+__device__ __forceinline__ void load_d(const void *base, int vh, int p, int mu, int i, double m[18]) {
+  typedef typename LinkIO<FMT>::real R;
+  R r[18];
+  LinkIO<FMT>::load(base, vh, p, mu, i, r);
+#pragma unroll
+  for (int k = 0; k < 18; k++) m[k] = (double)r[k];
+}
+
+// X += s * (U - U^dagger)
+__device__ __forceinline__ void acc_antiherm(double X[18], const double u[18], double s) {
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      X[LGT_RE(a, b)] += s * (u[LGT_RE(a, b)] - u[LGT_RE(b, a)]);
+      X[LGT_IM(a, b)] += s * (u[LGT_IM(a, b)] + u[LGT_IM(b, a)]);
+    }
+}
+
+// tr[D D^dagger] for D = traceless part of X/(2i), X anti-Hermitian
+__device__ __forceinline__ double traceless_norm(const double X[18]) {
+  const double d0 = 0.5 * X[LGT_IM(0, 0)], d1 = 0.5 * X[LGT_IM(1, 1)], d2 = 0.5 * X[LGT_IM(2, 2)];
+  const double tr3 = (d0 + d1 + d2) * (1.0 / 3.0);
+  double s = (d0 - tr3) * (d0 - tr3) + (d1 - tr3) * (d1 - tr3) + (d2 - tr3) * (d2 - tr3);
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = a + 1; b < 3; b++) s += 0.5 * (X[LGT_RE(a, b)] * X[LGT_RE(a, b)] + X[LGT_IM(a, b)] * X[LGT_IM(a, b)]);
+  return s;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
+  const int t = blockIdx.y, p = blockIdx.z;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[MEAS_NV];
+#pragma unroll
+  for (int k = 0; k < MEAS_NV; k++) v[k] = 0.0;
+  if (j < a.g.vs_half) {
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    double XL[18], XS[18];
+    mat_zero(XL);
+    mat_zero(XS);
+    for (int mu = 0; mu < 4; mu++) {
+      double u[18];
+      load_d<FMT>(a.links, a.g.vh, p, mu, i, u);
+      const double rt = u[LGT_RE(0, 0)] + u[LGT_RE(1, 1)] + u[LGT_RE(2, 2)];
+      v[0] += rt;
+      acc_antiherm(XL, u, 1.0);
+      if (mu > 0) {
+        v[1] += rt;
+        acc_antiherm(XS, u, 1.0);
+      }
+      load_d<FMT>(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+      acc_antiherm(XL, u, -1.0);
+      if (mu > 0) acc_antiherm(XS, u, -1.0);
+    }
+    v[2] = traceless_norm(XL);
+    v[3] = traceless_norm(XS);
+    if (a.with_plaq) {
+      for (int mu = 0; mu < 4; mu++)
+        for (int nu = mu + 1; nu < 4; nu++) {
+          double ua[18], ub[18], uc[18], ud[18], m1[18], m2[18];
+          load_d<FMT>(a.links, a.g.vh, p, mu, i, ua);
+          load_d<FMT>(a.links, a.g.vh, q, nu, cb_shift(a.g, c, mu, +1), ub);
+          load_d<FMT>(a.links, a.g.vh, q, mu, cb_shift(a.g, c, nu, +1), uc);
+          load_d<FMT>(a.links, a.g.vh, p, nu, i, ud);
+          mat_mul(ua, ub, m1);       // U_mu(x) U_nu(x+mu)
+          mat_mul(ud, uc, m2);       // U_nu(x) U_mu(x+nu)
+          // Re tr[m1 m2^dagger] = sum_ab Re(m1_ab conj(m2_ab))
+          double s = 0.0;
+#pragma unroll
+          for (int e = 0; e < 18; e++) s += m1[e] * m2[e];
+          v[4] += s;
+        }
+    }
+  }
+  __shared__ double tot[MEAS_NV];
+  __shared__ int am_last;
+  block_sum<MEAS_NV, double>(v, tot);
+  const int nblk = gridDim.x * 2;  // blocks of this slice
+  const int bidx = p * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) {
+    double *dst = a.partial + ((size_t)t * nblk + bidx) * MEAS_NV;
+#pragma unroll
+    for (int k = 0; k < MEAS_NV; k++) dst[k] = tot[k];
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.counter[t], 1u);
+    am_last = (prev == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  // last block of slice t: fixed-order sum over the slice's blocks
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < MEAS_NV; k++) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    const double *src = a.partial + ((size_t)t * nblk + b) * MEAS_NV;
+#pragma unroll
+    for (int k = 0; k < MEAS_NV; k++) v[k] += __ldcg(src + k);
+  }
+  block_sum<MEAS_NV, double>(v, tot);
+  __shared__ int am_final;
+  if (threadIdx.x == 0) {
+    const double vs = 2.0 * (double)a.g.vs_half;
+#pragma unroll
+    for (int k = 0; k < MEAS_NV; k++) a.slice_sum[(size_t)t * MEAS_NV + k] = tot[k];
+    const double ft = tot[1] / (9.0 * vs);
+    const double tt = tot[3] / (3.0 * vs);
+    a.slice_F[t] = ft;
+    a.slice_theta[t] = tt;
+    if (a.coulomb_target >= 0.0) a.active[t] = (tt >= a.coulomb_target) ? 1 : 0;
+    a.counter[t] = 0u;
+    __threadfence();
+    const unsigned prev = atomicAdd(a.glob, 1u);
+    am_final = (prev == (unsigned)a.g.nt - 1);
+  }
+  __syncthreads();
+  if (!am_final || threadIdx.x != 0) return;
+  // final block: totals over slices in slice order
+  __threadfence();
+  double s[MEAS_NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double fsum = 0.0, tmax = 0.0, tsum = 0.0;
+  int nact = 0;
+  for (int tt = 0; tt < a.g.nt; tt++) {
+#pragma unroll
+    for (int k = 0; k < MEAS_NV; k++) s[k] += __ldcg(a.slice_sum + (size_t)tt * MEAS_NV + k);
+    const double th = __ldcg(a.slice_theta + tt);
+    fsum += __ldcg(a.slice_F + tt);
+    tsum += th;
+    tmax = th > tmax ? th : tmax;
+    nact += (int)(*(volatile uint8_t *)(a.active + tt));
+  }
+  const double vol = 2.0 * (double)a.g.vh;
+  a.totals[TOT_F_LANDAU] = s[0] / (12.0 * vol);
+  a.totals[TOT_THETA_LANDAU] = s[2] / (3.0 * vol);
+  a.totals[TOT_PLAQ] = s[4] / (18.0 * vol);
+  a.totals[TOT_F_COULOMB] = fsum / (double)a.g.nt;
+  a.totals[TOT_THETA_COULOMB_MAX] = tmax;
+  a.totals[TOT_THETA_COULOMB_MEAN] = tsum / (double)a.g.nt;
+  a.totals[TOT_ACTIVE_SLICES] = (double)nact;
+  *a.glob = 0u;
+}
+
+cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
+                           double coulomb_target, int block, cudaStream_t st) {
+  MeasArgs a;
+  a.g = g;
+  a.links = links;
+  a.partial = w.meas_partial;
+  a.counter = w.meas_counter;
+  a.glob = w.glob_counter;
+  a.slice_sum = w.slice_sum;
+  a.slice_F = w.slice_F;
+  a.slice_theta = w.slice_theta;
+  a.totals = w.totals;
+  a.active = w.active;
+  a.coulomb_target = coulomb_target;
+  a.with_plaq = with_plaq;
+  dim3 grid(ceil_div(g.vs_half, block), g.nt, 2);
+  if (fmt == FMT_F64) k_measure<FMT_F64><<<grid, block, 0, st>>>(a);
+  else if (fmt == FMT_F32_18) k_measure<FMT_F32_18><<<grid, block, 0, st>>>(a);
+  else if (fmt == FMT_F32_12) k_measure<FMT_F32_12><<<grid, block, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- layout / ingest
+// thread -> (parity, direction, within-parity index); lexicographic site
+__device__ __forceinline__ bool link_of_thread(const Geom &g, long long gid, int &p, int &mu, int &i, Coords &c,
+                                               long long &lex) {
+  if (gid >= (long long)g.vh * 8) return false;
+  i = (int)(gid % g.vh);
+  const int pm = (int)(gid / g.vh);
+  p = pm >> 2;
+  mu = pm & 3;
+  const int t = i / g.vs_half;
+  c = coords_in_slice(g, p, t, i - t * g.vs_half);
+  lex = (long long)c.x1 + (long long)g.n1 * (c.x2 + (long long)g.n2 * (c.x3 + (long long)g.n3 * c.t));
+  return true;
+}
+
+template <int FMT>
+__global__ void k_ingest(Geom g, const double *aos, void *soa, int *err) {
+  int p, mu, i;
+  Coords c;
+  long long lex;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!link_of_thread(g, gid, p, mu, i, c, lex)) return;
+  const double *src = aos + ((size_t)lex * 4 + mu) * 18;
+  double u[18];
+  bool finite = true;
+#pragma unroll
+  for (int k = 0; k < 18; k++) {
+    u[k] = src[k];
+    finite = finite && isfinite(u[k]);
+  }
+  // SU(3) check: |U^dagger U - 1|_max and |det U - 1|
+  double worst = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {  // sum_k conj(U_ka) U_kb
+        re += u[LGT_RE(k, a)] * u[LGT_RE(k, b)] + u[LGT_IM(k, a)] * u[LGT_IM(k, b)];
+        im += u[LGT_RE(k, a)] * u[LGT_IM(k, b)] - u[LGT_IM(k, a)] * u[LGT_RE(k, b)];
+      }
+      re -= (a == b) ? 1.0 : 0.0;
+      worst = fmax(worst, fmax(fabs(re), fabs(im)));
+    }
+  double dre = 0.0, dim = 0.0;
+#pragma unroll
+  for (int cc = 0; cc < 3; cc++) {
+    const int a1 = (cc + 1) % 3, b1 = (cc + 2) % 3;
+    const double mre = u[LGT_RE(1, a1)] * u[LGT_RE(2, b1)] - u[LGT_IM(1, a1)] * u[LGT_IM(2, b1)] -
+                       (u[LGT_RE(1, b1)] * u[LGT_RE(2, a1)] - u[LGT_IM(1, b1)] * u[LGT_IM(2, a1)]);
+    const double mim = u[LGT_RE(1, a1)] * u[LGT_IM(2, b1)] + u[LGT_IM(1, a1)] * u[LGT_RE(2, b1)] -
+                       (u[LGT_RE(1, b1)] * u[LGT_IM(2, a1)] + u[LGT_IM(1, b1)] * u[LGT_RE(2, a1)]);
+    dre += u[LGT_RE(0, cc)] * mre - u[LGT_IM(0, cc)] * mim;
+    dim += u[LGT_RE(0, cc)] * mim + u[LGT_IM(0, cc)] * mre;
+  }
+  worst = fmax(worst, fmax(fabs(dre - 1.0), fabs(dim)));
+  if (!finite || !(worst < 1e-10)) atomicOr(err, 1);
+  typedef typename LinkIO<FMT>::real R;
+  R r[18];
+#pragma unroll
+  for (int k = 0; k < 18; k++) r[k] = (R)u[k];
+  LinkIO<FMT>::store(soa, g.vh, p, mu, i, r);
+}
+
+template <int FMT>
+__global__ void k_egress(Geom g, const void *soa, double *aos) {
+  int p, mu, i;
+  Coords c;
+  long long lex;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!link_of_thread(g, gid, p, mu, i, c, lex)) return;
+  double u[18];
+  load_d<FMT>(soa, g.vh, p, mu, i, u);
+  double *dst = aos + ((size_t)lex * 4 + mu) * 18;
+#pragma unroll
+  for (int k = 0; k < 18; k++) dst[k] = u[k];
+}
+
+cudaError_t launch_ingest(int fmt, const Geom &g, const double *aos, void *soa, int *err, cudaStream_t st) {
+  const long long n = (long long)g.vh * 8;
+  const int blk = 256;
+  const unsigned grid = (unsigned)((n + blk - 1) / blk);
+  if (fmt == FMT_F64) k_ingest<FMT_F64><<<grid, blk, 0, st>>>(g, aos, soa, err);
+  else if (fmt == FMT_F32_18) k_ingest<FMT_F32_18><<<grid, blk, 0, st>>>(g, aos, soa, err);
+  else if (fmt == FMT_F32_12) k_ingest<FMT_F32_12><<<grid, blk, 0, st>>>(g, aos, soa, err);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_egress(int fmt, const Geom &g, const void *soa, double *aos, cudaStream_t st) {
+  const long long n = (long long)g.vh * 8;
+  const int blk = 256;
+  const unsigned grid = (unsigned)((n + blk - 1) / blk);
+  if (fmt == FMT_F64) k_egress<FMT_F64><<<grid, blk, 0, st>>>(g, soa, aos);
+  else if (fmt == FMT_F32_18) k_egress<FMT_F32_18><<<grid, blk, 0, st>>>(g, soa, aos);
+  else if (fmt == FMT_F32_12) k_egress<FMT_F32_12><<<grid, blk, 0, st>>>(g, soa, aos);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ accumulated transformation
+__global__ void k_g_identity(Geom g, void *G) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)g.vh * 2) return;
+  const int p = (int)(gid / g.vh), i = (int)(gid % g.vh);
+  float m[18];
+  mat_zero(m);
+  m[LGT_RE(0, 0)] = m[LGT_RE(1, 1)] = m[LGT_RE(2, 2)] = 1.0f;
+  GIO::store(G, g.vh, p, i, m);
+}
+
+cudaError_t launch_g_identity(const Geom &g, void *G, cudaStream_t st) {
+  const long long n = (long long)g.vh * 2;
+  const int blk = 256;
+  k_g_identity<<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, G);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ void load_G_fp64(const void *G, int vh, int p, int i, double m[18]) {
+  float f[18];
+  GIO::load(G, vh, p, i, f);
+#pragma unroll
+  for (int k = 0; k < 18; k++) m[k] = (double)f[k];
+  reunitarise(m);
+}
+
+__global__ void k_apply_G(Geom g, const void *G, const void *u_in, void *u_out, double *aos_out, int skip_temporal) {
+  int p, mu, i;
+  Coords c;
+  long long lex;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!link_of_thread(g, gid, p, mu, i, c, lex)) return;
+  double u[18], r[18], gx[18], gy[18], tmp[18];
+  LinkIO<FMT_F64>::load(u_in, g.vh, p, mu, i, u);
+  if (skip_temporal && mu == 0) {
+#pragma unroll
+    for (int k = 0; k < 18; k++) r[k] = u[k];
+  } else {
+    load_G_fp64(G, g.vh, p, i, gx);
+    load_G_fp64(G, g.vh, p ^ 1, cb_shift(g, c, mu, +1), gy);
+    mat_mul(gx, u, tmp);
+    mat_mul_dag(tmp, gy, r);
+  }
+  if (aos_out) {
+    double *dst = aos_out + ((size_t)lex * 4 + mu) * 18;
+#pragma unroll
+    for (int k = 0; k < 18; k++) dst[k] = r[k];
+  } else {
+    LinkIO<FMT_F64>::store(u_out, g.vh, p, mu, i, r);
+  }
+}
+
+cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, void *u64_out, double *aos_out,
+                           int skip_temporal, cudaStream_t st) {
+  const long long n = (long long)g.vh * 8;
+  const int blk = 128;
+  k_apply_G<<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, G, u64_in, u64_out, aos_out, skip_temporal);
+  return cudaGetLastError();
+}
+
+}  // namespace lgt

@@ -1,0 +1,280 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: one sweep from the same input agrees to 1e-12 max-abs per link
+entry in FP64 and 5e-6 on FP32 link storage; converged runs agree in F to
+1e-10 with theta below the requested 1e-14 (converged links are not unique:
+a global gauge rotation or another Gribov copy changes them, so links are only
+compared after a fixed number of sweeps).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_3440_gb300 import synth
+from lattice_np import plaquettes, unitarity_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lgt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1305_3440_gb300 import build
+    build.build()
+    from paper_1305_3440_gb300 import lgt as mod
+    return mod
+
+
+GAUGES = {"landau": O.LANDAU, "coulomb": O.COULOMB}
+ALGOS = {"or": O.OR, "sr": O.SR}
+# several tiles per timeslice and a ragged tail (block 128: vs_half = 420 -> 3 full + 36)
+DIMS_RAGGED = (4, 6, 10, 14)
+
+
+def gpu_run(lgt, U, n, working=False, **kw):
+    dims = U.shape[:4]
+    p = lgt.lgt_params_default(dims=dims, **kw)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        if n:
+            lgt.lgt_sweep(ctx, n)
+        out = lgt.lgt_get_working_links(ctx, dims) if working else lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    return out
+
+
+def test_layout_roundtrip_is_exact(lgt):
+    U = synth.field(DIMS_RAGGED, 0.5, 3)
+    assert np.array_equal(gpu_run(lgt, U, 0), U)
+    for bulk, tol in [(lgt.LGT_FP32_18, 1.5e-7), (lgt.LGT_FP32_12, 1e-6)]:
+        assert np.array_equal(gpu_run(lgt, U, 0, bulk=bulk), U)  # G = 1 on the FP64 input
+        assert np.abs(gpu_run(lgt, U, 0, working=True, bulk=bulk) - U).max() < tol
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), DIMS_RAGGED, (2, 2, 2, 2), (6, 2, 4, 2)])
+def test_measurement_matches_oracle(lgt, dims):
+    U = synth.field(dims, 0.6, 4)
+    p = lgt.lgt_params_default(dims=dims)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        F, th, pl = lgt.lgt_measure(ctx)
+        Ft, tht = lgt.lgt_measure_slices(ctx, dims[0])
+    finally:
+        lgt.lgt_destroy(ctx)
+    m = O.measure(U)
+    mc = O.measure(U, O.COULOMB)
+    assert abs(F - m["F"]) < 1e-13 and abs(pl - m["plaq"]) < 1e-13
+    assert abs(th - m["theta"]) < 1e-13 * m["theta"]
+    assert np.allclose(Ft, mc["F_t"], rtol=0, atol=1e-13)
+    assert np.allclose(tht, mc["theta_t"], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("gauge", list(GAUGES))
+@pytest.mark.parametrize("algo", list(ALGOS))
+@pytest.mark.parametrize("dims,block", [(DIMS_RAGGED, 128), ((8, 8, 8, 8), 64), ((2, 4, 2, 6), 256)])
+def test_one_sweep_fp64_matches_oracle(lgt, gauge, algo, dims, block):
+    U = synth.field(dims, 0.5, 5)
+    kw = dict(gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=77, sweep_offset=3)
+    got = gpu_run(lgt, U, 2, block_size=block, **kw)
+    ref = U.copy()
+    O.sweeps(ref, 2, gauge=kw["gauge"], algo=kw["algo"], omega=1.7, p=0.8, seed=77, sweep0=3)
+    assert np.abs(got - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("bulk", ["fp32_18", "fp32_12"])
+@pytest.mark.parametrize("gauge", list(GAUGES))
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_one_sweep_fp32_matches_oracle(lgt, bulk, gauge, algo):
+    U = synth.field(DIMS_RAGGED, 0.5, 6)
+    b = lgt.LGT_FP32_18 if bulk == "fp32_18" else lgt.LGT_FP32_12
+    kw = dict(gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=78)
+    got = gpu_run(lgt, U, 1, working=True, bulk=b, reunit_every=0, **kw)
+    ref = U.copy()
+    O.sweeps(ref, 1, gauge=kw["gauge"], algo=kw["algo"], omega=1.7, p=0.8, seed=78)
+    assert np.abs(got - ref).max() < 5e-6
+    # the FP64 field G U G^dagger tracks the oracle as closely
+    full = gpu_run(lgt, U, 1, working=False, bulk=b, reunit_every=0, **kw)
+    assert np.abs(full - ref).max() < 5e-6
+
+
+def test_coulomb_temporal_option(lgt):
+    U = synth.field((4, 4, 6, 4), 0.5, 7)
+    got = gpu_run(lgt, U, 2, gauge=lgt.LGT_COULOMB, transform_temporal=0, omega=1.5)
+    ref = U.copy()
+    O.sweeps(ref, 2, gauge=O.COULOMB, omega=1.5, transform_temporal=0)
+    assert np.abs(got - ref).max() < 1e-12
+    assert np.array_equal(got[..., 0, :, :], U[..., 0, :, :])
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_18", "fp32_12"])
+def test_fix_8x4_matches_oracle(lgt, bulk):
+    """SU(3) Landau 8^4, eps = 0.3, seed 1, OR omega = 1.7 to theta < 1e-14."""
+    b = {"fp64": lgt.LGT_FP64, "fp32_18": lgt.LGT_FP32_18, "fp32_12": lgt.LGT_FP32_12}[bulk]
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 0.3, 1)
+    p = lgt.lgt_params_default(dims=dims, omega=1.7, bulk=b, max_sweeps=1000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    ref = U.copy()
+    r = O.fix(ref, omega=1.7, tol=1e-14, max_sweeps=1000)
+    assert st == lgt.LGT_OK and res.status == lgt.LGT_OK
+    assert res.theta < 1e-14 and abs(res.F - r["F"]) < 1e-10
+    m = O.measure(V)  # the oracle certifies the returned field
+    assert m["theta"] < 1e-14 and abs(m["F"] - res.F) < 1e-13
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+    e, d = unitarity_error(V)
+    assert e < 1e-12 and d < 1e-12
+    if b == lgt.LGT_FP64:
+        assert res.sweeps_bulk == 0 and res.sweeps_fp64 > 0
+    else:
+        assert res.sweeps_bulk > 0
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_12"])
+def test_fix_coulomb_matches_oracle(lgt, bulk):
+    b = lgt.LGT_FP64 if bulk == "fp64" else lgt.LGT_FP32_12
+    dims = (6, 8, 8, 8)
+    U = synth.field(dims, 0.5, 3)
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_COULOMB, omega=1.7, bulk=b, max_sweeps=2000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    ref = U.copy()
+    r = O.fix(ref, gauge=O.COULOMB, omega=1.7, tol=1e-14, max_sweeps=2000)
+    assert st == lgt.LGT_OK and r["converged"]
+    mg = O.measure(V, O.COULOMB)
+    mo = O.measure(ref, O.COULOMB)
+    assert np.all(mg["theta_t"] < 1e-14)
+    assert np.abs(mg["F_t"] - mo["F_t"]).max() < 1e-10
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+
+
+def test_stochastic_relaxation_fix(lgt):
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 0.3, 9)
+    p = lgt.lgt_params_default(dims=dims, algo=lgt.LGT_SR, p=0.8, seed=5, bulk=lgt.LGT_FP32_18,
+                               max_sweeps=3000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    ref = U.copy()
+    r = O.fix(ref, algo=O.SR, p=0.8, seed=5, tol=1e-14, max_sweeps=3000)
+    assert st == lgt.LGT_OK and r["converged"] and abs(res.F - r["F"]) < 1e-10
+
+
+def test_results_are_deterministic_and_load_restarts(lgt):
+    dims = (4, 8, 8, 8)
+    U = synth.field(dims, 0.5, 10)
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, max_sweeps=3000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st1, r1 = lgt.lgt_fix(ctx)
+        V1 = lgt.lgt_get_links(ctx, dims)
+        lgt.lgt_load(ctx, U)
+        assert lgt.lgt_get_progress(ctx) == (0, 0, 0)
+        st2, r2 = lgt.lgt_fix(ctx)
+        V2 = lgt.lgt_get_links(ctx, dims)
+        stats = lgt.lgt_get_stats(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st1 == st2 == lgt.LGT_OK
+    assert r1.F == r2.F and r1.theta == r2.theta and r1.sweeps_bulk == r2.sweeps_bulk
+    assert np.array_equal(V1, V2)
+    assert stats.sweep_launches[0] == 2 * r2.sweeps_bulk and stats.sweep_ms[0] > 0
+    assert stats.site_updates[0] == r2.sweeps_bulk * np.prod(dims)
+
+
+def test_device_resident_links(lgt):
+    import torch
+    dims = (4, 4, 6, 8)
+    U = synth.field(dims, 0.5, 11)
+    dev = torch.from_numpy(U).cuda()
+    out = torch.empty_like(dev)
+    p = lgt.lgt_params_default(dims=dims, omega=1.7)
+    s = torch.cuda.Stream()
+    ctx = lgt.lgt_create(p, dev, stream=s)
+    try:
+        lgt.lgt_sweep(ctx, 3)
+        lgt.lgt_get_links(ctx, out=out)
+    finally:
+        lgt.lgt_destroy(ctx)
+    ref = U.copy()
+    O.sweeps(ref, 3, omega=1.7)
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-12
+
+
+def test_rejects_non_su3_and_non_finite(lgt):
+    dims = (4, 4, 4, 4)
+    U = synth.field(dims, 0.5, 12)
+    p = lgt.lgt_params_default(dims=dims)
+    bad = U.copy()
+    bad[1, 2, 3, 0, 2, 1, 1] *= 1.001
+    with pytest.raises(lgt.LgtError) as e:
+        lgt.lgt_create(p, bad)
+    assert e.value.status == lgt.LGT_EINVAL and "SU(3)" in lgt.lgt_last_error()
+    bad = U.copy()
+    bad[0, 0, 0, 1, 0, 0, 0] = np.nan
+    with pytest.raises(lgt.LgtError):
+        lgt.lgt_create(p, bad)
+
+
+def test_not_converged_is_reported(lgt):
+    dims = (4, 4, 4, 4)
+    U = synth.field(dims, 0.5, 13)
+    p = lgt.lgt_params_default(dims=dims, max_sweeps=4, check_every=2)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        # the state is kept: continuing converges
+        p2 = lgt.lgt_get_progress(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_ENOTCONV and res.status == lgt.LGT_ENOTCONV and res.sweeps_fp64 == 4
+    assert p2[1] == 4
+
+
+# ------------------------------------------------------- full size: 32^4
+@pytest.fixture(scope="module")
+def field_32():
+    """SU(3) Landau 32^4, eps = 0.5, seed 2 (the benchmark's field)."""
+    return synth.field((32, 32, 32, 32), 0.5, 2)
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_18", "fp32_12"])
+def test_full_size_one_sweep_32(lgt, field_32, bulk):
+    b = {"fp64": lgt.LGT_FP64, "fp32_18": lgt.LGT_FP32_18, "fp32_12": lgt.LGT_FP32_12}[bulk]
+    got = gpu_run(lgt, field_32, 1, working=True, bulk=b, omega=1.7, reunit_every=0)
+    ref = field_32.copy()
+    O.sweeps(ref, 1, omega=1.7)
+    err = np.abs(got - ref).max()
+    assert err < (1e-12 if b == lgt.LGT_FP64 else 5e-6), err
+
+
+def test_full_size_fix_32_properties(lgt, field_32):
+    """The benchmark's run (FP32-12 bulk + FP64 polish to 1e-14): the oracle certifies
+    theta < 1e-14 on the returned field; every plaquette and unitarity are kept."""
+    dims = (32, 32, 32, 32)
+    p = lgt.lgt_params_default(dims=dims, omega=1.7, bulk=lgt.LGT_FP32_12, max_sweeps=20000)
+    ctx = lgt.lgt_create(p, field_32)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and res.theta < 1e-14
+    m = O.measure(V)
+    assert m["theta"] < 1e-14 and abs(m["F"] - res.F) < 1e-12
+    assert np.abs(plaquettes(V) - plaquettes(field_32)).max() < 1e-12
+    e, d = unitarity_error(V)
+    assert e < 1e-12 and d < 1e-12
