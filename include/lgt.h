@@ -131,6 +131,12 @@ LGT_API lgt_status lgt_create(const lgt_params *params, const double *links, int
  * convergence test.  Coulomb: every slice is updated.  n >= 0. */
 LGT_API lgt_status lgt_sweep(lgt_ctx *ctx, int32_t n);
 
+/* One half-sweep: every site of `parity` (0 even, 1 odd) gets its local
+ * update (Sec. 3: all sites of one parity subset at once; Sec. 4: one parity
+ * per kernel launch).  The SR counter is the current sweep number; it and the
+ * sweep count advance after parity 1.  Coulomb: every slice is updated. */
+LGT_API lgt_status lgt_half_sweep(lgt_ctx *ctx, int32_t parity);
+
 /* Exact measurement of the current working field, FP64 arithmetic and
  * fixed-order FP64 sums (Sec. 2: F and theta; plus the average plaquette).
  * In the bulk phase the working field is the FP32 links (widened).

@@ -369,28 +369,44 @@ extern "C" void lgt_destroy(lgt_ctx *ctx) {
 }
 
 // ------------------------------------------------------------------ sweeps
-static lgt_status run_sweeps(lgt_ctx *c, int n, int use_mask) {
+// half-sweeps [first_parity .. first_parity + n_half) (parity alternating);
+// the sweep counter advances after each odd half
+static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_mask) {
   const int fmt = c->phase == 0 ? c->bulk_fmt : FMT_F64;
   void *links = c->phase == 0 ? c->u32 : c->u64;
   void *G = c->phase == 0 ? c->G : nullptr;
   const int kind = c->phase == 0 ? 0 : 1;
-  if (n <= 0) return LGT_OK;
+  if (n_half <= 0) return LGT_OK;
   const int bt = batch_begin(c, kind);
-  for (int s = 0; s < n; s++) {
+  for (int h = 0; h < n_half; h++) {
+    const int parity = (first_parity + h) & 1;
     int reunit = 0;
     if (c->phase == 0 && c->prm.reunit_every > 0) reunit = ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
-    for (int parity = 0; parity < 2; parity++)
-      LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask,
-                                 c->block, c->stream));
-    c->sweep_index++;
-    if (c->phase == 0) c->sweeps_bulk++;
-    else c->sweeps_fp64++;
+    LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask,
+                               c->block, c->stream));
+    if (parity == 1) {
+      c->sweep_index++;
+      if (c->phase == 0) c->sweeps_bulk++;
+      else c->sweeps_fp64++;
+    }
   }
   batch_end(c, bt);
-  c->stats.sweep_launches[kind] += 2 * (int64_t)n;
-  c->stats.launches += 2 * (int64_t)n;
-  c->stats.site_updates[kind] += (int64_t)n * 2 * (int64_t)c->g.vh;
+  c->stats.sweep_launches[kind] += n_half;
+  c->stats.launches += n_half;
+  c->stats.site_updates[kind] += (int64_t)n_half * (int64_t)c->g.vh;
   return LGT_OK;
+}
+
+static lgt_status run_sweeps(lgt_ctx *c, int n, int use_mask) { return run_halves(c, 0, 2 * n, use_mask); }
+
+extern "C" lgt_status lgt_half_sweep(lgt_ctx *ctx, int32_t parity) {
+  if (!ctx || (parity != 0 && parity != 1)) {
+    lgt_set_error("lgt_half_sweep: bad arguments");
+    return LGT_EINVAL;
+  }
+  lgt_status st = run_halves(ctx, parity, 1, 0);
+  if (st != LGT_OK) return st;
+  return sync_stream(ctx);
 }
 
 extern "C" lgt_status lgt_sweep(lgt_ctx *ctx, int32_t n) {

@@ -76,6 +76,7 @@ _sigs = {
     "lgt_params_default": ([_P(lgt_params)], ctypes.c_int),
     "lgt_create": ([_P(lgt_params), _vp, ctypes.c_int, _vp, _P(_vp)], ctypes.c_int),
     "lgt_sweep": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lgt_half_sweep": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lgt_measure": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)], ctypes.c_int),
     "lgt_measure_slices": ([_vp, _vp, _vp], ctypes.c_int),
     "lgt_fix": ([_vp, _P(lgt_result)], ctypes.c_int),
@@ -165,6 +166,10 @@ def lgt_create(params: lgt_params, links, stream=None):
 
 def lgt_sweep(ctx, n: int) -> None:
     _check(_lib.lgt_sweep(ctx, int(n)))
+
+
+def lgt_half_sweep(ctx, parity: int) -> None:
+    _check(_lib.lgt_half_sweep(ctx, int(parity)))
 
 
 def lgt_measure(ctx):
