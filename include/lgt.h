@@ -81,6 +81,13 @@ typedef enum {
   LGT_FP32_12 = 2  /* bulk sweeps on FP32 links stored as rows 0,1 (12 reals) */
 } lgt_prec;
 
+/* Kernel of the FP64 sweeps that follow an FP32 bulk phase.  MIXED keeps
+ * FP64 link storage, FP64 K(x) and FP64 sums, and computes the local update
+ * as g = 1 + delta with the small delta and the link increments delta U in
+ * FP32 (added in FP64).  FP64 does every operation in FP64.  With
+ * bulk = LGT_FP64 every sweep uses the FP64 kernel. */
+typedef enum { LGT_POLISH_MIXED = 0, LGT_POLISH_FP64 = 1 } lgt_polish;
+
 typedef struct {
   int32_t dims[4];            /* N_t, N_3, N_2, N_1 */
   int32_t gauge;              /* lgt_gauge */
@@ -97,6 +104,8 @@ typedef struct {
   int32_t check_every;        /* exact theta check every k sweeps */
   int32_t reunit_every;       /* reunitarise FP32 links / G every n sweeps (0: never) */
   int32_t block_size;         /* threads per block of the sweep kernel (0: autotuned) */
+  int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
+  int32_t reserved;           /* must be 0 */
 } lgt_params;
 
 typedef struct {
@@ -112,7 +121,7 @@ typedef struct {
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-11, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0.  dims are zeroed.  Never fails for p != NULL. */
+ * transform_temporal 1, block_size 0, polish LGT_POLISH_MIXED.  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);
 
 /* Create a context for one lattice (Sec. 2 problem statement).

@@ -63,6 +63,8 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->check_every = 10;
   p->reunit_every = 50;
   p->block_size = 0;
+  p->polish = LGT_POLISH_MIXED;
+  p->reserved = 0;
   return LGT_OK;
 }
 
@@ -107,6 +109,10 @@ lgt_status lgt_validate_params(const lgt_params *p) {
   }
   if (p->max_sweeps < 0 || p->check_every < 1 || p->reunit_every < 0) {
     lgt_set_error("max_sweeps >= 0, check_every >= 1, reunit_every >= 0 required");
+    return LGT_EINVAL;
+  }
+  if (p->polish != LGT_POLISH_MIXED && p->polish != LGT_POLISH_FP64) {
+    lgt_set_error("polish %d unknown", p->polish);
     return LGT_EINVAL;
   }
   if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) {
@@ -371,8 +377,13 @@ extern "C" void lgt_destroy(lgt_ctx *ctx) {
 // ------------------------------------------------------------------ sweeps
 // half-sweeps [first_parity .. first_parity + n_half) (parity alternating);
 // the sweep counter advances after each odd half
+// kernel of the FP64 phase: mixed-arithmetic polish after an FP32 bulk phase
+static int fp64_kernel(const lgt_ctx *c) {
+  return (c->prm.bulk != LGT_FP64 && c->prm.polish == LGT_POLISH_MIXED) ? (int)FMT_F64_MIXED : (int)FMT_F64;
+}
+
 static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_mask) {
-  const int fmt = c->phase == 0 ? c->bulk_fmt : FMT_F64;
+  const int fmt = c->phase == 0 ? c->bulk_fmt : fp64_kernel(c);
   void *links = c->phase == 0 ? c->u32 : c->u64;
   void *G = c->phase == 0 ? c->G : nullptr;
   const int kind = c->phase == 0 ? 0 : 1;

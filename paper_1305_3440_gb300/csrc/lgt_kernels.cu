@@ -252,9 +252,63 @@ __global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
   fused_reduce<double>(a, p, t, acc);
 }
 
+// FP64 links, mixed arithmetic (the polishing sweeps of the precision
+// ladder): K is gathered in FP64, the local update is formed as
+// g = 1 + delta with delta in FP32 (local_update_delta), and each link gets
+// U + delta U (resp. U + U delta^dagger) with the small increment computed in
+// FP32 and added in FP64.  Storage, K and every sum stay FP64; FP32 only ever
+// carries deviations from the identity.
+template <int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_f64_mixed(SweepArgs a, int p) {
+  typedef LinkIO<FMT_F64> IO;
+  const int t = blockIdx.y;
+  if (a.active && !a.active[t]) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    int nb[4];
+    double W[18];
+    mat_zero(W);
+#pragma unroll
+    for (int mu = MU0; mu < 4; mu++) {
+      double u[18];
+      nb[mu] = cb_shift(a.g, c, mu, -1);
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      acc_add(W, u);
+      IO::load(a.links, a.g.vh, q, mu, nb[mu], u);
+      acc_add_dag(W, u);
+    }
+    violation_of_K(W, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    float d[18];
+    local_update_delta<ALGO>(W, d, (float)a.omega, a.sr_thr, draws);
+    const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
+    for (int mu = mu_lo; mu < 4; mu++) {
+      const int nbm = mu < MU0 ? cb_shift(a.g, c, 0, -1) : nb[mu];
+      double u[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      apply_left_delta(d, u);
+      IO::store(a.links, a.g.vh, p, mu, i, u);
+      IO::load(a.links, a.g.vh, q, mu, nbm, u);
+      apply_right_delta_dag(d, u);
+      IO::store(a.links, a.g.vh, q, mu, nbm, u);
+    }
+  }
+  fused_reduce<double>(a, p, t, acc);
+}
+
 typedef void (*sweep_fn)(SweepArgs, int);
 
 static sweep_fn pick_sweep(int fmt, int gauge, int algo) {
+  if (fmt == FMT_F64_MIXED) {
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_f64_mixed<GAUGE_LANDAU, ALGO_SR> : k_sweep_f64_mixed<GAUGE_LANDAU, ALGO_OR>;
+    return algo == ALGO_SR ? k_sweep_f64_mixed<GAUGE_COULOMB, ALGO_SR> : k_sweep_f64_mixed<GAUGE_COULOMB, ALGO_OR>;
+  }
 #define LGT_PICK(F, G, A) \
   if (fmt == F && gauge == G && algo == A) return (F == FMT_F64) ? (sweep_fn)k_sweep_f64<G, A> : (sweep_fn)k_sweep_f32<(F == FMT_F64 ? FMT_F32_18 : F), G, A>;
   LGT_PICK(FMT_F64, GAUGE_LANDAU, ALGO_OR)
