@@ -81,12 +81,16 @@ typedef enum {
   LGT_FP32_12 = 2  /* bulk sweeps on FP32 links stored as rows 0,1 (12 reals) */
 } lgt_prec;
 
-/* Kernel of the FP64 sweeps that follow an FP32 bulk phase.  MIXED keeps
- * FP64 link storage, FP64 K(x) and FP64 sums, and computes the local update
- * as g = 1 + delta with the small delta and the link increments delta U in
- * FP32 (added in FP64).  FP64 does every operation in FP64.  With
- * bulk = LGT_FP64 every sweep uses the FP64 kernel. */
-typedef enum { LGT_POLISH_MIXED = 0, LGT_POLISH_FP64 = 1 } lgt_polish;
+/* Precision of the polishing sweeps that follow an FP32 bulk phase.
+ * PAIR: links held as FP32 pairs (hi + lo, ~48-bit significand, converted
+ *   in place from the promoted FP64 field); K(x) accumulated in pair
+ *   arithmetic; the SU(2) rotation angles chosen in FP32; each rotation
+ *   formed unitary to second order and applied to the links in pair
+ *   arithmetic, so every update is a gauge transformation to ~2^-48.
+ *   Runs on the FP32 pipe.
+ * FP64: every operation in FP64.
+ * With bulk = LGT_FP64 every sweep uses the FP64 kernel. */
+typedef enum { LGT_POLISH_PAIR = 0, LGT_POLISH_FP64 = 1 } lgt_polish;
 
 typedef struct {
   int32_t dims[4];            /* N_t, N_3, N_2, N_1 */
@@ -114,14 +118,14 @@ typedef struct {
   double plaquette;     /* average plaquette Re tr U_P / 3 (gauge invariant) */
   double seconds;       /* wall time of the call */
   int64_t sweeps_bulk;  /* sweeps run in the bulk FP32 precision */
-  int64_t sweeps_fp64;  /* sweeps run in FP64 */
+  int64_t sweeps_fp64;  /* sweeps run after promotion (FP64 or FP32-pair polish) */
   int32_t status;       /* lgt_status of the job */
   int32_t reserved;
 } lgt_result;
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-11, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0, polish LGT_POLISH_MIXED.  dims are zeroed.  Never fails for p != NULL. */
+ * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR.  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);
 
 /* Create a context for one lattice (Sec. 2 problem statement).
@@ -180,7 +184,8 @@ LGT_API lgt_status lgt_get_links(lgt_ctx *ctx, double *out, int out_on_device);
  * storage with its third row rebuilt; FP64 phase: as lgt_get_links). */
 LGT_API lgt_status lgt_get_working_links(lgt_ctx *ctx, double *out, int out_on_device);
 
-/* Sweeps run so far in each precision and the phase (0 bulk, 1 FP64). */
+/* Sweeps run so far (bulk FP32; after promotion) and the phase: 0 bulk
+ * FP32, 1 FP64 storage, 2 FP32-pair polish. */
 LGT_API lgt_status lgt_get_progress(lgt_ctx *ctx, int64_t *sweeps_bulk, int64_t *sweeps_fp64, int32_t *phase);
 
 /* Replace the context's field with new links (same dims and params) and

@@ -63,7 +63,7 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->check_every = 10;
   p->reunit_every = 50;
   p->block_size = 0;
-  p->polish = LGT_POLISH_MIXED;
+  p->polish = LGT_POLISH_PAIR;
   p->reserved = 0;
   return LGT_OK;
 }
@@ -111,7 +111,7 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("max_sweeps >= 0, check_every >= 1, reunit_every >= 0 required");
     return LGT_EINVAL;
   }
-  if (p->polish != LGT_POLISH_MIXED && p->polish != LGT_POLISH_FP64) {
+  if (p->polish != LGT_POLISH_PAIR && p->polish != LGT_POLISH_FP64) {
     lgt_set_error("polish %d unknown", p->polish);
     return LGT_EINVAL;
   }
@@ -154,7 +154,7 @@ struct lgt_ctx {
   lgt_params prm;
   Geom g;
   cudaStream_t stream;
-  int phase;      // 0 bulk (FP32), 1 FP64
+  int phase;      // 0 bulk (FP32), 1 FP64 storage, 2 FP32-pair storage (in u64)
   int bulk_fmt;   // FMT_* of the bulk phase
   void *u64;      // FP64 links (the input while in the bulk phase)
   void *u32;      // bulk working links
@@ -377,13 +377,13 @@ extern "C" void lgt_destroy(lgt_ctx *ctx) {
 // ------------------------------------------------------------------ sweeps
 // half-sweeps [first_parity .. first_parity + n_half) (parity alternating);
 // the sweep counter advances after each odd half
-// kernel of the FP64 phase: mixed-arithmetic polish after an FP32 bulk phase
-static int fp64_kernel(const lgt_ctx *c) {
-  return (c->prm.bulk != LGT_FP64 && c->prm.polish == LGT_POLISH_MIXED) ? (int)FMT_F64_MIXED : (int)FMT_F64;
+// storage format (and kernel) of the working field in the current phase
+static int work_fmt(const lgt_ctx *c) {
+  return c->phase == 0 ? c->bulk_fmt : (c->phase == 2 ? (int)FMT_PAIR : (int)FMT_F64);
 }
 
 static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_mask) {
-  const int fmt = c->phase == 0 ? c->bulk_fmt : fp64_kernel(c);
+  const int fmt = work_fmt(c);
   void *links = c->phase == 0 ? c->u32 : c->u64;
   void *G = c->phase == 0 ? c->G : nullptr;
   const int kind = c->phase == 0 ? 0 : 1;
@@ -438,7 +438,7 @@ struct Meas {
 
 // exact measurement of the working field; coulomb_target >= 0 updates masks
 static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas *m) {
-  const int fmt = c->phase == 0 ? c->bulk_fmt : FMT_F64;
+  const int fmt = work_fmt(c);
   const void *links = c->phase == 0 ? c->u32 : c->u64;
   const int bt = batch_begin(c, 2);
   LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream));
@@ -496,11 +496,16 @@ extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *thet
 
 // --------------------------------------------------------------- promotion
 static lgt_status promote(lgt_ctx *c) {
-  if (c->phase == 1) return LGT_OK;
+  if (c->phase != 0) return LGT_OK;
   const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
   LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_t, c->stream));
   c->stats.launches++;
   c->phase = 1;
+  if (c->prm.polish == LGT_POLISH_PAIR) {
+    LGT_CUDA(launch_convert_pair(c->g, c->u64, 1, c->stream));
+    c->stats.launches++;
+    c->phase = 2;
+  }
   return sync_stream(c);
 }
 
@@ -604,7 +609,7 @@ static lgt_status to_output(lgt_ctx *c, double *out, int out_on_device, int work
     dst = tmp;
   }
   cudaError_t e;
-  if (c->phase == 1) e = launch_egress(FMT_F64, g, c->u64, dst, c->stream);
+  if (c->phase >= 1) e = launch_egress(work_fmt(c), g, c->u64, dst, c->stream);
   else if (working) e = launch_egress(c->bulk_fmt, g, c->u32, dst, c->stream);
   else {
     const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;

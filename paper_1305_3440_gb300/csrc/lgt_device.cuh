@@ -20,9 +20,11 @@
 namespace lgt {
 
 enum { FMT_F64 = 0, FMT_F32_18 = 1, FMT_F32_12 = 2 };
-// FP64 storage swept with the mixed-arithmetic polishing kernel (a kernel
-// choice, not a storage format: addressing is that of FMT_F64)
-enum { FMT_F64_MIXED = 3 };
+// FP32-pair storage (each real an unevaluated sum hi + lo of two floats,
+// ~48-bit significand): 9 float4 chunks per link, (hi_re, lo_re, hi_im, lo_im)
+// of element c in chunk c -- the same 16 B per element as FMT_F64, so a field
+// converts in place.
+enum { FMT_PAIR = 3 };
 enum { GAUGE_LANDAU = 0, GAUGE_COULOMB = 1 };
 enum { ALGO_OR = 0, ALGO_SR = 1 };
 
@@ -79,7 +81,7 @@ __device__ __forceinline__ int cb_shift(const Geom &g, const Coords &c, int mu, 
 // ------------------------------------------------------------- link formats
 __host__ __device__ __forceinline__ size_t link_bytes_per_half_site(int fmt) {
   // bytes of 4 links of one site (one parity's share of one site)
-  return fmt == FMT_F64 ? 4 * 144 : (fmt == FMT_F32_18 ? 4 * 72 : 4 * 48);
+  return (fmt == FMT_F64 || fmt == FMT_PAIR) ? 4 * 144 : (fmt == FMT_F32_18 ? 4 * 72 : 4 * 48);
 }
 
 template <int FMT>
@@ -428,125 +430,6 @@ __device__ __forceinline__ void local_update(R W[18], R g[18], R omega, uint64_t
       }
     }
   }
-}
-
-// Near-identity form of local_update for FP64 links (the polishing sweeps).
-// W = K stays FP64 (its anti-Hermitian part is a small difference of O(1)
-// numbers near convergence); each subgroup element is formed as R = 1 + rho
-// with rho in FP32 from the FP64 projection q, and the update comes back as
-// delta = g - 1 in FP32.  Every FP32 quantity here is a small deviation from
-// the identity, so its relative FP32 error costs only |delta| * 1e-7 absolute.
-// Same steps as local_update: projection, closed-form maximum, first-order
-// overrelaxation or squaring, W <- R W, g <- R g.
-template <int ALGO>
-__device__ __forceinline__ void local_update_delta(double W[18], float d[18], float omega, uint64_t sr_thr,
-                                                   uint4 draws) {
-#pragma unroll
-  for (int s = 0; s < 3; s++) {
-    const int i = (s == 2) ? 1 : 0;
-    const int j = (s == 0) ? 1 : 2;
-    const float q0 = (float)(W[LGT_RE(i, i)] + W[LGT_RE(j, j)]);
-    const float q1 = (float)(W[LGT_IM(i, j)] + W[LGT_IM(j, i)]);
-    const float q2 = (float)(W[LGT_RE(i, j)] - W[LGT_RE(j, i)]);
-    const float q3 = (float)(W[LGT_IM(i, i)] - W[LGT_IM(j, j)]);
-    const float v2 = q1 * q1 + q2 * q2 + q3 * q3;
-    const float n2 = q0 * q0 + v2;
-    float e0 = 0.0f, r1 = 0.0f, r2 = 0.0f, r3 = 0.0f;  // r = (1 + e0, r1, r2, r3)
-    if (n2 > 0.0f) {
-      const float inv = rsqrtf(n2);
-      const float n = n2 * inv;
-      r1 = -q1 * inv;
-      r2 = -q2 * inv;
-      r3 = -q3 * inv;
-      // r0 - 1 = (q0 - |q|)/|q| = -|q_vec|^2 / (|q| (q0 + |q|)) without cancellation
-      e0 = q0 > 0.0f ? -v2 * inv / (q0 + n) : q0 * inv - 1.0f;
-    }
-    if (ALGO == ALGO_OR) {
-      // (1 - omega) 1 + omega r = (1 + omega e0, omega r_vec), rescaled to unit length
-      const float a0 = omega * e0;
-      r1 *= omega;
-      r2 *= omega;
-      r3 *= omega;
-      const float t = a0 * (2.0f + a0) + (r1 * r1 + r2 * r2 + r3 * r3);  // |s|^2 - 1
-      const float sq = sqrtf(1.0f + t);
-      const float inv = 1.0f / sq;
-      e0 = a0 * inv - t * inv / (1.0f + sq);  // (1 + a0)/|s| - 1
-      r1 *= inv;
-      r2 *= inv;
-      r3 *= inv;
-    } else {
-      const uint32_t dr = s == 0 ? draws.x : (s == 1 ? draws.y : draws.z);
-      if ((uint64_t)dr < sr_thr) {  // r^2 = (r0^2 - |r|^2, 2 r0 r_vec)
-        const float vv = r1 * r1 + r2 * r2 + r3 * r3;
-        const float f2 = 2.0f * (1.0f + e0);
-        e0 = e0 * (2.0f + e0) - vv;
-        r1 *= f2;
-        r2 *= f2;
-        r3 *= f2;
-      }
-    }
-    // rho on rows/cols (i, j): [[e0 + i r3, r2 + i r1], [-r2 + i r1, e0 - i r3]]
-    if (s < 2) {  // W <- W + rho W (rho W in FP32, added in FP64)
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const float wire = (float)W[LGT_RE(i, c)], wiim = (float)W[LGT_IM(i, c)];
-        const float wjre = (float)W[LGT_RE(j, c)], wjim = (float)W[LGT_IM(j, c)];
-        W[LGT_RE(i, c)] += (double)(e0 * wire - r3 * wiim + r2 * wjre - r1 * wjim);
-        W[LGT_IM(i, c)] += (double)(e0 * wiim + r3 * wire + r2 * wjim + r1 * wjre);
-        W[LGT_RE(j, c)] += (double)(-r2 * wire - r1 * wiim + e0 * wjre + r3 * wjim);
-        W[LGT_IM(j, c)] += (double)(-r2 * wiim + r1 * wire + e0 * wjim - r3 * wjre);
-      }
-    }
-    if (s == 0) {
-      mat_zero(d);
-      d[LGT_RE(0, 0)] = e0;
-      d[LGT_IM(0, 0)] = r3;
-      d[LGT_RE(0, 1)] = r2;
-      d[LGT_IM(0, 1)] = r1;
-      d[LGT_RE(1, 0)] = -r2;
-      d[LGT_IM(1, 0)] = r1;
-      d[LGT_RE(1, 1)] = e0;
-      d[LGT_IM(1, 1)] = -r3;
-    } else {  // delta <- rho + delta + rho delta
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const float dire = d[LGT_RE(i, c)], diim = d[LGT_IM(i, c)];
-        const float djre = d[LGT_RE(j, c)], djim = d[LGT_IM(j, c)];
-        d[LGT_RE(i, c)] += e0 * dire - r3 * diim + r2 * djre - r1 * djim;
-        d[LGT_IM(i, c)] += e0 * diim + r3 * dire + r2 * djim + r1 * djre;
-        d[LGT_RE(j, c)] += -r2 * dire - r1 * diim + e0 * djre + r3 * djim;
-        d[LGT_IM(j, c)] += -r2 * diim + r1 * dire + e0 * djim - r3 * djre;
-      }
-      d[LGT_RE(i, i)] += e0;
-      d[LGT_IM(i, i)] += r3;
-      d[LGT_RE(i, j)] += r2;
-      d[LGT_IM(i, j)] += r1;
-      d[LGT_RE(j, i)] += -r2;
-      d[LGT_IM(j, i)] += r1;
-      d[LGT_RE(j, j)] += e0;
-      d[LGT_IM(j, j)] += -r3;
-    }
-  }
-}
-
-// U <- U + delta U  (delta = g - 1 in FP32; U FP64; the product in FP32)
-__device__ __forceinline__ void apply_left_delta(const float d[18], double u[18]) {
-  float uf[18], r[18];
-#pragma unroll
-  for (int k = 0; k < 18; k++) uf[k] = (float)u[k];
-  mat_mul(d, uf, r);
-#pragma unroll
-  for (int k = 0; k < 18; k++) u[k] += (double)r[k];
-}
-
-// U <- U + U delta^dagger  (U g^dagger with g = 1 + delta)
-__device__ __forceinline__ void apply_right_delta_dag(const float d[18], double u[18]) {
-  float uf[18], r[18];
-#pragma unroll
-  for (int k = 0; k < 18; k++) uf[k] = (float)u[k];
-  mat_mul_dag(uf, d, r);
-#pragma unroll
-  for (int k = 0; k < 18; k++) u[k] += (double)r[k];
 }
 
 // Re tr K and tr[Delta Delta^dagger] with Delta = traceless part of

@@ -82,4 +82,8 @@ cudaError_t launch_g_identity(const Geom &g, void *G, cudaStream_t st);
 cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, void *u64_out, double *aos_out,
                            int skip_temporal, cudaStream_t st);
 
+// In-place conversion of an FP64 field to FP32-pair storage (to_pair = 1)
+// or back (to_pair = 0).
+cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_t st);
+
 }  // namespace lgt

@@ -19,6 +19,7 @@
 
 #include "lgt_device.cuh"
 #include "lgt_internal.h"
+#include "lgt_pair.cuh"
 
 namespace lgt {
 
@@ -83,28 +84,32 @@ struct SweepArgs {
   unsigned long long sweep;
   int transform_temporal;
   int reunit;
+  // batched launches only: reunitarise when (count_base + s + 1) % reunit_every == 0
+  int reunit_every;
+  long long count_base;
 };
 
 // Fixed-order per-slice sum of the block partials by the slice's last block.
+// bx: this block's index within timeslice t, nbx: blocks per timeslice.
 template <typename T>
-__device__ __forceinline__ void fused_reduce(const SweepArgs &a, int p, int t, T acc[2]) {
+__device__ __forceinline__ void fused_reduce(const SweepArgs &a, int p, int t, int bx, int nbx, T acc[2]) {
   __shared__ double tot[2];
   __shared__ int am_last;
   block_sum<2, T>(acc, tot);
   if (threadIdx.x == 0) {
-    double *dst = a.partial + ((size_t)t * gridDim.x + blockIdx.x) * 2;
+    double *dst = a.partial + ((size_t)t * nbx + bx) * 2;
     dst[0] = tot[0];
     dst[1] = tot[1];
     __threadfence();
     const unsigned prev = atomicAdd(&a.counter[t], 1u);
-    am_last = (prev == gridDim.x - 1);
+    am_last = (prev == (unsigned)nbx - 1);
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
   double v[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    const double *src = a.partial + ((size_t)t * gridDim.x + b) * 2;
+  for (int b = threadIdx.x; b < nbx; b += blockDim.x) {
+    const double *src = a.partial + ((size_t)t * nbx + b) * 2;
     v[0] += __ldcg(src);
     v[1] += __ldcg(src + 1);
   }
@@ -130,11 +135,10 @@ __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
 // FP32 link formats: all links of the site in registers.  12-real links stay
 // compressed (rows 0, 1) and row 2 is rebuilt where it is needed.
 template <int FMT, int GAUGE, int ALGO>
-__global__ void __launch_bounds__(256) k_sweep_f32(SweepArgs a, int p) {
+__device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t, int bx, int nbx) {
   typedef LinkIO<FMT> IO;
-  const int t = blockIdx.y;
   if (a.active && !a.active[t]) return;  // whole block belongs to one slice
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = bx * blockDim.x + threadIdx.x;
   float acc[2] = {0.0f, 0.0f};
   if (j < a.g.vs_half) {
     constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
@@ -204,16 +208,20 @@ __global__ void __launch_bounds__(256) k_sweep_f32(SweepArgs a, int p) {
       GIO::store(a.G, a.g.vh, p, i, r);
     }
   }
-  fused_reduce<float>(a, p, t, acc);
+  fused_reduce<float>(a, p, t, bx, nbx, acc);
+}
+
+template <int FMT, int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_f32(SweepArgs a, int p) {
+  sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // FP64: K gathered streaming, links re-read for the write-back.
 template <int GAUGE, int ALGO>
-__global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
+__device__ __forceinline__ void sweep_body_f64(const SweepArgs &a, int p, int t, int bx, int nbx) {
   typedef LinkIO<FMT_F64> IO;
-  const int t = blockIdx.y;
   if (a.active && !a.active[t]) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = bx * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};
   if (j < a.g.vs_half) {
     constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
@@ -249,65 +257,79 @@ __global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
       IO::store(a.links, a.g.vh, q, mu, nbm, r);
     }
   }
-  fused_reduce<double>(a, p, t, acc);
+  fused_reduce<double>(a, p, t, bx, nbx, acc);
 }
 
-// FP64 links, mixed arithmetic (the polishing sweeps of the precision
-// ladder): K is gathered in FP64, the local update is formed as
-// g = 1 + delta with delta in FP32 (local_update_delta), and each link gets
-// U + delta U (resp. U + U delta^dagger) with the small increment computed in
-// FP32 and added in FP64.  Storage, K and every sum stay FP64; FP32 only ever
-// carries deviations from the identity.
 template <int GAUGE, int ALGO>
-__global__ void __launch_bounds__(256) k_sweep_f64_mixed(SweepArgs a, int p) {
-  typedef LinkIO<FMT_F64> IO;
-  const int t = blockIdx.y;
+__global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
+  sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// FP32-pair polishing sweep (FMT_PAIR storage): K(x) in pair arithmetic, the
+// rotation angles in FP32, the three SU(2) elements applied to every link in
+// pair arithmetic (see lgt_pair.cuh).  Links are re-read for the write-back.
+template <int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t, int bx, int nbx) {
+  typedef LinkIO<FMT_PAIR> IO;
   if (a.active && !a.active[t]) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2] = {0.0, 0.0};
+  const int j = bx * blockDim.x + threadIdx.x;
+  float acc[2] = {0.0f, 0.0f};
   if (j < a.g.vs_half) {
     constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
     const Coords c = coords_in_slice(a.g, p, t, j);
     const int i = t * a.g.vs_half + j;
     const int q = p ^ 1;
     int nb[4];
-    double W[18];
-    mat_zero(W);
+    f2 W[18];
+#pragma unroll
+    for (int e = 0; e < 18; e++) W[e] = f2{0.0f, 0.0f};
 #pragma unroll
     for (int mu = MU0; mu < 4; mu++) {
-      double u[18];
+      f2 u[18];
       nb[mu] = cb_shift(a.g, c, mu, -1);
       IO::load(a.links, a.g.vh, p, mu, i, u);
-      acc_add(W, u);
+#pragma unroll
+      for (int e = 0; e < 18; e++) W[e] = pair_add(W[e], u[e]);
       IO::load(a.links, a.g.vh, q, mu, nb[mu], u);
-      acc_add_dag(W, u);
+#pragma unroll
+      for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) {  // K += U^dagger
+          W[LGT_RE(r, cc)] = pair_add(W[LGT_RE(r, cc)], u[LGT_RE(cc, r)]);
+          W[LGT_IM(r, cc)] = pair_add(W[LGT_IM(r, cc)], pair_neg(u[LGT_IM(cc, r)]));
+        }
     }
-    violation_of_K(W, acc[0], acc[1]);
+    pair_violation(W, acc[0], acc[1]);
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
-    float d[18];
-    local_update_delta<ALGO>(W, d, (float)a.omega, a.sr_thr, draws);
+    Rot rot[3];
+    pair_local_update<ALGO>(W, rot, (float)a.omega, a.sr_thr, draws);
     const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
     for (int mu = mu_lo; mu < 4; mu++) {
       const int nbm = mu < MU0 ? cb_shift(a.g, c, 0, -1) : nb[mu];
-      double u[18];
+      f2 u[18];
       IO::load(a.links, a.g.vh, p, mu, i, u);
-      apply_left_delta(d, u);
+      pair_apply_left(u, rot);
       IO::store(a.links, a.g.vh, p, mu, i, u);
       IO::load(a.links, a.g.vh, q, mu, nbm, u);
-      apply_right_delta_dag(d, u);
+      pair_apply_right_dag(u, rot);
       IO::store(a.links, a.g.vh, q, mu, nbm, u);
     }
   }
-  fused_reduce<double>(a, p, t, acc);
+  fused_reduce<float>(a, p, t, bx, nbx, acc);
+}
+
+template <int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_pair(SweepArgs a, int p) {
+  sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 typedef void (*sweep_fn)(SweepArgs, int);
 
 static sweep_fn pick_sweep(int fmt, int gauge, int algo) {
-  if (fmt == FMT_F64_MIXED) {
-    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_f64_mixed<GAUGE_LANDAU, ALGO_SR> : k_sweep_f64_mixed<GAUGE_LANDAU, ALGO_OR>;
-    return algo == ALGO_SR ? k_sweep_f64_mixed<GAUGE_COULOMB, ALGO_SR> : k_sweep_f64_mixed<GAUGE_COULOMB, ALGO_OR>;
+  if (fmt == FMT_PAIR) {
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_pair<GAUGE_LANDAU, ALGO_SR> : k_sweep_pair<GAUGE_LANDAU, ALGO_OR>;
+    return algo == ALGO_SR ? k_sweep_pair<GAUGE_COULOMB, ALGO_SR> : k_sweep_pair<GAUGE_COULOMB, ALGO_OR>;
   }
 #define LGT_PICK(F, G, A) \
   if (fmt == F && gauge == G && algo == A) return (F == FMT_F64) ? (sweep_fn)k_sweep_f64<G, A> : (sweep_fn)k_sweep_f32<(F == FMT_F64 ? FMT_F32_18 : F), G, A>;
@@ -368,12 +390,30 @@ struct MeasArgs {
 };
 
 template <int FMT>
-__device__ __forceinline__ void load_d(const void *base, int vh, int p, int mu, int i, double m[18]) {
-  typedef typename LinkIO<FMT>::real R;
-  R r[18];
-  LinkIO<FMT>::load(base, vh, p, mu, i, r);
+struct LoadD {
+  static __device__ __forceinline__ void run(const void *base, int vh, int p, int mu, int i, double m[18]) {
+    typedef typename LinkIO<FMT>::real R;
+    R r[18];
+    LinkIO<FMT>::load(base, vh, p, mu, i, r);
 #pragma unroll
-  for (int k = 0; k < 18; k++) m[k] = (double)r[k];
+    for (int k = 0; k < 18; k++) m[k] = (double)r[k];
+  }
+};
+
+template <>
+struct LoadD<FMT_PAIR> {
+  static __device__ __forceinline__ void run(const void *base, int vh, int p, int mu, int i, double m[18]) {
+    f2 r[18];
+    LinkIO<FMT_PAIR>::load(base, vh, p, mu, i, r);
+#pragma unroll
+    for (int k = 0; k < 18; k++) m[k] = (double)r[k].hi + (double)r[k].lo;
+  }
+};
+
+// a link of any storage format, widened to FP64
+template <int FMT>
+__device__ __forceinline__ void load_d(const void *base, int vh, int p, int mu, int i, double m[18]) {
+  LoadD<FMT>::run(base, vh, p, mu, i, m);
 }
 
 // X += s * (U - U^dagger)
@@ -400,9 +440,8 @@ __device__ __forceinline__ double traceless_norm(const double X[18]) {
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
-  const int t = blockIdx.y, p = blockIdx.z;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void measure_body(const MeasArgs &a, int t, int p, int bx, int nbx) {
+  const int j = bx * blockDim.x + threadIdx.x;
   double v[MEAS_NV];
 #pragma unroll
   for (int k = 0; k < MEAS_NV; k++) v[k] = 0.0;
@@ -450,8 +489,8 @@ __global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
   __shared__ double tot[MEAS_NV];
   __shared__ int am_last;
   block_sum<MEAS_NV, double>(v, tot);
-  const int nblk = gridDim.x * 2;  // blocks of this slice
-  const int bidx = p * gridDim.x + blockIdx.x;
+  const int nblk = nbx * 2;  // blocks of this slice
+  const int bidx = p * nbx + bx;
   if (threadIdx.x == 0) {
     double *dst = a.partial + ((size_t)t * nblk + bidx) * MEAS_NV;
 #pragma unroll
@@ -514,6 +553,11 @@ __global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
   *a.glob = 0u;
 }
 
+template <int FMT>
+__global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
+  measure_body<FMT>(a, blockIdx.y, blockIdx.z, blockIdx.x, gridDim.x);
+}
+
 cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
                            double coulomb_target, int block, cudaStream_t st) {
   MeasArgs a;
@@ -533,6 +577,7 @@ cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Work
   if (fmt == FMT_F64) k_measure<FMT_F64><<<grid, block, 0, st>>>(a);
   else if (fmt == FMT_F32_18) k_measure<FMT_F32_18><<<grid, block, 0, st>>>(a);
   else if (fmt == FMT_F32_12) k_measure<FMT_F32_12><<<grid, block, 0, st>>>(a);
+  else if (fmt == FMT_PAIR) k_measure<FMT_PAIR><<<grid, block, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -634,6 +679,7 @@ cudaError_t launch_egress(int fmt, const Geom &g, const void *soa, double *aos, 
   if (fmt == FMT_F64) k_egress<FMT_F64><<<grid, blk, 0, st>>>(g, soa, aos);
   else if (fmt == FMT_F32_18) k_egress<FMT_F32_18><<<grid, blk, 0, st>>>(g, soa, aos);
   else if (fmt == FMT_F32_12) k_egress<FMT_F32_12><<<grid, blk, 0, st>>>(g, soa, aos);
+  else if (fmt == FMT_PAIR) k_egress<FMT_PAIR><<<grid, blk, 0, st>>>(g, soa, aos);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -695,6 +741,34 @@ cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, voi
   const long long n = (long long)g.vh * 8;
   const int blk = 128;
   k_apply_G<<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, G, u64_in, u64_out, aos_out, skip_temporal);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- FP64 <-> FP32-pair, in place
+// Each thread owns one 16-byte element chunk: (re, im) as double2 or
+// (hi_re, lo_re, hi_im, lo_im) as float4 at the same address.
+__global__ void k_f64_to_pair(double2 *u, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double2 v = u[k];
+  const float hr = __double2float_rn(v.x), hi = __double2float_rn(v.y);
+  const float lr = __double2float_rn(v.x - (double)hr), li = __double2float_rn(v.y - (double)hi);
+  reinterpret_cast<float4 *>(u)[k] = make_float4(hr, lr, hi, li);
+}
+
+__global__ void k_pair_to_f64(double2 *u, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float4 v = reinterpret_cast<const float4 *>(u)[k];
+  u[k] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_t st) {
+  const long long n = (long long)g.vh * 2 * 4 * 9;
+  const int blk = 256;
+  const unsigned grid = (unsigned)((n + blk - 1) / blk);
+  if (to_pair) k_f64_to_pair<<<grid, blk, 0, st>>>(reinterpret_cast<double2 *>(u), n);
+  else k_pair_to_f64<<<grid, blk, 0, st>>>(reinterpret_cast<double2 *>(u), n);
   return cudaGetLastError();
 }
 

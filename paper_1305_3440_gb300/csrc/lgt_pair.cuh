@@ -1,0 +1,242 @@
+// lgt_pair.cuh -- FP32-pair ("double-float") arithmetic and the pair-precision
+// local update used by the polishing sweeps.
+//
+// A real is held as the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi)/2 (Dekker 1971, Knuth TAOCP vol. 2: the error-free
+// transformations TwoSum and, with a fused multiply-add, TwoProd), which gives a
+// ~48-bit significand using only the FP32 pipe.  On this part FP64 arithmetic
+// and FP64<->FP32 conversion both run at ~2 operations/clock/SM against ~128
+// for FP32, so pair arithmetic is the fast way to carry more than FP32
+// precision.
+//
+// The polishing update keeps two concerns apart:
+//   * the rotation angles (which SU(2) element to apply) are chosen in FP32
+//     from the pair-precision K(x); a slightly suboptimal angle is still a
+//     gauge transformation and only costs optimality;
+//   * every SU(2) element is formed as R = 1 + rho with rho from
+//     (e0 = r0 - 1, r1, r2, r3) in FP32.  e0 is second order in |r| and is
+//     computed without cancellation, so R is unitary to ~2^-24 |r|^2, and R is
+//     applied to the links in pair arithmetic.  The field therefore stays an
+//     exact (to ~2^-48) gauge transform of its input.
+#pragma once
+
+#include "lgt_device.cuh"
+
+namespace lgt {
+
+struct f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ f2 quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+// a + b in pair arithmetic (absolute error ~2^-48 max(|a|, |b|))
+__device__ __forceinline__ f2 pair_add(f2 a, f2 b) {
+  const f2 s = two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ f2 pair_neg(f2 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ float pair_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
+
+// sum_k c[k] * x[k] for float coefficients and pair values: exact products of
+// the high parts (TwoProd via fma), low parts folded in with one rounding each
+__device__ __forceinline__ f2 pair_dot4(float c0, f2 x0, float c1, f2 x1, float c2, f2 x2, float c3, f2 x3) {
+  const float p0 = __fmul_rn(c0, x0.hi), p1 = __fmul_rn(c1, x1.hi);
+  const float p2 = __fmul_rn(c2, x2.hi), p3 = __fmul_rn(c3, x3.hi);
+  float e = __fmaf_rn(c0, x0.hi, -p0);
+  e = __fadd_rn(e, __fmaf_rn(c1, x1.hi, -p1));
+  e = __fadd_rn(e, __fmaf_rn(c2, x2.hi, -p2));
+  e = __fadd_rn(e, __fmaf_rn(c3, x3.hi, -p3));
+  e = __fmaf_rn(c0, x0.lo, e);
+  e = __fmaf_rn(c1, x1.lo, e);
+  e = __fmaf_rn(c2, x2.lo, e);
+  e = __fmaf_rn(c3, x3.lo, e);
+  f2 s = two_sum(p0, p1);
+  e = __fadd_rn(e, s.lo);
+  s = two_sum(s.hi, p2);
+  e = __fadd_rn(e, s.lo);
+  s = two_sum(s.hi, p3);
+  e = __fadd_rn(e, s.lo);
+  return quick_two_sum(s.hi, e);
+}
+
+template <>
+struct LinkIO<FMT_PAIR> {
+  static __device__ __forceinline__ void load(const void *base, int vh, int p, int mu, int i, f2 m[18]) {
+    const float4 *b = reinterpret_cast<const float4 *>(base) + (size_t)((p * 4 + mu) * 9) * vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; c++) {
+      const float4 v = __ldg(b + (size_t)c * vh);
+      m[2 * c] = {v.x, v.y};
+      m[2 * c + 1] = {v.z, v.w};
+    }
+  }
+  static __device__ __forceinline__ void store(void *base, int vh, int p, int mu, int i, const f2 m[18]) {
+    float4 *b = reinterpret_cast<float4 *>(base) + (size_t)((p * 4 + mu) * 9) * vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; c++) b[(size_t)c * vh] = make_float4(m[2 * c].hi, m[2 * c].lo, m[2 * c + 1].hi, m[2 * c + 1].lo);
+  }
+};
+
+// One subgroup element as the FP32 quadruple (e0 = r0 - 1, r1, r2, r3).
+struct Rot {
+  float e0, r1, r2, r3;
+};
+
+// Sec. 3 closed-form SU(2) maximum of the projection (q0, q) (any positive
+// scale), then Sec. 3.1 first-order overrelaxation or Sec. 3.2 squaring, all
+// in the near-identity form r = (1 + e0, r_vec).
+template <int ALGO>
+__device__ __forceinline__ Rot subgroup_rotation(float q0, float q1, float q2, float q3, float omega, bool square) {
+  const float v2 = q1 * q1 + q2 * q2 + q3 * q3;
+  const float n2 = q0 * q0 + v2;
+  Rot r = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (n2 > 0.0f) {
+    const float inv = rsqrtf(n2);
+    const float n = n2 * inv;
+    r.r1 = -q1 * inv;
+    r.r2 = -q2 * inv;
+    r.r3 = -q3 * inv;
+    // r0 - 1 = (q0 - |q|)/|q| = -|q_vec|^2 / (|q| (q0 + |q|)) without cancellation
+    r.e0 = q0 > 0.0f ? -v2 * inv / (q0 + n) : q0 * inv - 1.0f;
+  }
+  if (ALGO == ALGO_OR) {
+    // (1 - omega) 1 + omega r = (1 + omega e0, omega r_vec), rescaled to |.| = 1
+    const float a0 = omega * r.e0;
+    const float s1 = omega * r.r1, s2 = omega * r.r2, s3 = omega * r.r3;
+    const float t = a0 * (2.0f + a0) + (s1 * s1 + s2 * s2 + s3 * s3);  // |s|^2 - 1
+    const float sq = sqrtf(1.0f + t);
+    const float inv = 1.0f / sq;
+    r.e0 = a0 * inv - t * inv / (1.0f + sq);  // (1 + a0)/|s| - 1
+    r.r1 = s1 * inv;
+    r.r2 = s2 * inv;
+    r.r3 = s3 * inv;
+  } else if (square) {  // r^2 = (r0^2 - |r|^2, 2 r0 r_vec)
+    const float vv = r.r1 * r.r1 + r.r2 * r.r2 + r.r3 * r.r3;
+    const float f2x = 2.0f * (1.0f + r.e0);
+    r.e0 = r.e0 * (2.0f + r.e0) - vv;
+    r.r1 *= f2x;
+    r.r2 *= f2x;
+    r.r3 *= f2x;
+  }
+  return r;
+}
+
+// rows (i, j) of m <- R rows, R = [[r0 + i r3, r2 + i r1], [-r2 + i r1, r0 - i r3]],
+// written as m + rho m with rho = R - 1 and the increment in pair arithmetic
+template <int I, int J>
+__device__ __forceinline__ void rotate_rows(f2 m[18], const Rot &r) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const f2 xi = m[LGT_RE(I, c)], yi = m[LGT_IM(I, c)];
+    const f2 xj = m[LGT_RE(J, c)], yj = m[LGT_IM(J, c)];
+    // (e0 + i r3) (xi + i yi) + (r2 + i r1) (xj + i yj)
+    m[LGT_RE(I, c)] = pair_add(xi, pair_dot4(r.e0, xi, -r.r3, yi, r.r2, xj, -r.r1, yj));
+    m[LGT_IM(I, c)] = pair_add(yi, pair_dot4(r.e0, yi, r.r3, xi, r.r2, yj, r.r1, xj));
+    // (-r2 + i r1) (xi + i yi) + (e0 - i r3) (xj + i yj)
+    m[LGT_RE(J, c)] = pair_add(xj, pair_dot4(-r.r2, xi, -r.r1, yi, r.e0, xj, r.r3, yj));
+    m[LGT_IM(J, c)] = pair_add(yj, pair_dot4(-r.r2, yi, r.r1, xi, r.e0, yj, -r.r3, xj));
+  }
+}
+
+// columns (i, j) of m <- m R^dagger
+template <int I, int J>
+__device__ __forceinline__ void rotate_cols_dag(f2 m[18], const Rot &r) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const f2 xi = m[LGT_RE(a, I)], yi = m[LGT_IM(a, I)];
+    const f2 xj = m[LGT_RE(a, J)], yj = m[LGT_IM(a, J)];
+    // m_ai conj(r0 + i r3) + m_aj conj(r2 + i r1) = m_ai (e0 - i r3) + m_aj (r2 - i r1) (+ m_ai)
+    m[LGT_RE(a, I)] = pair_add(xi, pair_dot4(r.e0, xi, r.r3, yi, r.r2, xj, r.r1, yj));
+    m[LGT_IM(a, I)] = pair_add(yi, pair_dot4(r.e0, yi, -r.r3, xi, r.r2, yj, -r.r1, xj));
+    // m_ai conj(-r2 + i r1) + m_aj conj(r0 - i r3) = m_ai (-r2 - i r1) + m_aj (e0 + i r3) (+ m_aj)
+    m[LGT_RE(a, J)] = pair_add(xj, pair_dot4(-r.r2, xi, r.r1, yi, r.e0, xj, -r.r3, yj));
+    m[LGT_IM(a, J)] = pair_add(yj, pair_dot4(-r.r2, yi, -r.r1, xi, r.e0, yj, r.r3, xj));
+  }
+}
+
+// W <- W + rho W on rows (i, j) with the increment in FP32 (it only steers the
+// next subgroup's choice; the applied rotations are exact regardless)
+template <int I, int J>
+__device__ __forceinline__ void steer_rows(f2 W[18], const Rot &r) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const float xi = W[LGT_RE(I, c)].hi, yi = W[LGT_IM(I, c)].hi;
+    const float xj = W[LGT_RE(J, c)].hi, yj = W[LGT_IM(J, c)].hi;
+    W[LGT_RE(I, c)] = pair_add(W[LGT_RE(I, c)], f2{r.e0 * xi - r.r3 * yi + r.r2 * xj - r.r1 * yj, 0.0f});
+    W[LGT_IM(I, c)] = pair_add(W[LGT_IM(I, c)], f2{r.e0 * yi + r.r3 * xi + r.r2 * yj + r.r1 * xj, 0.0f});
+    W[LGT_RE(J, c)] = pair_add(W[LGT_RE(J, c)], f2{-r.r2 * xi - r.r1 * yi + r.e0 * xj + r.r3 * yj, 0.0f});
+    W[LGT_IM(J, c)] = pair_add(W[LGT_IM(J, c)], f2{-r.r2 * yi + r.r1 * xi + r.e0 * yj - r.r3 * xj, 0.0f});
+  }
+}
+
+// Sec. 3 local update at pair precision: the three subgroup elements for
+// W = K (the block projections taken from the pair values without
+// cancellation loss).
+template <int ALGO>
+__device__ __forceinline__ void pair_local_update(f2 W[18], Rot rot[3], float omega, uint64_t sr_thr, uint4 draws) {
+#pragma unroll
+  for (int s = 0; s < 3; s++) {
+    const int i = (s == 2) ? 1 : 0;
+    const int j = (s == 0) ? 1 : 2;
+    const float q0 = pair_to_float(pair_add(W[LGT_RE(i, i)], W[LGT_RE(j, j)]));
+    const float q1 = pair_to_float(pair_add(W[LGT_IM(i, j)], W[LGT_IM(j, i)]));
+    const float q2 = pair_to_float(pair_add(W[LGT_RE(i, j)], pair_neg(W[LGT_RE(j, i)])));
+    const float q3 = pair_to_float(pair_add(W[LGT_IM(i, i)], pair_neg(W[LGT_IM(j, j)])));
+    const uint32_t d = s == 0 ? draws.x : (s == 1 ? draws.y : draws.z);
+    rot[s] = subgroup_rotation<ALGO>(q0, q1, q2, q3, omega, (uint64_t)d < sr_thr);
+    if (s == 0) steer_rows<0, 1>(W, rot[0]);
+    if (s == 1) steer_rows<0, 2>(W, rot[1]);
+  }
+}
+
+// U <- g U = R2 R1 R0 U
+__device__ __forceinline__ void pair_apply_left(f2 u[18], const Rot rot[3]) {
+  rotate_rows<0, 1>(u, rot[0]);
+  rotate_rows<0, 2>(u, rot[1]);
+  rotate_rows<1, 2>(u, rot[2]);
+}
+
+// U <- U g^dagger = U R0^dagger R1^dagger R2^dagger
+__device__ __forceinline__ void pair_apply_right_dag(f2 u[18], const Rot rot[3]) {
+  rotate_cols_dag<0, 1>(u, rot[0]);
+  rotate_cols_dag<0, 2>(u, rot[1]);
+  rotate_cols_dag<1, 2>(u, rot[2]);
+}
+
+// Fused estimate from the pair K: Re tr K and tr[Delta Delta^dagger],
+// Delta = traceless part of (K - K^dagger)/(2i) (differences taken in pairs).
+__device__ __forceinline__ void pair_violation(const f2 K[18], float &retr, float &delta2) {
+  retr = pair_to_float(pair_add(pair_add(K[LGT_RE(0, 0)], K[LGT_RE(1, 1)]), K[LGT_RE(2, 2)]));
+  const float d0 = pair_to_float(K[LGT_IM(0, 0)]), d1 = pair_to_float(K[LGT_IM(1, 1)]);
+  const float d2 = pair_to_float(K[LGT_IM(2, 2)]);
+  const float tr3 = pair_to_float(pair_add(pair_add(K[LGT_IM(0, 0)], K[LGT_IM(1, 1)]), K[LGT_IM(2, 2)])) *
+                    (1.0f / 3.0f);
+  float s = (d0 - tr3) * (d0 - tr3) + (d1 - tr3) * (d1 - tr3) + (d2 - tr3) * (d2 - tr3);
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = a + 1; b < 3; b++) {
+      const float zre = pair_to_float(pair_add(K[LGT_RE(a, b)], pair_neg(K[LGT_RE(b, a)])));
+      const float zim = pair_to_float(pair_add(K[LGT_IM(a, b)], K[LGT_IM(b, a)]));
+      s += 0.5f * (zre * zre + zim * zim);
+    }
+  delta2 = s;
+}
+
+}  // namespace lgt

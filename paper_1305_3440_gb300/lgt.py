@@ -25,7 +25,7 @@ LGT_OK, LGT_EINVAL, LGT_ENOMEM, LGT_ECUDA, LGT_ENOTCONV, LGT_EAGAIN, LGT_ETIMEOU
 LGT_LANDAU, LGT_COULOMB = 0, 1
 LGT_OR, LGT_SR = 0, 1
 LGT_FP64, LGT_FP32_18, LGT_FP32_12 = 0, 1, 2
-LGT_POLISH_MIXED, LGT_POLISH_FP64 = 0, 1
+LGT_POLISH_PAIR, LGT_POLISH_FP64 = 0, 1
 
 STATUS_NAMES = {0: "LGT_OK", 1: "LGT_EINVAL", 2: "LGT_ENOMEM", 3: "LGT_ECUDA", 4: "LGT_ENOTCONV",
                 5: "LGT_EAGAIN", 6: "LGT_ETIMEOUT", 7: "LGT_EBUSY", 8: "LGT_ECANCELLED", 9: "LGT_ENOTFOUND"}

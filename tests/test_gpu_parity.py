@@ -296,28 +296,49 @@ def test_not_converged_is_reported(lgt):
     assert p2[1] == 4
 
 
-# ------------------------------------------- FP64 polish, mixed arithmetic
+# ----------------------------------------------- FP32-pair polishing sweeps
 @pytest.fixture(scope="module")
 def near_fixed_8():
-    """8^4 Landau field relaxed by the oracle to theta ~ 1e-10 (the polish regime)."""
-    U = synth.field((8, 8, 8, 8), 0.3, 1)
-    r = O.fix(U, omega=1.7, tol=1e-10, max_sweeps=1000, check_every=1)
-    assert r["converged"]
-    return U
+    """8^4 fields relaxed by the oracle to theta ~ 1e-10 (the polish regime), per gauge."""
+    out = {}
+    for gauge in (O.LANDAU, O.COULOMB):
+        U = synth.field((8, 8, 8, 8), 0.3, 1)
+        r = O.fix(U, gauge=gauge, omega=1.7, tol=1e-10, max_sweeps=2000, check_every=1)
+        assert r["converged"]
+        out[gauge] = U
+    return out
+
+
+def promoted_ctx(lgt, U, **kw):
+    p = lgt.lgt_params_default(dims=U.shape[:4], bulk=lgt.LGT_FP32_12, polish=lgt.LGT_POLISH_PAIR, **kw)
+    ctx = lgt.lgt_create(p, U)
+    lgt.lgt_promote(ctx)  # G = 1: the pair field is the input to ~2^-48
+    assert lgt.lgt_get_progress(ctx)[2] == 2
+    return ctx
+
+
+def test_pair_storage_roundtrip(lgt):
+    U = synth.field(DIMS_RAGGED, 0.5, 16)
+    ctx = promoted_ctx(lgt, U)
+    try:
+        V = lgt.lgt_get_links(ctx, DIMS_RAGGED)
+        F, th, pl = lgt.lgt_measure(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert np.abs(V - U).max() < 2e-15
+    m = O.measure(U)
+    assert abs(F - m["F"]) < 1e-13 and abs(th - m["theta"]) < 1e-12 * m["theta"]
 
 
 @pytest.mark.parametrize("gauge", list(GAUGES))
 @pytest.mark.parametrize("algo", list(ALGOS))
-def test_mixed_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo):
-    """One polish sweep (FP64 links, FP32 increments) on a field at theta ~ 1e-10 agrees
-    with the FP64 oracle to 1e-12 per link entry: its error is ~|g - 1| * 2^-24."""
-    U = near_fixed_8
+def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo):
+    """Two polish sweeps on a field at theta ~ 1e-10 agree with the FP64 oracle to 1e-12
+    per link entry (FP32 angles cost ~|g - 1| 2^-24; pair arithmetic ~2^-48)."""
+    U = near_fixed_8[GAUGES[gauge]]
     kw = dict(gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=80)
-    p = lgt.lgt_params_default(dims=U.shape[:4], bulk=lgt.LGT_FP32_12, polish=lgt.LGT_POLISH_MIXED, **kw)
-    ctx = lgt.lgt_create(p, U)
+    ctx = promoted_ctx(lgt, U, **kw)
     try:
-        lgt.lgt_promote(ctx)  # G = 1: the FP64 field is the input, exactly
-        assert np.array_equal(lgt.lgt_get_links(ctx, U.shape[:4]), U)
         lgt.lgt_sweep(ctx, 2)
         got = lgt.lgt_get_links(ctx, U.shape[:4])
     finally:
@@ -327,27 +348,34 @@ def test_mixed_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo):
     assert np.abs(got - ref).max() < 1e-12
 
 
-def test_mixed_polish_on_rough_field_is_fp32_accurate(lgt):
+@pytest.mark.parametrize("gauge", list(GAUGES))
+def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
+    """Even far from convergence (FP32-accurate angles) every pair update is a gauge
+    transformation to ~2^-48: plaquettes and unitarity hold to 1e-13 after 20 sweeps."""
     U = synth.field(DIMS_RAGGED, 0.5, 14)
-    p = lgt.lgt_params_default(dims=DIMS_RAGGED, bulk=lgt.LGT_FP32_18, omega=1.7)
-    ctx = lgt.lgt_create(p, U)
+    ctx = promoted_ctx(lgt, U, gauge=GAUGES[gauge], omega=1.7)
     try:
-        lgt.lgt_promote(ctx)
         lgt.lgt_half_sweep(ctx, 0)
-        got = lgt.lgt_get_links(ctx, DIMS_RAGGED)
+        half = lgt.lgt_get_links(ctx, DIMS_RAGGED)
+        lgt.lgt_half_sweep(ctx, 1)
+        lgt.lgt_sweep(ctx, 19)
+        V = lgt.lgt_get_links(ctx, DIMS_RAGGED)
     finally:
         lgt.lgt_destroy(ctx)
     ref = U.copy()
-    O.half_sweep(ref, 0, omega=1.7)
-    assert np.abs(got - ref).max() < 5e-6
+    O.half_sweep(ref, 0, gauge=GAUGES[gauge], omega=1.7)
+    assert np.abs(half - ref).max() < 5e-6
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-13
+    e, d = unitarity_error(V)
+    assert e < 1e-13 and d < 1e-13
 
 
-@pytest.mark.parametrize("polish", ["mixed", "fp64"])
+@pytest.mark.parametrize("polish", ["pair", "fp64"])
 def test_fix_with_each_polish_kernel(lgt, polish):
     dims = (4, 8, 8, 8)
     U = synth.field(dims, 0.5, 15)
-    pk = lgt.LGT_POLISH_MIXED if polish == "mixed" else lgt.LGT_POLISH_FP64
-    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, polish=pk, theta_switch=1e-9, max_sweeps=4000)
+    pk = lgt.LGT_POLISH_PAIR if polish == "pair" else lgt.LGT_POLISH_FP64
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, polish=pk, theta_switch=1e-8, max_sweeps=4000)
     ctx = lgt.lgt_create(p, U)
     try:
         st, res = lgt.lgt_fix(ctx)
