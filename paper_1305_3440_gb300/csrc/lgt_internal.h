@@ -45,6 +45,54 @@ struct Workspace {
 size_t workspace_bytes(const Geom &g, int min_block);
 void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w);
 
+// Arguments of one lattice's half-sweep (also one row of a batched launch).
+struct SweepArgs {
+  Geom g;
+  void *links;
+  void *G;
+  const uint8_t *active;
+  double *partial;    // [nt][gridDim.x][2]
+  unsigned *counter;  // [nt]
+  double *fused;      // [2][nt][2]
+  double omega;
+  unsigned long long sr_thr;
+  unsigned long long seed;
+  unsigned long long sweep;
+  int transform_temporal;
+  int reunit;
+  // batched launches only: reunitarise when (count_base + s + 1) % reunit_every == 0
+  int reunit_every;
+  long long count_base;
+};
+
+// Arguments of one lattice's exact measurement.
+struct MeasArgs {
+  Geom g;
+  const void *links;
+  double *partial;      // [nt][2][gridDim.x][MEAS_NV]
+  unsigned *counter;    // [nt]
+  unsigned *glob;       // [1]
+  double *slice_sum;    // [nt][MEAS_NV]
+  double *slice_F;      // [nt]
+  double *slice_theta;  // [nt]
+  double *totals;       // [TOT_N]
+  uint8_t *active;      // [nt]
+  double coulomb_target;
+  int with_plaq;
+};
+
+// One row of a batched launch: a lattice's arguments and its block range.
+struct BatchSweep {
+  SweepArgs a;
+  int block_begin;  // first block of this lattice in the batched grid
+  int nbx;          // blocks per timeslice
+};
+struct BatchMeas {
+  MeasArgs a;
+  int block_begin;
+  int nbx;
+};
+
 struct SweepCfg {
   int gauge;                 // GAUGE_*
   int algo;                  // ALGO_*
@@ -85,5 +133,19 @@ cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, voi
 // In-place conversion of an FP64 field to FP32-pair storage (to_pair = 1)
 // or back (to_pair = 0).
 cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_t st);
+
+// Batched half-sweep over n lattices of one kernel variant (fmt, gauge,
+// algo): blocks [jobs[k].block_begin, jobs[k+1].block_begin) belong to
+// lattice k; total_blocks in all.  s: sweep offset within the batch (SR
+// counter and reunitarisation schedule: jobs[k].a.sweep + s, count_base + s).
+cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSweep *jobs, int n, int total_blocks,
+                                    int parity, int s, int block, cudaStream_t st);
+// Batched exact measurement over n lattices of one storage format.
+cudaError_t launch_measure_batch(int fmt, const BatchMeas *jobs, int n, int total_blocks, int block, cudaStream_t st);
+// Fill the batch row of a lattice (pointers into its workspace).
+void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                     unsigned long long sweep, int reunit, int use_mask);
+void fill_meas_args(MeasArgs *a, const Geom &g, const void *links, const Workspace &w, int with_plaq,
+                    double coulomb_target);
 
 }  // namespace lgt

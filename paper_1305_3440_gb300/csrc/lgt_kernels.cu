@@ -70,24 +70,7 @@ void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
 }
 
 // ----------------------------------------------------------------- sweeps
-struct SweepArgs {
-  Geom g;
-  void *links;
-  void *G;
-  const uint8_t *active;
-  double *partial;    // [nt][gridDim.x][2]
-  unsigned *counter;  // [nt]
-  double *fused;      // [2][nt][2]
-  double omega;
-  unsigned long long sr_thr;
-  unsigned long long seed;
-  unsigned long long sweep;
-  int transform_temporal;
-  int reunit;
-  // batched launches only: reunitarise when (count_base + s + 1) % reunit_every == 0
-  int reunit_every;
-  long long count_base;
-};
+
 
 // Fixed-order per-slice sum of the block partials by the slice's last block.
 // bx: this block's index within timeslice t, nbx: blocks per timeslice.
@@ -349,45 +332,39 @@ static sweep_fn pick_sweep(int fmt, int gauge, int algo) {
   return nullptr;
 }
 
+void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                     unsigned long long sweep, int reunit, int use_mask) {
+  a->g = g;
+  a->links = links;
+  a->G = G;
+  a->active = use_mask ? w.active : nullptr;
+  a->partial = w.sweep_partial;
+  a->counter = w.sweep_counter;
+  a->fused = w.fused;
+  a->omega = c.omega;
+  a->sr_thr = c.sr_thr;
+  a->seed = c.seed;
+  a->sweep = sweep;
+  a->transform_temporal = c.transform_temporal;
+  a->reunit = reunit;
+  a->reunit_every = 0;
+  a->count_base = 0;
+}
+
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int block,
                               cudaStream_t st) {
   sweep_fn fn = pick_sweep(fmt, c.gauge, c.algo);
   if (!fn) return cudaErrorInvalidValue;
   SweepArgs a;
-  a.g = g;
-  a.links = links;
-  a.G = G;
-  a.active = use_mask ? w.active : nullptr;
-  a.partial = w.sweep_partial;
-  a.counter = w.sweep_counter;
-  a.fused = w.fused;
-  a.omega = c.omega;
-  a.sr_thr = c.sr_thr;
-  a.seed = c.seed;
-  a.sweep = sweep;
-  a.transform_temporal = c.transform_temporal;
-  a.reunit = reunit;
+  fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   dim3 grid(ceil_div(g.vs_half, block), g.nt);
   fn<<<grid, block, 0, st>>>(a, parity & 1);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ measurement
-struct MeasArgs {
-  Geom g;
-  const void *links;
-  double *partial;      // [nt][2][gridDim.x][MEAS_NV]
-  unsigned *counter;    // [nt]
-  unsigned *glob;       // [1]
-  double *slice_sum;    // [nt][MEAS_NV]
-  double *slice_F;      // [nt]
-  double *slice_theta;  // [nt]
-  double *totals;       // [TOT_N]
-  uint8_t *active;      // [nt]
-  double coulomb_target;
-  int with_plaq;
-};
+
 
 template <int FMT>
 struct LoadD {
@@ -558,21 +535,26 @@ __global__ void __launch_bounds__(256) k_measure(MeasArgs a) {
   measure_body<FMT>(a, blockIdx.y, blockIdx.z, blockIdx.x, gridDim.x);
 }
 
+void fill_meas_args(MeasArgs *a, const Geom &g, const void *links, const Workspace &w, int with_plaq,
+                    double coulomb_target) {
+  a->g = g;
+  a->links = links;
+  a->partial = w.meas_partial;
+  a->counter = w.meas_counter;
+  a->glob = w.glob_counter;
+  a->slice_sum = w.slice_sum;
+  a->slice_F = w.slice_F;
+  a->slice_theta = w.slice_theta;
+  a->totals = w.totals;
+  a->active = w.active;
+  a->coulomb_target = coulomb_target;
+  a->with_plaq = with_plaq;
+}
+
 cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
                            double coulomb_target, int block, cudaStream_t st) {
   MeasArgs a;
-  a.g = g;
-  a.links = links;
-  a.partial = w.meas_partial;
-  a.counter = w.meas_counter;
-  a.glob = w.glob_counter;
-  a.slice_sum = w.slice_sum;
-  a.slice_F = w.slice_F;
-  a.slice_theta = w.slice_theta;
-  a.totals = w.totals;
-  a.active = w.active;
-  a.coulomb_target = coulomb_target;
-  a.with_plaq = with_plaq;
+  fill_meas_args(&a, g, links, w, with_plaq, coulomb_target);
   dim3 grid(ceil_div(g.vs_half, block), g.nt, 2);
   if (fmt == FMT_F64) k_measure<FMT_F64><<<grid, block, 0, st>>>(a);
   else if (fmt == FMT_F32_18) k_measure<FMT_F32_18><<<grid, block, 0, st>>>(a);
@@ -769,6 +751,83 @@ cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_
   const unsigned grid = (unsigned)((n + blk - 1) / blk);
   if (to_pair) k_f64_to_pair<<<grid, blk, 0, st>>>(reinterpret_cast<double2 *>(u), n);
   else k_pair_to_f64<<<grid, blk, 0, st>>>(reinterpret_cast<double2 *>(u), n);
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------- batched launches
+// Block b of a batched grid belongs to the last row k with
+// jobs[k].block_begin <= b (rows sorted by block_begin).
+__device__ __forceinline__ int batch_row(const int *begins, int stride_bytes, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int beg = *reinterpret_cast<const int *>(reinterpret_cast<const char *>(begins) + (size_t)mid * stride_bytes);
+    if (beg <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int FMT, int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_dispatch(const SweepArgs &a, int p, int t, int bx, int nbx) {
+  if (FMT == FMT_F64) sweep_body_f64<GAUGE, ALGO>(a, p, t, bx, nbx);
+  else if (FMT == FMT_PAIR) sweep_body_pair<GAUGE, ALGO>(a, p, t, bx, nbx);
+  else sweep_body_f32<(FMT == FMT_F32_12 ? FMT_F32_12 : FMT_F32_18), GAUGE, ALGO>(a, p, t, bx, nbx);
+}
+
+template <int FMT, int GAUGE, int ALGO>
+__global__ void __launch_bounds__(256) k_sweep_batch(const BatchSweep *jobs, int n, int p, int s) {
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, blockIdx.x);
+  const BatchSweep &J = jobs[k];
+  SweepArgs a = J.a;
+  a.sweep += (unsigned long long)s;
+  a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
+  const int local = blockIdx.x - J.block_begin;
+  const int t = local / J.nbx;
+  sweep_dispatch<FMT, GAUGE, ALGO>(a, p, t, local - t * J.nbx, J.nbx);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_measure_batch(const BatchMeas *jobs, int n) {
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchMeas), n, blockIdx.x);
+  const BatchMeas &J = jobs[k];
+  const int local = blockIdx.x - J.block_begin;
+  const int per_t = 2 * J.nbx;
+  const int t = local / per_t;
+  const int rem = local - t * per_t;
+  const int p = rem / J.nbx;
+  measure_body<FMT>(J.a, t, p, rem - p * J.nbx, J.nbx);
+}
+
+typedef void (*batch_fn)(const BatchSweep *, int, int, int);
+
+template <int FMT>
+static batch_fn pick_batch_fmt(int gauge, int algo) {
+  if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_batch<FMT, GAUGE_LANDAU, ALGO_SR> : k_sweep_batch<FMT, GAUGE_LANDAU, ALGO_OR>;
+  return algo == ALGO_SR ? k_sweep_batch<FMT, GAUGE_COULOMB, ALGO_SR> : k_sweep_batch<FMT, GAUGE_COULOMB, ALGO_OR>;
+}
+
+cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSweep *jobs, int n, int total_blocks,
+                                    int parity, int s, int block, cudaStream_t st) {
+  if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+  batch_fn fn = nullptr;
+  if (fmt == FMT_F64) fn = pick_batch_fmt<FMT_F64>(gauge, algo);
+  else if (fmt == FMT_F32_18) fn = pick_batch_fmt<FMT_F32_18>(gauge, algo);
+  else if (fmt == FMT_F32_12) fn = pick_batch_fmt<FMT_F32_12>(gauge, algo);
+  else if (fmt == FMT_PAIR) fn = pick_batch_fmt<FMT_PAIR>(gauge, algo);
+  if (!fn) return cudaErrorInvalidValue;
+  fn<<<total_blocks, block, 0, st>>>(jobs, n, parity & 1, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure_batch(int fmt, const BatchMeas *jobs, int n, int total_blocks, int block, cudaStream_t st) {
+  if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+  if (fmt == FMT_F64) k_measure_batch<FMT_F64><<<total_blocks, block, 0, st>>>(jobs, n);
+  else if (fmt == FMT_F32_18) k_measure_batch<FMT_F32_18><<<total_blocks, block, 0, st>>>(jobs, n);
+  else if (fmt == FMT_F32_12) k_measure_batch<FMT_F32_12><<<total_blocks, block, 0, st>>>(jobs, n);
+  else if (fmt == FMT_PAIR) k_measure_batch<FMT_PAIR><<<total_blocks, block, 0, st>>>(jobs, n);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -13,11 +13,11 @@
 //   * the rotation angles (which SU(2) element to apply) are chosen in FP32
 //     from the pair-precision K(x); a slightly suboptimal angle is still a
 //     gauge transformation and only costs optimality;
-//   * every SU(2) element is formed as R = 1 + rho with rho from
-//     (e0 = r0 - 1, r1, r2, r3) in FP32.  e0 is second order in |r| and is
-//     computed without cancellation, so R is unitary to ~2^-24 |r|^2, and R is
-//     applied to the links in pair arithmetic.  The field therefore stays an
-//     exact (to ~2^-48) gauge transform of its input.
+//   * every SU(2) element takes its angles r1, r2, r3 as exact FP32 numbers
+//     and r0 = +-sqrt(1 - |r|^2) in pair precision, so it is unitary to ~2^-48
+//     at any rotation size, and it is applied to the links as R = 1 + rho in
+//     pair arithmetic.  The field therefore stays an exact (to ~2^-48) gauge
+//     transform of its input.
 #pragma once
 
 #include "lgt_device.cuh"
@@ -53,12 +53,28 @@ __device__ __forceinline__ f2 pair_neg(f2 a) { return {-a.hi, -a.lo}; }
 
 __device__ __forceinline__ float pair_to_float(f2 a) { return __fadd_rn(a.hi, a.lo); }
 
-// sum_k c[k] * x[k] for float coefficients and pair values: exact products of
-// the high parts (TwoProd via fma), low parts folded in with one rounding each
-__device__ __forceinline__ f2 pair_dot4(float c0, f2 x0, float c1, f2 x1, float c2, f2 x2, float c3, f2 x3) {
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// sqrt of a pair in [0, 1]: one Newton step on the FP32 root
+__device__ __forceinline__ f2 pair_sqrt(f2 w) {
+  if (!(w.hi > 0.0f)) return {0.0f, 0.0f};
+  const float s0 = __fsqrt_rn(w.hi);
+  const f2 sq = two_prod(s0, s0);
+  const f2 res = pair_add(w, pair_neg(sq));
+  return quick_two_sum(s0, __fdiv_rn(pair_to_float(res), __fmul_rn(2.0f, s0)));
+}
+
+// sum_k c[k] * x[k] + extra for float coefficients and pair values: exact
+// products of the high parts (TwoProd via fma), low parts and the small extra
+// term folded in with one rounding each
+__device__ __forceinline__ f2 pair_dot4(float c0, f2 x0, float c1, f2 x1, float c2, f2 x2, float c3, f2 x3,
+                                        float extra) {
   const float p0 = __fmul_rn(c0, x0.hi), p1 = __fmul_rn(c1, x1.hi);
   const float p2 = __fmul_rn(c2, x2.hi), p3 = __fmul_rn(c3, x3.hi);
-  float e = __fmaf_rn(c0, x0.hi, -p0);
+  float e = __fadd_rn(extra, __fmaf_rn(c0, x0.hi, -p0));
   e = __fadd_rn(e, __fmaf_rn(c1, x1.hi, -p1));
   e = __fadd_rn(e, __fmaf_rn(c2, x2.hi, -p2));
   e = __fadd_rn(e, __fmaf_rn(c3, x3.hi, -p3));
@@ -93,19 +109,39 @@ struct LinkIO<FMT_PAIR> {
   }
 };
 
-// One subgroup element as the FP32 quadruple (e0 = r0 - 1, r1, r2, r3).
+// One subgroup element (r0, r1, r2, r3), r0 = 1 + e0.  The angles r1..r3 are
+// FP32 numbers taken as exact; e0 is the pair-precision value of
+// +-sqrt(1 - |r|^2) - 1, so the element is unitary to ~2^-48 at any size.
 struct Rot {
+  f2 e0;
+  float r1, r2, r3;
+};
+
+// FP32 choice of the element, before its pair-precision r0
+struct RotF {
   float e0, r1, r2, r3;
 };
+
+__device__ __forceinline__ Rot exact_rotation(const RotF &f) {
+  const f2 v = pair_add(pair_add(two_prod(f.r1, f.r1), two_prod(f.r2, f.r2)), two_prod(f.r3, f.r3));
+  f2 r0 = pair_sqrt(pair_add(f2{1.0f, 0.0f}, pair_neg(v)));
+  if (1.0f + f.e0 < 0.0f) r0 = pair_neg(r0);
+  Rot r;
+  r.e0 = pair_add(r0, f2{-1.0f, 0.0f});
+  r.r1 = f.r1;
+  r.r2 = f.r2;
+  r.r3 = f.r3;
+  return r;
+}
 
 // Sec. 3 closed-form SU(2) maximum of the projection (q0, q) (any positive
 // scale), then Sec. 3.1 first-order overrelaxation or Sec. 3.2 squaring, all
 // in the near-identity form r = (1 + e0, r_vec).
 template <int ALGO>
-__device__ __forceinline__ Rot subgroup_rotation(float q0, float q1, float q2, float q3, float omega, bool square) {
+__device__ __forceinline__ RotF subgroup_rotation(float q0, float q1, float q2, float q3, float omega, bool square) {
   const float v2 = q1 * q1 + q2 * q2 + q3 * q3;
   const float n2 = q0 * q0 + v2;
-  Rot r = {0.0f, 0.0f, 0.0f, 0.0f};
+  RotF r = {0.0f, 0.0f, 0.0f, 0.0f};
   if (n2 > 0.0f) {
     const float inv = rsqrtf(n2);
     const float n = n2 * inv;
@@ -145,12 +181,13 @@ __device__ __forceinline__ void rotate_rows(f2 m[18], const Rot &r) {
   for (int c = 0; c < 3; c++) {
     const f2 xi = m[LGT_RE(I, c)], yi = m[LGT_IM(I, c)];
     const f2 xj = m[LGT_RE(J, c)], yj = m[LGT_IM(J, c)];
+    const float e = r.e0.hi, el = r.e0.lo;
     // (e0 + i r3) (xi + i yi) + (r2 + i r1) (xj + i yj)
-    m[LGT_RE(I, c)] = pair_add(xi, pair_dot4(r.e0, xi, -r.r3, yi, r.r2, xj, -r.r1, yj));
-    m[LGT_IM(I, c)] = pair_add(yi, pair_dot4(r.e0, yi, r.r3, xi, r.r2, yj, r.r1, xj));
+    m[LGT_RE(I, c)] = pair_add(xi, pair_dot4(e, xi, -r.r3, yi, r.r2, xj, -r.r1, yj, el * xi.hi));
+    m[LGT_IM(I, c)] = pair_add(yi, pair_dot4(e, yi, r.r3, xi, r.r2, yj, r.r1, xj, el * yi.hi));
     // (-r2 + i r1) (xi + i yi) + (e0 - i r3) (xj + i yj)
-    m[LGT_RE(J, c)] = pair_add(xj, pair_dot4(-r.r2, xi, -r.r1, yi, r.e0, xj, r.r3, yj));
-    m[LGT_IM(J, c)] = pair_add(yj, pair_dot4(-r.r2, yi, r.r1, xi, r.e0, yj, -r.r3, xj));
+    m[LGT_RE(J, c)] = pair_add(xj, pair_dot4(-r.r2, xi, -r.r1, yi, e, xj, r.r3, yj, el * xj.hi));
+    m[LGT_IM(J, c)] = pair_add(yj, pair_dot4(-r.r2, yi, r.r1, xi, e, yj, -r.r3, xj, el * yj.hi));
   }
 }
 
@@ -161,19 +198,20 @@ __device__ __forceinline__ void rotate_cols_dag(f2 m[18], const Rot &r) {
   for (int a = 0; a < 3; a++) {
     const f2 xi = m[LGT_RE(a, I)], yi = m[LGT_IM(a, I)];
     const f2 xj = m[LGT_RE(a, J)], yj = m[LGT_IM(a, J)];
+    const float e = r.e0.hi, el = r.e0.lo;
     // m_ai conj(r0 + i r3) + m_aj conj(r2 + i r1) = m_ai (e0 - i r3) + m_aj (r2 - i r1) (+ m_ai)
-    m[LGT_RE(a, I)] = pair_add(xi, pair_dot4(r.e0, xi, r.r3, yi, r.r2, xj, r.r1, yj));
-    m[LGT_IM(a, I)] = pair_add(yi, pair_dot4(r.e0, yi, -r.r3, xi, r.r2, yj, -r.r1, xj));
+    m[LGT_RE(a, I)] = pair_add(xi, pair_dot4(e, xi, r.r3, yi, r.r2, xj, r.r1, yj, el * xi.hi));
+    m[LGT_IM(a, I)] = pair_add(yi, pair_dot4(e, yi, -r.r3, xi, r.r2, yj, -r.r1, xj, el * yi.hi));
     // m_ai conj(-r2 + i r1) + m_aj conj(r0 - i r3) = m_ai (-r2 - i r1) + m_aj (e0 + i r3) (+ m_aj)
-    m[LGT_RE(a, J)] = pair_add(xj, pair_dot4(-r.r2, xi, r.r1, yi, r.e0, xj, -r.r3, yj));
-    m[LGT_IM(a, J)] = pair_add(yj, pair_dot4(-r.r2, yi, -r.r1, xi, r.e0, yj, r.r3, xj));
+    m[LGT_RE(a, J)] = pair_add(xj, pair_dot4(-r.r2, xi, r.r1, yi, e, xj, -r.r3, yj, el * xj.hi));
+    m[LGT_IM(a, J)] = pair_add(yj, pair_dot4(-r.r2, yi, -r.r1, xi, e, yj, r.r3, xj, el * yj.hi));
   }
 }
 
 // W <- W + rho W on rows (i, j) with the increment in FP32 (it only steers the
 // next subgroup's choice; the applied rotations are exact regardless)
 template <int I, int J>
-__device__ __forceinline__ void steer_rows(f2 W[18], const Rot &r) {
+__device__ __forceinline__ void steer_rows(f2 W[18], const RotF &r) {
 #pragma unroll
   for (int c = 0; c < 3; c++) {
     const float xi = W[LGT_RE(I, c)].hi, yi = W[LGT_IM(I, c)].hi;
@@ -199,9 +237,10 @@ __device__ __forceinline__ void pair_local_update(f2 W[18], Rot rot[3], float om
     const float q2 = pair_to_float(pair_add(W[LGT_RE(i, j)], pair_neg(W[LGT_RE(j, i)])));
     const float q3 = pair_to_float(pair_add(W[LGT_IM(i, i)], pair_neg(W[LGT_IM(j, j)])));
     const uint32_t d = s == 0 ? draws.x : (s == 1 ? draws.y : draws.z);
-    rot[s] = subgroup_rotation<ALGO>(q0, q1, q2, q3, omega, (uint64_t)d < sr_thr);
-    if (s == 0) steer_rows<0, 1>(W, rot[0]);
-    if (s == 1) steer_rows<0, 2>(W, rot[1]);
+    const RotF rf = subgroup_rotation<ALGO>(q0, q1, q2, q3, omega, (uint64_t)d < sr_thr);
+    rot[s] = exact_rotation(rf);
+    if (s == 0) steer_rows<0, 1>(W, rf);
+    if (s == 1) steer_rows<0, 2>(W, rf);
   }
 }
 

@@ -1,30 +1,634 @@
-// lgt_server.cu -- continuous-batching job server (see include/lgt.h).
+// lgt_server.cu -- continuous-batching gauge-fixing server (include/lgt.h).
+//
+// One worker thread owns a CUDA stream and a device memory pool.  Each tick:
+//   1. admit queued jobs (FIFO) while their device footprint fits the HBM
+//      budget: allocate, upload, ingest (SU(3) check), measure;
+//   2. advance every live job by up to check_every sweeps: for each sweep and
+//      parity, one batched half-sweep launch per kernel variant (storage
+//      format x gauge x algorithm) covers the sites of all live jobs of that
+//      variant;
+//   3. one batched exact measurement per storage format gives each job's F and
+//      theta (one device->host copy for all jobs);
+//   4. per job, the same ladder decisions as lgt_fix (Sec. 4 driver): bulk FP32
+//      until theta < theta_switch (or the FP32 floor), promotion, polishing to
+//      theta < theta_tol, or max_sweeps; finished jobs are measured once more,
+//      copied out and their memory released, which admits the next ones.
+// A job's sequence of kernels and decisions depends only on its own
+// parameters, so its result is bit-identical alone and in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "lgt_api_internal.h"
+#include "lgt_internal.h"
+
+using namespace lgt;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum { JOB_QUEUED = 0, JOB_RUNNING = 1, JOB_DONE = 2 };
+
+constexpr int kServerBlock = 128;
+constexpr int kMaxSlots = 4096;
+
+int fmt_of_prec(int32_t prec) {
+  return prec == LGT_FP32_18 ? FMT_F32_18 : (prec == LGT_FP32_12 ? FMT_F32_12 : FMT_F64);
+}
+
+unsigned long long sr_thr_of(double p) {
+  if (!(p > 0.0)) return 0ull;
+  if (p >= 1.0) return 1ull << 32;
+  return (unsigned long long)floor(p * 4294967296.0);
+}
+
+struct Job {
+  uint64_t id = 0;
+  lgt_params prm;
+  std::vector<double> input, output;
+  lgt_result res;
+  int state = JOB_QUEUED;
+  bool cancel = false;
+  Clock::time_point t_submit, t_start, t_end;
+  size_t bytes = 0;
+  int slot = -1;
+  // device state
+  Geom g;
+  void *u64 = nullptr, *u32 = nullptr, *G = nullptr, *ws_base = nullptr;
+  Workspace ws;
+  int phase = 0, bulk_fmt = FMT_F64;
+  SweepCfg cfg;
+  int64_t sweeps_bulk = 0, sweeps_fp64 = 0, remaining = 0;
+  uint64_t sweep_index = 0;
+  double best = 0.0;
+  int stall = 0;
+  bool measure_only = true;  // next tick measures without sweeping
+  int nthis = 0;             // sweeps in the current tick
+  int nbx = 0;
+
+  int work_fmt() const { return phase == 0 ? bulk_fmt : (phase == 2 ? (int)FMT_PAIR : (int)FMT_F64); }
+  void *work_links() const { return phase == 0 ? u32 : u64; }
+  double theta_of(const double *tot) const {
+    return prm.gauge == LGT_COULOMB ? tot[TOT_THETA_COULOMB_MAX] : tot[TOT_THETA_LANDAU];
+  }
+  double F_of(const double *tot) const {
+    return prm.gauge == LGT_COULOMB ? tot[TOT_F_COULOMB] : tot[TOT_F_LANDAU];
+  }
+};
+
+size_t aos_bytes_of(const Geom &g) { return (size_t)g.vh * 2 * 4 * 18 * sizeof(double); }
+
+}  // namespace
+
+struct lgt_server {
+  size_t budget = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Job *> queue;
+  std::map<uint64_t, Job *> jobs;
+  uint64_t next_id = 1, done = 0;
+  size_t used = 0;
+  bool stop = false;
+  std::thread worker;
+  // worker-owned
+  std::vector<Job *> live;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  double *d_totals = nullptr, *h_totals = nullptr;
+  std::vector<int> free_slots;
+  BatchSweep *d_sweep = nullptr, *h_sweep = nullptr;
+  BatchMeas *d_meas = nullptr, *h_meas = nullptr;
+  size_t sweep_cap = 0, meas_cap = 0;
+  cudaError_t fatal = cudaSuccess;
+};
+
+namespace {
+
+cudaError_t dev_alloc(lgt_server *s, void **p, size_t n) { return cudaMallocFromPoolAsync(p, n, s->pool, s->stream); }
+
+void release_job_device(lgt_server *s, Job *j) {
+  void **ptrs[] = {&j->u64, &j->u32, &j->G, &j->ws_base};
+  for (void **p : ptrs)
+    if (*p) {
+      cudaFreeAsync(*p, s->stream);
+      *p = nullptr;
+    }
+  if (j->slot >= 0) {
+    s->free_slots.push_back(j->slot);
+    j->slot = -1;
+  }
+}
+
+// under s->mu
+void finish_locked(lgt_server *s, Job *j, int status) {
+  j->state = JOB_DONE;
+  j->t_end = Clock::now();
+  j->res.status = status;
+  j->res.seconds = std::chrono::duration<double>(j->t_end - j->t_submit).count();
+  j->res.sweeps_bulk = j->sweeps_bulk;
+  j->res.sweeps_fp64 = j->sweeps_fp64;
+  s->used -= j->bytes;
+  j->bytes = 0;
+  s->done++;
+  s->cv.notify_all();
+}
+
+// allocate, upload and ingest one job (worker thread; j->slot already taken)
+cudaError_t admit(lgt_server *s, Job *j, int *bad_input) {
+  const lgt_params &p = j->prm;
+  j->g = lgt_make_geom(p.dims);
+  const Geom &g = j->g;
+  j->bulk_fmt = fmt_of_prec(p.bulk);
+  j->phase = p.bulk == LGT_FP64 ? 1 : 0;
+  j->cfg.gauge = p.gauge == LGT_COULOMB ? GAUGE_COULOMB : GAUGE_LANDAU;
+  j->cfg.algo = p.algo == LGT_SR ? ALGO_SR : ALGO_OR;
+  j->cfg.omega = p.omega;
+  j->cfg.sr_thr = sr_thr_of(p.p);
+  j->cfg.seed = p.seed;
+  j->cfg.transform_temporal = p.transform_temporal ? 1 : 0;
+  j->sweep_index = p.sweep_offset;
+  j->remaining = p.max_sweeps;
+  j->nbx = (g.vs_half + kServerBlock - 1) / kServerBlock;
+  cudaError_t e;
+  if ((e = dev_alloc(s, &j->u64, field_bytes(FMT_F64, g.vh))) != cudaSuccess) return e;
+  if (p.bulk != LGT_FP64) {
+    if ((e = dev_alloc(s, &j->u32, field_bytes(j->bulk_fmt, g.vh))) != cudaSuccess) return e;
+    if ((e = dev_alloc(s, &j->G, g_bytes(g.vh))) != cudaSuccess) return e;
+  }
+  const size_t wsb = workspace_bytes(g, 64);
+  if ((e = dev_alloc(s, &j->ws_base, wsb)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(j->ws_base, 0, wsb, s->stream)) != cudaSuccess) return e;
+  workspace_carve(j->ws_base, g, 64, &j->ws);
+  j->ws.totals = s->d_totals + (size_t)j->slot * TOT_N;
+  if ((e = cudaMemsetAsync(j->ws.active, 1, (size_t)g.nt, s->stream)) != cudaSuccess) return e;
+  void *stage = nullptr;
+  if ((e = dev_alloc(s, &stage, aos_bytes_of(g))) != cudaSuccess) return e;
+  e = cudaMemcpyAsync(stage, j->input.data(), aos_bytes_of(g), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = launch_ingest(FMT_F64, g, (const double *)stage, j->u64, j->ws.err, s->stream);
+  if (e == cudaSuccess && j->u32) e = launch_ingest(j->bulk_fmt, g, (const double *)stage, j->u32, j->ws.err, s->stream);
+  if (e == cudaSuccess && j->G) e = launch_g_identity(g, j->G, s->stream);
+  int err_h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err_h, j->ws.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(stage, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  std::vector<double>().swap(j->input);
+  *bad_input = err_h != 0;
+  return e;
+}
+
+double coulomb_target(const Job *j) {
+  if (j->prm.gauge != LGT_COULOMB) return -1.0;
+  return j->phase == 0 ? j->prm.theta_switch : j->prm.theta_tol;
+}
+
+struct Segment {
+  int fmt, gauge, algo, s;
+  size_t offset;
+  int n, blocks;
+};
+
+cudaError_t ensure_tables(lgt_server *s, size_t nsweep, size_t nmeas) {
+  cudaError_t e = cudaSuccess;
+  if (nsweep > s->sweep_cap) {
+    size_t cap = std::max(nsweep, 2 * s->sweep_cap);
+    if (s->d_sweep) cudaFree(s->d_sweep);
+    if (s->h_sweep) cudaFreeHost(s->h_sweep);
+    s->d_sweep = nullptr;
+    s->h_sweep = nullptr;
+    if ((e = cudaMalloc(&s->d_sweep, cap * sizeof(BatchSweep))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&s->h_sweep, cap * sizeof(BatchSweep))) != cudaSuccess) return e;
+    s->sweep_cap = cap;
+  }
+  if (nmeas > s->meas_cap) {
+    size_t cap = std::max(nmeas, 2 * s->meas_cap);
+    if (s->d_meas) cudaFree(s->d_meas);
+    if (s->h_meas) cudaFreeHost(s->h_meas);
+    s->d_meas = nullptr;
+    s->h_meas = nullptr;
+    if ((e = cudaMalloc(&s->d_meas, cap * sizeof(BatchMeas))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&s->h_meas, cap * sizeof(BatchMeas))) != cudaSuccess) return e;
+    s->meas_cap = cap;
+  }
+  return e;
+}
+
+// One tick over the live jobs: sweeps, measurement, read back.
+cudaError_t tick(lgt_server *s) {
+  std::vector<Job *> &live = s->live;
+  int kmax = 0;
+  for (Job *j : live) {
+    j->nthis = j->measure_only ? 0 : (int)std::min<int64_t>(j->prm.check_every, j->remaining);
+    kmax = std::max(kmax, j->nthis);
+  }
+  // sweep segments: for each sweep offset s, jobs grouped by kernel variant
+  std::vector<Segment> segs;
+  std::vector<BatchSweep> rows;
+  std::vector<Job *> order(live);
+  std::stable_sort(order.begin(), order.end(), [](const Job *a, const Job *b) {
+    const int ka = (a->work_fmt() * 2 + a->cfg.gauge) * 2 + a->cfg.algo;
+    const int kb = (b->work_fmt() * 2 + b->cfg.gauge) * 2 + b->cfg.algo;
+    return ka < kb;
+  });
+  for (int sw = 0; sw < kmax; sw++) {
+    size_t i = 0;
+    while (i < order.size()) {
+      const Job *h = order[i];
+      Segment seg = {h->work_fmt(), h->cfg.gauge, h->cfg.algo, sw, rows.size(), 0, 0};
+      size_t k = i;
+      for (; k < order.size(); k++) {
+        Job *j = order[k];
+        if (j->work_fmt() != seg.fmt || j->cfg.gauge != seg.gauge || j->cfg.algo != seg.algo) break;
+        if (sw >= j->nthis) continue;
+        BatchSweep r;
+        fill_sweep_args(&r.a, j->g, j->work_links(), j->phase == 0 ? j->G : nullptr, j->ws, j->cfg, j->sweep_index,
+                        0, j->prm.gauge == LGT_COULOMB ? 1 : 0);
+        r.a.reunit_every = j->phase == 0 ? j->prm.reunit_every : 0;
+        r.a.count_base = j->sweeps_bulk;
+        r.block_begin = seg.blocks;
+        r.nbx = j->nbx;
+        rows.push_back(r);
+        seg.n++;
+        seg.blocks += j->nbx * j->g.nt;
+      }
+      if (seg.n) segs.push_back(seg);
+      i = k;
+    }
+  }
+  // measurement segments: one per storage format
+  std::vector<Segment> msegs;
+  std::vector<BatchMeas> mrows;
+  std::vector<Job *> morder(live);
+  std::stable_sort(morder.begin(), morder.end(),
+                   [](const Job *a, const Job *b) { return a->work_fmt() < b->work_fmt(); });
+  for (size_t i = 0; i < morder.size();) {
+    Segment seg = {morder[i]->work_fmt(), 0, 0, 0, mrows.size(), 0, 0};
+    size_t k = i;
+    for (; k < morder.size() && morder[k]->work_fmt() == seg.fmt; k++) {
+      Job *j = morder[k];
+      BatchMeas r;
+      fill_meas_args(&r.a, j->g, j->work_links(), j->ws, 0, coulomb_target(j));
+      r.block_begin = seg.blocks;
+      r.nbx = j->nbx;
+      mrows.push_back(r);
+      seg.n++;
+      seg.blocks += 2 * j->nbx * j->g.nt;
+    }
+    msegs.push_back(seg);
+    i = k;
+  }
+  cudaError_t e = ensure_tables(s, rows.size(), mrows.size());
+  if (e != cudaSuccess) return e;
+  if (!rows.empty()) {
+    memcpy(s->h_sweep, rows.data(), rows.size() * sizeof(BatchSweep));
+    if ((e = cudaMemcpyAsync(s->d_sweep, s->h_sweep, rows.size() * sizeof(BatchSweep), cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
+      return e;
+  }
+  memcpy(s->h_meas, mrows.data(), mrows.size() * sizeof(BatchMeas));
+  if ((e = cudaMemcpyAsync(s->d_meas, s->h_meas, mrows.size() * sizeof(BatchMeas), cudaMemcpyHostToDevice,
+                           s->stream)) != cudaSuccess)
+    return e;
+  // sweeps: for each sweep offset, both parities, every variant
+  size_t si = 0;
+  for (int sw = 0; sw < kmax; sw++) {
+    size_t first = si;
+    while (si < segs.size() && segs[si].s == sw) si++;
+    for (int parity = 0; parity < 2; parity++)
+      for (size_t q = first; q < si; q++) {
+        const Segment &g = segs[q];
+        e = launch_half_sweep_batch(g.fmt, g.gauge, g.algo, s->d_sweep + g.offset, g.n, g.blocks, parity, sw,
+                                    kServerBlock, s->stream);
+        if (e != cudaSuccess) return e;
+      }
+  }
+  for (const Segment &g : msegs) {
+    e = launch_measure_batch(g.fmt, s->d_meas + g.offset, g.n, g.blocks, kServerBlock, s->stream);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemcpyAsync(s->h_totals, s->d_totals, sizeof(double) * TOT_N * kMaxSlots, cudaMemcpyDeviceToHost,
+                      s->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s->stream);
+}
+
+// final measurement with plaquette and copy-out of a finished job
+cudaError_t collect(lgt_server *s, Job *j) {
+  cudaError_t e = launch_measure(j->work_fmt(), j->g, j->work_links(), j->ws, 1, -1.0, kServerBlock, s->stream);
+  if (e != cudaSuccess) return e;
+  void *stage = nullptr;
+  if ((e = dev_alloc(s, &stage, aos_bytes_of(j->g))) != cudaSuccess) return e;
+  if (j->phase >= 1) e = launch_egress(j->work_fmt(), j->g, j->u64, (double *)stage, s->stream);
+  else e = launch_apply_G(j->g, j->G, j->u64, nullptr, (double *)stage,
+                          (j->prm.gauge == LGT_COULOMB && !j->prm.transform_temporal) ? 1 : 0, s->stream);
+  j->output.resize(aos_bytes_of(j->g) / sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(j->output.data(), stage, aos_bytes_of(j->g), cudaMemcpyDeviceToHost, s->stream);
+  double tot[TOT_N];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot, j->ws.totals, sizeof tot, cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(stage, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return e;
+  j->res.F = j->F_of(tot);
+  j->res.theta = j->theta_of(tot);
+  j->res.plaquette = tot[TOT_PLAQ];
+  return cudaSuccess;
+}
+
+cudaError_t promote_job(lgt_server *s, Job *j) {
+  const int skip_t = (j->prm.gauge == LGT_COULOMB && !j->prm.transform_temporal) ? 1 : 0;
+  cudaError_t e = launch_apply_G(j->g, j->G, j->u64, j->u64, nullptr, skip_t, s->stream);
+  j->phase = 1;
+  if (e == cudaSuccess && j->prm.polish == LGT_POLISH_PAIR) {
+    e = launch_convert_pair(j->g, j->u64, 1, s->stream);
+    j->phase = 2;
+  }
+  j->measure_only = true;
+  return e;
+}
+
+void worker_main(lgt_server *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // admission (FIFO, by budget)
+    while (!s->stop && s->fatal == cudaSuccess && !s->queue.empty()) {
+      Job *j = s->queue.front();
+      if (j->cancel) {
+        s->queue.pop_front();
+        finish_locked(s, j, LGT_ECANCELLED);
+        continue;
+      }
+      const size_t need = lgt_ctx_device_bytes(&j->prm);
+      const size_t stage = aos_bytes_of(lgt_make_geom(j->prm.dims));
+      if (s->used + need + stage > s->budget || s->free_slots.empty()) break;
+      s->queue.pop_front();
+      j->bytes = need;
+      s->used += need;
+      j->slot = s->free_slots.back();
+      s->free_slots.pop_back();
+      j->state = JOB_RUNNING;
+      j->t_start = Clock::now();
+      int bad = 0;
+      lk.unlock();
+      cudaError_t e = admit(s, j, &bad);
+      lk.lock();
+      if (e != cudaSuccess) {
+        s->fatal = e;
+        release_job_device(s, j);
+        finish_locked(s, j, e == cudaErrorMemoryAllocation ? LGT_ENOMEM : LGT_ECUDA);
+        break;
+      }
+      if (bad) {
+        release_job_device(s, j);
+        finish_locked(s, j, LGT_EINVAL);
+        continue;
+      }
+      s->live.push_back(j);
+    }
+    if (s->stop) break;
+    if (s->live.empty()) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(50));
+      continue;
+    }
+    // cancelled jobs leave at the tick boundary
+    for (size_t i = 0; i < s->live.size();) {
+      Job *j = s->live[i];
+      if (j->cancel) {
+        release_job_device(s, j);
+        finish_locked(s, j, LGT_ECANCELLED);
+        s->live.erase(s->live.begin() + i);
+      } else {
+        i++;
+      }
+    }
+    if (s->live.empty()) continue;
+    lk.unlock();
+    cudaError_t e = tick(s);
+    std::vector<Job *> finished;
+    std::vector<int> fstatus;
+    if (e == cudaSuccess) {
+      for (Job *j : s->live) {
+        const double *tot = s->h_totals + (size_t)j->slot * TOT_N;
+        const double theta = j->theta_of(tot);
+        const bool was_measure_only = j->measure_only;
+        if (!was_measure_only) {
+          if (j->phase == 0) j->sweeps_bulk += j->nthis;
+          else j->sweeps_fp64 += j->nthis;
+          j->remaining -= j->nthis;
+          j->sweep_index += (uint64_t)j->nthis;
+        }
+        j->measure_only = false;
+        if (j->phase == 0) {
+          if (was_measure_only) {
+            j->best = theta;
+            j->stall = 0;
+          } else if (theta < j->best) {
+            j->best = theta;
+            j->stall = 0;
+          } else {
+            j->stall++;
+          }
+          if (theta < j->prm.theta_switch || j->remaining <= 0 || j->stall >= 3) {
+            if ((e = promote_job(s, j)) != cudaSuccess) break;
+          }
+        } else if (theta < j->prm.theta_tol) {
+          finished.push_back(j);
+          fstatus.push_back(LGT_OK);
+        } else if (j->remaining <= 0) {
+          finished.push_back(j);
+          fstatus.push_back(LGT_ENOTCONV);
+        }
+      }
+      for (size_t q = 0; q < finished.size() && e == cudaSuccess; q++) e = collect(s, finished[q]);
+    }
+    lk.lock();
+    if (e != cudaSuccess) {
+      s->fatal = e;
+      lgt_set_error("server worker: %s", cudaGetErrorString(e));
+      for (Job *j : s->live) {
+        release_job_device(s, j);
+        finish_locked(s, j, LGT_ECUDA);
+      }
+      s->live.clear();
+      continue;
+    }
+    for (size_t q = 0; q < finished.size(); q++) {
+      Job *j = finished[q];
+      release_job_device(s, j);
+      finish_locked(s, j, fstatus[q]);
+      s->live.erase(std::find(s->live.begin(), s->live.end(), j));
+    }
+  }
+  // shutdown: queued and live jobs are cancelled
+  for (Job *j : s->live) {
+    release_job_device(s, j);
+    finish_locked(s, j, LGT_ECANCELLED);
+  }
+  s->live.clear();
+  while (!s->queue.empty()) {
+    finish_locked(s, s->queue.front(), LGT_ECANCELLED);
+    s->queue.pop_front();
+  }
+  lk.unlock();
+  cudaStreamSynchronize(s->stream);
+}
+
+}  // namespace
 
 extern "C" lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt_server **out) {
-  (void)hbm_budget_bytes; (void)device;
-  if (out) *out = nullptr;
-  lgt_set_error("server not available in this build");
-  return LGT_EINVAL;
+  if (!out) {
+    lgt_set_error("lgt_server_create: out is NULL");
+    return LGT_EINVAL;
+  }
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    lgt_set_error("lgt_server_create: no CUDA device %d (%s)", device, cudaGetErrorString(e));
+    return e == cudaSuccess ? LGT_EINVAL : LGT_ECUDA;
+  }
+  lgt_server *s = new lgt_server();
+  s->budget = hbm_budget_bytes;
+  s->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&s->pool, &props);
+  }
+  if (e == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached for the next admissions
+    e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_totals, sizeof(double) * TOT_N * kMaxSlots);
+  if (e == cudaSuccess) e = cudaMemset(s->d_totals, 0, sizeof(double) * TOT_N * kMaxSlots);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_totals, sizeof(double) * TOT_N * kMaxSlots);
+  if (e != cudaSuccess) {
+    lgt_set_error("lgt_server_create: %s", cudaGetErrorString(e));
+    if (s->d_totals) cudaFree(s->d_totals);
+    if (s->h_totals) cudaFreeHost(s->h_totals);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return e == cudaErrorMemoryAllocation ? LGT_ENOMEM : LGT_ECUDA;
+  }
+  for (int k = kMaxSlots - 1; k >= 0; k--) s->free_slots.push_back(k);
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return LGT_OK;
 }
+
 extern "C" lgt_status lgt_submit(lgt_server *s, const lgt_params *params, const double *links, uint64_t *job_id) {
-  (void)s; (void)params; (void)links; (void)job_id;
-  lgt_set_error("server not available in this build");
-  return LGT_EINVAL;
+  if (!s || !links || !job_id) {
+    lgt_set_error("lgt_submit: bad arguments");
+    return LGT_EINVAL;
+  }
+  lgt_status st = lgt_validate_params(params);
+  if (st != LGT_OK) return st;
+  const size_t need = lgt_ctx_device_bytes(params) + aos_bytes_of(lgt_make_geom(params->dims));
+  if (need > s->budget) {
+    lgt_set_error("job needs %zu device bytes, more than the server budget %zu", need, s->budget);
+    return LGT_ENOMEM;
+  }
+  Job *j = new Job();
+  j->prm = *params;
+  memset(&j->res, 0, sizeof j->res);
+  const Geom g = lgt_make_geom(params->dims);
+  j->input.assign(links, links + aos_bytes_of(g) / sizeof(double));
+  j->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) {
+    delete j;
+    lgt_set_error("lgt_submit: server is stopping");
+    return LGT_EBUSY;
+  }
+  j->id = s->next_id++;
+  s->jobs[j->id] = j;
+  s->queue.push_back(j);
+  *job_id = j->id;
+  s->cv.notify_all();
+  return LGT_OK;
 }
+
 extern "C" lgt_status lgt_poll(lgt_server *s, uint64_t job_id, lgt_result *res, double *links_out) {
-  (void)s; (void)job_id; (void)res; (void)links_out;
-  lgt_set_error("server not available in this build");
-  return LGT_EINVAL;
+  if (!s) {
+    lgt_set_error("lgt_poll: NULL server");
+    return LGT_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) {
+    lgt_set_error("lgt_poll: unknown job %llu", (unsigned long long)job_id);
+    return LGT_ENOTFOUND;
+  }
+  Job *j = it->second;
+  if (j->state != JOB_DONE) return LGT_EAGAIN;
+  if (res) *res = j->res;
+  if (links_out && !j->output.empty()) memcpy(links_out, j->output.data(), j->output.size() * sizeof(double));
+  const lgt_status st = (lgt_status)j->res.status;
+  s->jobs.erase(it);
+  delete j;
+  return st;
 }
+
 extern "C" lgt_status lgt_cancel(lgt_server *s, uint64_t job_id) {
-  (void)s; (void)job_id;
-  lgt_set_error("server not available in this build");
-  return LGT_EINVAL;
+  if (!s) {
+    lgt_set_error("lgt_cancel: NULL server");
+    return LGT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) {
+    lgt_set_error("lgt_cancel: unknown job %llu", (unsigned long long)job_id);
+    return LGT_ENOTFOUND;
+  }
+  it->second->cancel = true;
+  s->cv.notify_all();
+  return LGT_OK;
 }
-extern "C" lgt_status lgt_server_stats(lgt_server *s, uint64_t *a, uint64_t *b, size_t *c) {
-  (void)s; (void)a; (void)b; (void)c;
-  lgt_set_error("server not available in this build");
-  return LGT_EINVAL;
+
+extern "C" lgt_status lgt_server_stats(lgt_server *s, uint64_t *jobs_done, uint64_t *jobs_live, size_t *bytes_in_use) {
+  if (!s) {
+    lgt_set_error("lgt_server_stats: NULL server");
+    return LGT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (jobs_done) *jobs_done = s->done;
+  if (jobs_live) *jobs_live = s->live.size();
+  if (bytes_in_use) *bytes_in_use = s->used;
+  return s->fatal == cudaSuccess ? LGT_OK : LGT_ECUDA;
 }
-extern "C" void lgt_server_destroy(lgt_server *s) { (void)s; }
+
+extern "C" void lgt_server_destroy(lgt_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (auto &kv : s->jobs) delete kv.second;
+  if (s->d_sweep) cudaFree(s->d_sweep);
+  if (s->h_sweep) cudaFreeHost(s->h_sweep);
+  if (s->d_meas) cudaFree(s->d_meas);
+  if (s->h_meas) cudaFreeHost(s->h_meas);
+  if (s->d_totals) cudaFree(s->d_totals);
+  if (s->h_totals) cudaFreeHost(s->h_totals);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}

@@ -258,7 +258,8 @@ def lgt_submit(server, params: lgt_params, links: np.ndarray) -> int:
 
 
 def lgt_poll(server, job_id: int, links_out: np.ndarray | None = None):
-    """(status, lgt_result); status LGT_EAGAIN while the job runs, else its final status."""
+    """(status, lgt_result); status LGT_EAGAIN while the job runs, else the job's final
+    status (LGT_OK, LGT_ENOTCONV, LGT_ECANCELLED, or the error that ended it)."""
     res = lgt_result()
     ptr = None
     if links_out is not None:
@@ -266,7 +267,8 @@ def lgt_poll(server, job_id: int, links_out: np.ndarray | None = None):
         if on_dev:
             raise TypeError("lgt_poll writes host links")
     st = _lib.lgt_poll(server, int(job_id), ctypes.byref(res), ptr)
-    _check(st, (LGT_OK, LGT_EAGAIN, LGT_ENOTCONV, LGT_ECANCELLED, LGT_ETIMEOUT))
+    if st == LGT_ENOTFOUND:
+        raise LgtError(st, lgt_last_error())
     return st, res
 
 

@@ -1,0 +1,164 @@
+"""The continuous-batching server: every job's result is the same alone and in a
+mix (bit for bit: each job's kernels and decisions depend only on its own
+parameters), matches the single-context driver, and admission respects the
+device-memory budget."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1305_3440_gb300 import synth
+from lattice_np import plaquettes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lgt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1305_3440_gb300 import build
+    build.build()
+    from paper_1305_3440_gb300 import lgt as mod
+    return mod
+
+
+# (dims, gauge, algo, bulk, tol, eps, seed)
+JOBS = [
+    ((4, 4, 4, 4), 0, 0, 2, 1e-14, 0.3, 101),
+    ((6, 4, 4, 8), 1, 0, 1, 1e-12, 0.5, 102),
+    ((8, 8, 8, 8), 0, 0, 0, 1e-14, 0.4, 103),
+    ((4, 8, 8, 8), 1, 0, 2, 1e-14, 0.5, 104),
+    ((8, 4, 4, 4), 0, 1, 2, 1e-14, 0.3, 105),
+    ((8, 8, 8, 8), 0, 0, 2, 1e-12, 0.6, 106),
+]
+
+
+def params_of(lgt, spec):
+    dims, gauge, algo, bulk, tol, eps, seed = spec
+    return lgt.lgt_params_default(dims=dims, gauge=gauge, algo=algo, bulk=bulk, theta_tol=tol, p=0.8,
+                                  seed=seed, max_sweeps=5000)
+
+
+def wait_all(lgt, srv, ids, dims_of, timeout=300):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(ids):
+        assert time.time() - t0 < timeout, "server jobs did not finish"
+        for jid in ids:
+            if jid in out:
+                continue
+            links = np.empty(tuple(dims_of[jid]) + (4, 3, 3), np.complex128)
+            st, res = lgt.lgt_poll(srv, jid, links)
+            if st != lgt.LGT_EAGAIN:
+                out[jid] = (st, res.as_dict(), links)
+        time.sleep(0.005)
+    return out
+
+
+def run_server(lgt, specs, budget=8 << 30):
+    srv = lgt.lgt_server_create(budget, 0)
+    try:
+        ids, dims_of = [], {}
+        for spec in specs:
+            U = synth.field(spec[0], spec[5], spec[6])
+            jid = lgt.lgt_submit(srv, params_of(lgt, spec), U)
+            ids.append(jid)
+            dims_of[jid] = spec[0]
+        res = wait_all(lgt, srv, ids, dims_of)
+        done, live, used = lgt.lgt_server_stats(srv)
+        assert done == len(specs) and live == 0 and used == 0
+    finally:
+        lgt.lgt_server_destroy(srv)
+    return [res[j] for j in ids]
+
+
+def test_server_results_same_alone_and_in_mix(lgt):
+    mix = run_server(lgt, JOBS)
+    for spec, (st, res, links) in zip(JOBS, mix):
+        assert st == lgt.LGT_OK and res["theta"] < spec[4]
+        st1, res1, links1 = run_server(lgt, [spec])[0]
+        assert st1 == st
+        assert res1["F"] == res["F"] and res1["theta"] == res["theta"]
+        assert res1["sweeps_bulk"] == res["sweeps_bulk"] and res1["sweeps_fp64"] == res["sweeps_fp64"]
+        assert np.array_equal(links1, links)
+
+
+def test_server_matches_single_context_and_oracle(lgt):
+    mix = run_server(lgt, JOBS[:4])
+    for spec, (st, res, links) in zip(JOBS[:4], mix):
+        dims, gauge, algo, bulk, tol, eps, seed = spec
+        U = synth.field(dims, eps, seed)
+        ctx = lgt.lgt_create(params_of(lgt, spec), U)
+        try:
+            st2, r2 = lgt.lgt_fix(ctx)
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st2 == st == lgt.LGT_OK
+        assert abs(r2.F - res["F"]) < 1e-12
+        assert r2.sweeps_bulk == res["sweeps_bulk"] and r2.sweeps_fp64 == res["sweeps_fp64"]
+        m = O.measure(links, gauge)
+        assert m["theta"] < tol
+        assert np.abs(plaquettes(links) - plaquettes(U)).max() < 1e-12
+        ref = U.copy()
+        r = O.fix(ref, gauge=gauge, algo=algo, p=0.8, seed=seed, tol=tol, max_sweeps=5000)
+        assert r["converged"] and abs(r["F"] - res["F"]) < 1e-10
+
+
+def test_server_admission_respects_budget(lgt):
+    """A budget that fits one 8^4 FP32 job at a time: jobs run one after another."""
+    spec = ((8, 8, 8, 8), 0, 0, 2, 1e-12, 0.3, 200)
+    one = 8 * 8 * 8 * 8 * (576 + 192 + 36 + 576) + (1 << 20)
+    srv = lgt.lgt_server_create(int(one * 1.2), 0)
+    try:
+        ids, dims_of = [], {}
+        for k in range(4):
+            s = spec[:6] + (200 + k,)
+            jid = lgt.lgt_submit(srv, params_of(lgt, s), synth.field(s[0], s[5], s[6]))
+            ids.append(jid)
+            dims_of[jid] = s[0]
+        peak_live = 0
+        t0 = time.time()
+        while True:
+            done, live, used = lgt.lgt_server_stats(srv)
+            peak_live = max(peak_live, live)
+            assert used <= int(one * 1.2)
+            if done == 4:
+                break
+            assert time.time() - t0 < 120
+            time.sleep(0.002)
+        res = wait_all(lgt, srv, ids, dims_of)
+    finally:
+        lgt.lgt_server_destroy(srv)
+    assert peak_live <= 1
+    assert all(st == lgt.LGT_OK for st, _, _ in res.values())
+
+
+def test_server_errors_and_cancel(lgt):
+    srv = lgt.lgt_server_create(64 << 20, 0)
+    try:
+        big = lgt.lgt_params_default(dims=(16, 16, 16, 16))
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_submit(srv, big, synth.field((16, 16, 16, 16), 0.3, 1))
+        assert e.value.status == lgt.LGT_ENOMEM
+        bad = lgt.lgt_params_default(dims=(4, 4, 4, 5))
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_submit(srv, bad, np.zeros((4, 4, 4, 5, 4, 3, 3), np.complex128))
+        assert e.value.status == lgt.LGT_EINVAL
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_poll(srv, 12345)
+        assert e.value.status == lgt.LGT_ENOTFOUND
+        # non-SU(3) input finishes with EINVAL; a long job is cancelled
+        U = synth.field((4, 4, 4, 4), 0.3, 2)
+        U[0, 0, 0, 0, 0] *= 2
+        j_bad = lgt.lgt_submit(srv, lgt.lgt_params_default(dims=(4, 4, 4, 4)), U)
+        p_long = lgt.lgt_params_default(dims=(8, 8, 8, 8), theta_tol=1e-30, max_sweeps=10**9, bulk=0)
+        j_long = lgt.lgt_submit(srv, p_long, synth.field((8, 8, 8, 8), 0.3, 3))
+        time.sleep(0.2)
+        lgt.lgt_cancel(srv, j_long)
+        res = wait_all(lgt, srv, [j_bad, j_long], {j_bad: (4, 4, 4, 4), j_long: (8, 8, 8, 8)}, timeout=60)
+        assert res[j_bad][0] == lgt.LGT_EINVAL
+        assert res[j_long][0] == lgt.LGT_ECANCELLED
+    finally:
+        lgt.lgt_server_destroy(srv)
