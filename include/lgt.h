@@ -124,7 +124,7 @@ typedef struct {
 } lgt_result;
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
- * theta_switch 1e-11, max_sweeps 10000, check_every 10, reunit_every 50,
+ * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
  * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR.  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);
 

@@ -58,7 +58,7 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->seed = 0;
   p->sweep_offset = 0;
   p->theta_tol = 1e-14;
-  p->theta_switch = 1e-11;
+  p->theta_switch = 1e-13;
   p->max_sweeps = 10000;
   p->check_every = 10;
   p->reunit_every = 50;
@@ -436,18 +436,7 @@ struct Meas {
   int active;
 };
 
-// exact measurement of the working field; coulomb_target >= 0 updates masks
-static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas *m) {
-  const int fmt = work_fmt(c);
-  const void *links = c->phase == 0 ? c->u32 : c->u64;
-  const int bt = batch_begin(c, 2);
-  LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream));
-  batch_end(c, bt);
-  c->stats.measure_launches++;
-  c->stats.launches++;
-  lgt_status st = read_back(c, c->ws.totals, sizeof(double) * TOT_N);
-  if (st != LGT_OK) return st;
-  const double *t = c->host;
+static void fill_meas(const lgt_ctx *c, const double *t, Meas *m) {
   if (c->prm.gauge == LGT_COULOMB) {
     m->F = t[TOT_F_COULOMB];
     m->theta = t[TOT_THETA_COULOMB_MAX];
@@ -459,6 +448,30 @@ static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas
   }
   m->plaq = t[TOT_PLAQ];
   m->active = (int)t[TOT_ACTIVE_SLICES];
+}
+
+// exact measurement of the working field; coulomb_target >= 0 updates masks
+static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas *m) {
+  const int fmt = work_fmt(c);
+  const void *links = c->phase == 0 ? c->u32 : c->u64;
+  const int bt = batch_begin(c, 2);
+  LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream));
+  batch_end(c, bt);
+  c->stats.measure_launches++;
+  c->stats.launches++;
+  lgt_status st = read_back(c, c->ws.totals, sizeof(double) * TOT_N);
+  if (st != LGT_OK) return st;
+  fill_meas(c, c->host, m);
+  return LGT_OK;
+}
+
+// fused estimate from the last sweep's own K(x) (theta lagged by half a sweep)
+static lgt_status estimate(lgt_ctx *c, double coulomb_target, Meas *m) {
+  LGT_CUDA(launch_fused_finish(c->g, c->ws, c->cfg.gauge, c->block, coulomb_target, c->stream));
+  c->stats.launches++;
+  lgt_status st = read_back(c, c->ws.fused_totals, sizeof(double) * TOT_N);
+  if (st != LGT_OK) return st;
+  fill_meas(c, c->host, m);
   return LGT_OK;
 }
 
@@ -544,7 +557,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
       st = run_sweeps(c, n, coulomb ? 1 : 0);
       if (st != LGT_OK) return st;
       remaining -= n;
-      st = measure(c, 0, coulomb ? target : -1.0, &m);
+      st = estimate(c, coulomb ? target : -1.0, &m);
       if (st != LGT_OK) return st;
       if (m.theta < best) {
         best = m.theta;
@@ -565,8 +578,12 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     st = run_sweeps(c, n, coulomb ? 1 : 0);
     if (st != LGT_OK) return st;
     remaining -= n;
-    st = measure(c, 0, coulomb ? tol : -1.0, &m);
+    st = estimate(c, coulomb ? tol : -1.0, &m);
     if (st != LGT_OK) return st;
+    if (m.theta < tol) {  // the estimate says converged: certify with the exact measurement
+      st = measure(c, 0, coulomb ? tol : -1.0, &m);
+      if (st != LGT_OK) return st;
+    }
   }
   // all slices active again for later calls
   LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)c->g.nt, c->stream));

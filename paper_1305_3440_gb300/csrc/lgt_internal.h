@@ -28,9 +28,11 @@ enum {
 
 // Device workspace of one lattice (one allocation, carved up).
 struct Workspace {
-  double *sweep_partial;    // [nt][gx_max][2]
-  unsigned *sweep_counter;  // [nt]
-  double *fused;            // [2][nt][2]  Re tr K, tr Delta^2 per parity and slice
+  double2 *warp_part;       // [2][nt][wps] per-warp (Re tr K, tr Delta^2) of each parity's last half-sweep
+  int wps;                  // warps per timeslice (stride of warp_part)
+  double *fused_slice;      // [nt][2] per-slice fused sums (parity-0 Re tr K, both parities' tr Delta^2)
+  unsigned *fused_counter;  // [1]
+  double *fused_totals;     // [TOT_N] fused estimate, layout of totals
   double *meas_partial;     // [nt][2][gx_max][MEAS_NV]
   unsigned *meas_counter;   // [nt]
   unsigned *glob_counter;   // [1]
@@ -51,9 +53,8 @@ struct SweepArgs {
   void *links;
   void *G;
   const uint8_t *active;
-  double *partial;    // [nt][gridDim.x][2]
-  unsigned *counter;  // [nt]
-  double *fused;      // [2][nt][2]
+  double2 *warp_part;  // [2][nt][wps]
+  int wps;
   double omega;
   unsigned long long sr_thr;
   unsigned long long seed;
@@ -81,6 +82,20 @@ struct MeasArgs {
   int with_plaq;
 };
 
+// Arguments of the fused estimate's finishing reduction (one block per slice).
+struct FusedArgs {
+  Geom g;
+  const double2 *warp_part;
+  int wps;
+  int nw;  // warps per slice that wrote in the last half-sweeps
+  int gauge;
+  double *slice;
+  unsigned *counter;
+  double *totals;
+  uint8_t *active;
+  double coulomb_target;
+};
+
 // One row of a batched launch: a lattice's arguments and its block range.
 struct BatchSweep {
   SweepArgs a;
@@ -91,6 +106,11 @@ struct BatchMeas {
   MeasArgs a;
   int block_begin;
   int nbx;
+};
+struct BatchFused {
+  FusedArgs a;
+  int block_begin;  // one block per timeslice
+  int nbx;          // unused
 };
 
 struct SweepCfg {
@@ -107,6 +127,17 @@ struct SweepCfg {
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int block,
                               cudaStream_t st);
+
+// Fused estimate of F and theta from the last two half-sweeps (each sweep
+// kernel leaves per-warp sums of Re tr K and tr Delta^2 computed from the K it
+// used, so theta is lagged by half a sweep).  Reduced in fixed order into
+// w.fused_totals; if coulomb_target >= 0 the slice mask is set to
+// (theta_t >= coulomb_target).  sweep_block: block size of those sweeps.
+cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_block, double coulomb_target,
+                                cudaStream_t st);
+void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_block,
+                     double coulomb_target);
+cudaError_t launch_fused_finish_batch(const BatchFused *jobs, int n, int total_blocks, cudaStream_t st);
 
 // Exact measurement of a field of format fmt (FP64 arithmetic) into
 // w.totals / w.slice_F / w.slice_theta.  If coulomb_target >= 0 the slice

@@ -25,18 +25,21 @@ namespace lgt {
 
 static inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+static int warps_per_slice(const Geom &g) { return ceil_div(g.vs_half, 32) + 8; }
+
 size_t workspace_bytes(const Geom &g, int min_block) {
   const int gx = ceil_div(g.vs_half, min_block);
   size_t b = 0;
-  b += sizeof(double) * (size_t)g.nt * gx * 2;             // sweep_partial
-  b += sizeof(double) * 2 * (size_t)g.nt * 2;              // fused
+  b += sizeof(double2) * 2 * (size_t)g.nt * warps_per_slice(g);  // warp_part
+  b += sizeof(double) * (size_t)g.nt * 2 + sizeof(unsigned);     // fused_slice, fused_counter
+  b += sizeof(double) * TOT_N;                                    // fused_totals
   b += sizeof(double) * (size_t)g.nt * 2 * gx * MEAS_NV;   // meas_partial
   b += sizeof(double) * (size_t)g.nt * MEAS_NV;            // slice_sum
   b += sizeof(double) * (size_t)g.nt * 2;                  // slice_F, slice_theta
   b += sizeof(double) * TOT_N;                             // totals
-  b += sizeof(unsigned) * ((size_t)g.nt * 2 + 1);          // counters
+  b += sizeof(unsigned) * ((size_t)g.nt + 1);              // counters
   b += (size_t)g.nt + sizeof(int);                         // active, err
-  return b + 16 * 16;                                      // alignment slack
+  return b + 16 * 20;                                      // alignment slack
 }
 
 static char *align16(char *p) { return (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15); }
@@ -44,10 +47,15 @@ static char *align16(char *p) { return (char *)(((uintptr_t)p + 15) & ~(uintptr_
 void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
   const int gx = ceil_div(g.vs_half, min_block);
   char *p = align16((char *)base);
-  w->sweep_partial = (double *)p;
-  p = align16(p + sizeof(double) * (size_t)g.nt * gx * 2);
-  w->fused = (double *)p;
-  p = align16(p + sizeof(double) * 2 * (size_t)g.nt * 2);
+  w->wps = warps_per_slice(g);
+  w->warp_part = (double2 *)p;
+  p = align16(p + sizeof(double2) * 2 * (size_t)g.nt * w->wps);
+  w->fused_slice = (double *)p;
+  p = align16(p + sizeof(double) * (size_t)g.nt * 2);
+  w->fused_counter = (unsigned *)p;
+  p = align16(p + sizeof(unsigned));
+  w->fused_totals = (double *)p;
+  p = align16(p + sizeof(double) * TOT_N);
   w->meas_partial = (double *)p;
   p = align16(p + sizeof(double) * (size_t)g.nt * 2 * gx * MEAS_NV);
   w->slice_sum = (double *)p;
@@ -58,8 +66,6 @@ void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
   p = align16(p + sizeof(double) * (size_t)g.nt);
   w->totals = (double *)p;
   p = align16(p + sizeof(double) * TOT_N);
-  w->sweep_counter = (unsigned *)p;
-  p = align16(p + sizeof(unsigned) * (size_t)g.nt);
   w->meas_counter = (unsigned *)p;
   p = align16(p + sizeof(unsigned) * (size_t)g.nt);
   w->glob_counter = (unsigned *)p;
@@ -72,35 +78,18 @@ void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
 // ----------------------------------------------------------------- sweeps
 
 
-// Fixed-order per-slice sum of the block partials by the slice's last block.
-// bx: this block's index within timeslice t, nbx: blocks per timeslice.
+// The fused estimate: each warp's sum of (Re tr K, tr Delta^2) over its sites
+// goes to its own slot (xor butterfly: fixed order; no block barrier, no
+// atomics); k_fused_finish reduces the slots when an estimate is wanted.
 template <typename T>
-__device__ __forceinline__ void fused_reduce(const SweepArgs &a, int p, int t, int bx, int nbx, T acc[2]) {
-  __shared__ double tot[2];
-  __shared__ int am_last;
-  block_sum<2, T>(acc, tot);
-  if (threadIdx.x == 0) {
-    double *dst = a.partial + ((size_t)t * nbx + bx) * 2;
-    dst[0] = tot[0];
-    dst[1] = tot[1];
-    __threadfence();
-    const unsigned prev = atomicAdd(&a.counter[t], 1u);
-    am_last = (prev == (unsigned)nbx - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  double v[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nbx; b += blockDim.x) {
-    const double *src = a.partial + ((size_t)t * nbx + b) * 2;
-    v[0] += __ldcg(src);
-    v[1] += __ldcg(src + 1);
-  }
-  block_sum<2, double>(v, tot);
-  if (threadIdx.x == 0) {
-    a.fused[((size_t)p * a.g.nt + t) * 2] = tot[0];
-    a.fused[((size_t)p * a.g.nt + t) * 2 + 1] = tot[1];
-    a.counter[t] = 0u;
+__device__ __forceinline__ void fused_store(const SweepArgs &a, int p, int t, int bx, T acc[2]) {
+#pragma unroll
+  for (int k = 0; k < 2; k++)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if ((threadIdx.x & 31) == 0) {
+    const int w = bx * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    a.warp_part[((size_t)p * a.g.nt + t) * a.wps + w] = make_double2((double)acc[0], (double)acc[1]);
   }
 }
 
@@ -191,7 +180,7 @@ __device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t,
       GIO::store(a.G, a.g.vh, p, i, r);
     }
   }
-  fused_reduce<float>(a, p, t, bx, nbx, acc);
+  fused_store<float>(a, p, t, bx, acc);
 }
 
 template <int FMT, int GAUGE, int ALGO>
@@ -240,7 +229,7 @@ __device__ __forceinline__ void sweep_body_f64(const SweepArgs &a, int p, int t,
       IO::store(a.links, a.g.vh, q, mu, nbm, r);
     }
   }
-  fused_reduce<double>(a, p, t, bx, nbx, acc);
+  fused_store<double>(a, p, t, bx, acc);
 }
 
 template <int GAUGE, int ALGO>
@@ -249,8 +238,11 @@ __global__ void __launch_bounds__(256) k_sweep_f64(SweepArgs a, int p) {
 }
 
 // FP32-pair polishing sweep (FMT_PAIR storage): K(x) in pair arithmetic, the
-// rotation angles in FP32, the three SU(2) elements applied to every link in
+// rotation angles in FP32, g = R2 R1 R0 formed in pair precision (unitary to
+// ~2^-48) and applied to every link as U + delta U / U + U delta^dagger in
 // pair arithmetic (see lgt_pair.cuh).  Links are re-read for the write-back.
+// The loops over directions are not unrolled: the body is instruction-bound
+// and a compact loop keeps it in the instruction cache.
 template <int GAUGE, int ALGO>
 __device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t, int bx, int nbx) {
   typedef LinkIO<FMT_PAIR> IO;
@@ -262,18 +254,16 @@ __device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t
     const Coords c = coords_in_slice(a.g, p, t, j);
     const int i = t * a.g.vs_half + j;
     const int q = p ^ 1;
-    int nb[4];
     f2 W[18];
 #pragma unroll
     for (int e = 0; e < 18; e++) W[e] = f2{0.0f, 0.0f};
-#pragma unroll
+#pragma unroll 1
     for (int mu = MU0; mu < 4; mu++) {
       f2 u[18];
-      nb[mu] = cb_shift(a.g, c, mu, -1);
       IO::load(a.links, a.g.vh, p, mu, i, u);
 #pragma unroll
       for (int e = 0; e < 18; e++) W[e] = pair_add(W[e], u[e]);
-      IO::load(a.links, a.g.vh, q, mu, nb[mu], u);
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
 #pragma unroll
       for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -287,19 +277,22 @@ __device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
     Rot rot[3];
     pair_local_update<ALGO>(W, rot, (float)a.omega, a.sr_thr, draws);
+    f2 d[18];
+    pair_delta(rot, d);
     const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
+#pragma unroll 1
     for (int mu = mu_lo; mu < 4; mu++) {
-      const int nbm = mu < MU0 ? cb_shift(a.g, c, 0, -1) : nb[mu];
+      const int nbm = cb_shift(a.g, c, mu, -1);
       f2 u[18];
       IO::load(a.links, a.g.vh, p, mu, i, u);
-      pair_apply_left(u, rot);
+      pair_apply_left(u, d);
       IO::store(a.links, a.g.vh, p, mu, i, u);
       IO::load(a.links, a.g.vh, q, mu, nbm, u);
-      pair_apply_right_dag(u, rot);
+      pair_apply_right_dag(u, d);
       IO::store(a.links, a.g.vh, q, mu, nbm, u);
     }
   }
-  fused_reduce<float>(a, p, t, bx, nbx, acc);
+  fused_store<float>(a, p, t, bx, acc);
 }
 
 template <int GAUGE, int ALGO>
@@ -338,9 +331,8 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->links = links;
   a->G = G;
   a->active = use_mask ? w.active : nullptr;
-  a->partial = w.sweep_partial;
-  a->counter = w.sweep_counter;
-  a->fused = w.fused;
+  a->warp_part = w.warp_part;
+  a->wps = w.wps;
   a->omega = c.omega;
   a->sr_thr = c.sr_thr;
   a->seed = c.seed;
@@ -755,6 +747,87 @@ cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_
 }
 
 
+// ------------------------------------------------- fused estimate, finish
+void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_block,
+                     double coulomb_target) {
+  a->g = g;
+  a->warp_part = w.warp_part;
+  a->wps = w.wps;
+  a->nw = ceil_div(g.vs_half, sweep_block) * (sweep_block / 32);
+  a->gauge = gauge;
+  a->slice = w.fused_slice;
+  a->counter = w.fused_counter;
+  a->totals = w.fused_totals;
+  a->active = w.active;
+  a->coulomb_target = coulomb_target;
+}
+
+// One block per timeslice: fixed-order sums of the slice's warp slots
+// (parity-0 Re tr K; tr Delta^2 of both parities); the last block forms the
+// totals in slice order.  Slices masked off (converged) keep their previous
+// Re tr K sum and report zero violation.
+__device__ __forceinline__ void fused_finish_body(const FusedArgs &a, int t) {
+  __shared__ double tot[2];
+  __shared__ int am_last;
+  if (a.active[t]) {
+    double v[2] = {0.0, 0.0};
+    const double2 *p0 = a.warp_part + (size_t)t * a.wps;
+    const double2 *p1 = a.warp_part + ((size_t)a.g.nt + t) * a.wps;
+    for (int w = threadIdx.x; w < a.nw; w += blockDim.x) {
+      const double2 x0 = p0[w], x1 = p1[w];
+      v[0] += x0.x;
+      v[1] += x0.y + x1.y;
+    }
+    block_sum<2, double>(v, tot);
+    if (threadIdx.x == 0) {
+      a.slice[2 * t] = tot[0];
+      a.slice[2 * t + 1] = tot[1];
+    }
+  } else if (threadIdx.x == 0) {
+    a.slice[2 * t + 1] = 0.0;  // converged and masked off: no new estimate
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    am_last = atomicAdd(a.counter, 1u) == (unsigned)a.g.nt - 1;
+  }
+  __syncthreads();
+  if (!am_last || threadIdx.x != 0) return;
+  __threadfence();
+  const double vs = 2.0 * (double)a.g.vs_half, vol = 2.0 * (double)a.g.vh;
+  const double nd = a.gauge == GAUGE_COULOMB ? 3.0 : 4.0;
+  double fsum = 0.0, tsum = 0.0, tmax = 0.0, ftot = 0.0, ttot = 0.0;
+  int nact = 0;
+  for (int tt = 0; tt < a.g.nt; tt++) {
+    const double rk = __ldcg(a.slice + 2 * tt), th2 = __ldcg(a.slice + 2 * tt + 1);
+    ftot += rk;
+    ttot += th2;
+    const double ft = rk / (3.0 * nd * vs), th = th2 / (3.0 * vs);
+    fsum += ft;
+    tsum += th;
+    tmax = th > tmax ? th : tmax;
+    if (a.coulomb_target >= 0.0) a.active[tt] = th >= a.coulomb_target ? 1 : 0;
+    nact += a.active[tt];
+  }
+  a.totals[TOT_F_LANDAU] = ftot / (3.0 * nd * vol);
+  a.totals[TOT_THETA_LANDAU] = ttot / (3.0 * vol);
+  a.totals[TOT_PLAQ] = 0.0;
+  a.totals[TOT_F_COULOMB] = fsum / (double)a.g.nt;
+  a.totals[TOT_THETA_COULOMB_MAX] = tmax;
+  a.totals[TOT_THETA_COULOMB_MEAN] = tsum / (double)a.g.nt;
+  a.totals[TOT_ACTIVE_SLICES] = (double)nact;
+  *a.counter = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_fused_finish(FusedArgs a) { fused_finish_body(a, blockIdx.x); }
+
+cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_block, double coulomb_target,
+                                cudaStream_t st) {
+  FusedArgs a;
+  fill_fused_args(&a, g, w, gauge, sweep_block, coulomb_target);
+  k_fused_finish<<<g.nt, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------- batched launches
 // Block b of a batched grid belongs to the last row k with
 // jobs[k].block_begin <= b (rows sorted by block_begin).
@@ -828,6 +901,17 @@ cudaError_t launch_measure_batch(int fmt, const BatchMeas *jobs, int n, int tota
   else if (fmt == FMT_F32_12) k_measure_batch<FMT_F32_12><<<total_blocks, block, 0, st>>>(jobs, n);
   else if (fmt == FMT_PAIR) k_measure_batch<FMT_PAIR><<<total_blocks, block, 0, st>>>(jobs, n);
   else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_fused_finish_batch(const BatchFused *jobs, int n) {
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchFused), n, blockIdx.x);
+  fused_finish_body(jobs[k].a, blockIdx.x - jobs[k].block_begin);
+}
+
+cudaError_t launch_fused_finish_batch(const BatchFused *jobs, int n, int total_blocks, cudaStream_t st) {
+  if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+  k_fused_finish_batch<<<total_blocks, 256, 0, st>>>(jobs, n);
   return cudaGetLastError();
 }
 

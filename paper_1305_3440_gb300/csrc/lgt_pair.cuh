@@ -13,11 +13,10 @@
 //   * the rotation angles (which SU(2) element to apply) are chosen in FP32
 //     from the pair-precision K(x); a slightly suboptimal angle is still a
 //     gauge transformation and only costs optimality;
-//   * every SU(2) element takes its angles r1, r2, r3 as exact FP32 numbers
-//     and r0 = +-sqrt(1 - |r|^2) in pair precision, so it is unitary to ~2^-48
-//     at any rotation size, and it is applied to the links as R = 1 + rho in
-//     pair arithmetic.  The field therefore stays an exact (to ~2^-48) gauge
-//     transform of its input.
+//   * every SU(2) element is the FP32 quaternion rescaled to unit length in
+//     pair arithmetic, so it is unitary to ~2^-48 at any rotation size, and it
+//     is applied to the links as R = 1 + rho in pair arithmetic.  The field
+//     therefore stays an exact (to ~2^-48) gauge transform of its input.
 #pragma once
 
 #include "lgt_device.cuh"
@@ -58,36 +57,65 @@ __device__ __forceinline__ f2 two_prod(float a, float b) {
   return {p, __fmaf_rn(a, b, -p)};
 }
 
-// sqrt of a pair in [0, 1]: one Newton step on the FP32 root
-__device__ __forceinline__ f2 pair_sqrt(f2 w) {
-  if (!(w.hi > 0.0f)) return {0.0f, 0.0f};
-  const float s0 = __fsqrt_rn(w.hi);
-  const f2 sq = two_prod(s0, s0);
-  const f2 res = pair_add(w, pair_neg(sq));
-  return quick_two_sum(s0, __fdiv_rn(pair_to_float(res), __fmul_rn(2.0f, s0)));
+__device__ __forceinline__ f2 pair_mul(f2 a, f2 b) {
+  f2 p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return quick_two_sum(p.hi, p.lo);
 }
 
-// sum_k c[k] * x[k] + extra for float coefficients and pair values: exact
-// products of the high parts (TwoProd via fma), low parts and the small extra
-// term folded in with one rounding each
-__device__ __forceinline__ f2 pair_dot4(float c0, f2 x0, float c1, f2 x1, float c2, f2 x2, float c3, f2 x3,
-                                        float extra) {
-  const float p0 = __fmul_rn(c0, x0.hi), p1 = __fmul_rn(c1, x1.hi);
-  const float p2 = __fmul_rn(c2, x2.hi), p3 = __fmul_rn(c3, x3.hi);
-  float e = __fadd_rn(extra, __fmaf_rn(c0, x0.hi, -p0));
-  e = __fadd_rn(e, __fmaf_rn(c1, x1.hi, -p1));
-  e = __fadd_rn(e, __fmaf_rn(c2, x2.hi, -p2));
-  e = __fadd_rn(e, __fmaf_rn(c3, x3.hi, -p3));
-  e = __fmaf_rn(c0, x0.lo, e);
-  e = __fmaf_rn(c1, x1.lo, e);
-  e = __fmaf_rn(c2, x2.lo, e);
-  e = __fmaf_rn(c3, x3.lo, e);
+// 1/sqrt of a positive pair: correctly rounded FP32 root, one Newton step in pairs
+__device__ __forceinline__ f2 pair_rsqrt(f2 x) {
+  const float y = __frsqrt_rn(x.hi);
+  const f2 yy = two_prod(y, y);
+  const f2 r = pair_add(f2{1.0f, 0.0f}, pair_neg(pair_mul(x, yy)));  // 1 - x y^2
+  return quick_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), pair_to_float(r)));
+}
+
+// sum_k c[k] * x[k] for pair coefficients and pair values: exact products of
+// the high parts (TwoProd via fma), the low-part products folded in with one
+// rounding each
+__device__ __forceinline__ f2 pair_dot4(f2 c0, f2 x0, f2 c1, f2 x1, f2 c2, f2 x2, f2 c3, f2 x3) {
+  const float p0 = __fmul_rn(c0.hi, x0.hi), p1 = __fmul_rn(c1.hi, x1.hi);
+  const float p2 = __fmul_rn(c2.hi, x2.hi), p3 = __fmul_rn(c3.hi, x3.hi);
+  float e = __fmaf_rn(c0.hi, x0.hi, -p0);
+  e = __fadd_rn(e, __fmaf_rn(c1.hi, x1.hi, -p1));
+  e = __fadd_rn(e, __fmaf_rn(c2.hi, x2.hi, -p2));
+  e = __fadd_rn(e, __fmaf_rn(c3.hi, x3.hi, -p3));
+  e = __fmaf_rn(c0.hi, x0.lo, e);
+  e = __fmaf_rn(c1.hi, x1.lo, e);
+  e = __fmaf_rn(c2.hi, x2.lo, e);
+  e = __fmaf_rn(c3.hi, x3.lo, e);
+  e = __fmaf_rn(c0.lo, x0.hi, e);
+  e = __fmaf_rn(c1.lo, x1.hi, e);
+  e = __fmaf_rn(c2.lo, x2.hi, e);
+  e = __fmaf_rn(c3.lo, x3.hi, e);
   f2 s = two_sum(p0, p1);
   e = __fadd_rn(e, s.lo);
   s = two_sum(s.hi, p2);
   e = __fadd_rn(e, s.lo);
   s = two_sum(s.hi, p3);
   e = __fadd_rn(e, s.lo);
+  return quick_two_sum(s.hi, e);
+}
+
+// sum of six products of pairs (absolute error ~2^-48 of the largest term)
+__device__ __forceinline__ f2 pair_dot6(const f2 c[6], const f2 x[6]) {
+  float ph[6];
+  float e = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    ph[k] = __fmul_rn(c[k].hi, x[k].hi);
+    e = __fadd_rn(e, __fmaf_rn(c[k].hi, x[k].hi, -ph[k]));
+    e = __fmaf_rn(c[k].hi, x[k].lo, e);
+    e = __fmaf_rn(c[k].lo, x[k].hi, e);
+  }
+  f2 s = two_sum(ph[0], ph[1]);
+  e = __fadd_rn(e, s.lo);
+#pragma unroll
+  for (int k = 2; k < 6; k++) {
+    s = two_sum(s.hi, ph[k]);
+    e = __fadd_rn(e, s.lo);
+  }
   return quick_two_sum(s.hi, e);
 }
 
@@ -109,12 +137,11 @@ struct LinkIO<FMT_PAIR> {
   }
 };
 
-// One subgroup element (r0, r1, r2, r3), r0 = 1 + e0.  The angles r1..r3 are
-// FP32 numbers taken as exact; e0 is the pair-precision value of
-// +-sqrt(1 - |r|^2) - 1, so the element is unitary to ~2^-48 at any size.
+// One subgroup element (r0, r1, r2, r3) in pair precision, r0 = 1 + e0: the
+// FP32 quaternion rescaled to unit length in pair arithmetic, so the element is
+// unitary to ~2^-48 at any rotation size (well conditioned even at r0 ~ 0).
 struct Rot {
-  f2 e0;
-  float r1, r2, r3;
+  f2 e0, r1, r2, r3;
 };
 
 // FP32 choice of the element, before its pair-precision r0
@@ -123,14 +150,15 @@ struct RotF {
 };
 
 __device__ __forceinline__ Rot exact_rotation(const RotF &f) {
-  const f2 v = pair_add(pair_add(two_prod(f.r1, f.r1), two_prod(f.r2, f.r2)), two_prod(f.r3, f.r3));
-  f2 r0 = pair_sqrt(pair_add(f2{1.0f, 0.0f}, pair_neg(v)));
-  if (1.0f + f.e0 < 0.0f) r0 = pair_neg(r0);
+  const f2 r0 = two_sum(1.0f, f.e0);  // 1 + e0 exactly
+  const f2 n2 = pair_add(pair_add(pair_mul(r0, r0), two_prod(f.r1, f.r1)),
+                         pair_add(two_prod(f.r2, f.r2), two_prod(f.r3, f.r3)));
+  const f2 inv = pair_rsqrt(n2);
   Rot r;
-  r.e0 = pair_add(r0, f2{-1.0f, 0.0f});
-  r.r1 = f.r1;
-  r.r2 = f.r2;
-  r.r3 = f.r3;
+  r.e0 = pair_add(pair_mul(r0, inv), f2{-1.0f, 0.0f});
+  r.r1 = pair_mul(f2{f.r1, 0.0f}, inv);
+  r.r2 = pair_mul(f2{f.r2, 0.0f}, inv);
+  r.r3 = pair_mul(f2{f.r3, 0.0f}, inv);
   return r;
 }
 
@@ -181,30 +209,13 @@ __device__ __forceinline__ void rotate_rows(f2 m[18], const Rot &r) {
   for (int c = 0; c < 3; c++) {
     const f2 xi = m[LGT_RE(I, c)], yi = m[LGT_IM(I, c)];
     const f2 xj = m[LGT_RE(J, c)], yj = m[LGT_IM(J, c)];
-    const float e = r.e0.hi, el = r.e0.lo;
+    const f2 e = r.e0, r1 = r.r1, r2 = r.r2, r3 = r.r3, n1 = pair_neg(r.r1), n2 = pair_neg(r.r2), n3 = pair_neg(r.r3);
     // (e0 + i r3) (xi + i yi) + (r2 + i r1) (xj + i yj)
-    m[LGT_RE(I, c)] = pair_add(xi, pair_dot4(e, xi, -r.r3, yi, r.r2, xj, -r.r1, yj, el * xi.hi));
-    m[LGT_IM(I, c)] = pair_add(yi, pair_dot4(e, yi, r.r3, xi, r.r2, yj, r.r1, xj, el * yi.hi));
+    m[LGT_RE(I, c)] = pair_add(xi, pair_dot4(e, xi, n3, yi, r2, xj, n1, yj));
+    m[LGT_IM(I, c)] = pair_add(yi, pair_dot4(e, yi, r3, xi, r2, yj, r1, xj));
     // (-r2 + i r1) (xi + i yi) + (e0 - i r3) (xj + i yj)
-    m[LGT_RE(J, c)] = pair_add(xj, pair_dot4(-r.r2, xi, -r.r1, yi, e, xj, r.r3, yj, el * xj.hi));
-    m[LGT_IM(J, c)] = pair_add(yj, pair_dot4(-r.r2, yi, r.r1, xi, e, yj, -r.r3, xj, el * yj.hi));
-  }
-}
-
-// columns (i, j) of m <- m R^dagger
-template <int I, int J>
-__device__ __forceinline__ void rotate_cols_dag(f2 m[18], const Rot &r) {
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    const f2 xi = m[LGT_RE(a, I)], yi = m[LGT_IM(a, I)];
-    const f2 xj = m[LGT_RE(a, J)], yj = m[LGT_IM(a, J)];
-    const float e = r.e0.hi, el = r.e0.lo;
-    // m_ai conj(r0 + i r3) + m_aj conj(r2 + i r1) = m_ai (e0 - i r3) + m_aj (r2 - i r1) (+ m_ai)
-    m[LGT_RE(a, I)] = pair_add(xi, pair_dot4(e, xi, r.r3, yi, r.r2, xj, r.r1, yj, el * xi.hi));
-    m[LGT_IM(a, I)] = pair_add(yi, pair_dot4(e, yi, -r.r3, xi, r.r2, yj, -r.r1, xj, el * yi.hi));
-    // m_ai conj(-r2 + i r1) + m_aj conj(r0 - i r3) = m_ai (-r2 - i r1) + m_aj (e0 + i r3) (+ m_aj)
-    m[LGT_RE(a, J)] = pair_add(xj, pair_dot4(-r.r2, xi, r.r1, yi, e, xj, -r.r3, yj, el * xj.hi));
-    m[LGT_IM(a, J)] = pair_add(yj, pair_dot4(-r.r2, yi, -r.r1, xi, e, yj, r.r3, xj, el * yj.hi));
+    m[LGT_RE(J, c)] = pair_add(xj, pair_dot4(n2, xi, n1, yi, e, xj, r3, yj));
+    m[LGT_IM(J, c)] = pair_add(yj, pair_dot4(n2, yi, r1, xi, e, yj, n3, xj));
   }
 }
 
@@ -244,18 +255,74 @@ __device__ __forceinline__ void pair_local_update(f2 W[18], Rot rot[3], float om
   }
 }
 
-// U <- g U = R2 R1 R0 U
-__device__ __forceinline__ void pair_apply_left(f2 u[18], const Rot rot[3]) {
-  rotate_rows<0, 1>(u, rot[0]);
-  rotate_rows<0, 2>(u, rot[1]);
-  rotate_rows<1, 2>(u, rot[2]);
+// delta = g - 1 for g = R2 R1 R0, in pair precision (g unitary to ~2^-48)
+__device__ __forceinline__ void pair_delta(const Rot rot[3], f2 d[18]) {
+#pragma unroll
+  for (int e = 0; e < 18; e++) d[e] = f2{0.0f, 0.0f};
+  d[LGT_RE(0, 0)] = d[LGT_RE(1, 1)] = d[LGT_RE(2, 2)] = f2{1.0f, 0.0f};
+  rotate_rows<0, 1>(d, rot[0]);
+  rotate_rows<0, 2>(d, rot[1]);
+  rotate_rows<1, 2>(d, rot[2]);
+#pragma unroll
+  for (int a = 0; a < 3; a++) d[LGT_RE(a, a)] = pair_add(d[LGT_RE(a, a)], f2{-1.0f, 0.0f});
 }
 
-// U <- U g^dagger = U R0^dagger R1^dagger R2^dagger
-__device__ __forceinline__ void pair_apply_right_dag(f2 u[18], const Rot rot[3]) {
-  rotate_cols_dag<0, 1>(u, rot[0]);
-  rotate_cols_dag<0, 2>(u, rot[1]);
-  rotate_cols_dag<1, 2>(u, rot[2]);
+// U <- g U = U + delta U  (pair arithmetic)
+__device__ __forceinline__ void pair_apply_left(f2 u[18], const f2 d[18]) {
+  f2 r[18];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      f2 c[6], x[6];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {  // re: d_re u_re - d_im u_im
+        c[2 * k] = d[LGT_RE(i, k)];
+        x[2 * k] = u[LGT_RE(k, j)];
+        c[2 * k + 1] = pair_neg(d[LGT_IM(i, k)]);
+        x[2 * k + 1] = u[LGT_IM(k, j)];
+      }
+      r[LGT_RE(i, j)] = pair_add(u[LGT_RE(i, j)], pair_dot6(c, x));
+#pragma unroll
+      for (int k = 0; k < 3; k++) {  // im: d_re u_im + d_im u_re
+        c[2 * k] = d[LGT_RE(i, k)];
+        x[2 * k] = u[LGT_IM(k, j)];
+        c[2 * k + 1] = d[LGT_IM(i, k)];
+        x[2 * k + 1] = u[LGT_RE(k, j)];
+      }
+      r[LGT_IM(i, j)] = pair_add(u[LGT_IM(i, j)], pair_dot6(c, x));
+    }
+#pragma unroll
+  for (int e = 0; e < 18; e++) u[e] = r[e];
+}
+
+// U <- U g^dagger = U + U delta^dagger  (pair arithmetic)
+__device__ __forceinline__ void pair_apply_right_dag(f2 u[18], const f2 d[18]) {
+  f2 r[18];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      f2 c[6], x[6];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {  // re: u_re d_re + u_im d_im  (d_jk conjugated)
+        c[2 * k] = d[LGT_RE(j, k)];
+        x[2 * k] = u[LGT_RE(i, k)];
+        c[2 * k + 1] = d[LGT_IM(j, k)];
+        x[2 * k + 1] = u[LGT_IM(i, k)];
+      }
+      r[LGT_RE(i, j)] = pair_add(u[LGT_RE(i, j)], pair_dot6(c, x));
+#pragma unroll
+      for (int k = 0; k < 3; k++) {  // im: u_im d_re - u_re d_im
+        c[2 * k] = d[LGT_RE(j, k)];
+        x[2 * k] = u[LGT_IM(i, k)];
+        c[2 * k + 1] = pair_neg(d[LGT_IM(j, k)]);
+        x[2 * k + 1] = u[LGT_RE(i, k)];
+      }
+      r[LGT_IM(i, j)] = pair_add(u[LGT_IM(i, j)], pair_dot6(c, x));
+    }
+#pragma unroll
+  for (int e = 0; e < 18; e++) u[e] = r[e];
 }
 
 // Fused estimate from the pair K: Re tr K and tr[Delta Delta^dagger],

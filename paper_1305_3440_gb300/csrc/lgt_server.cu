@@ -7,8 +7,10 @@
 //      parity, one batched half-sweep launch per kernel variant (storage
 //      format x gauge x algorithm) covers the sites of all live jobs of that
 //      variant;
-//   3. one batched exact measurement per storage format gives each job's F and
-//      theta (one device->host copy for all jobs);
+//   3. one batched reduction of the sweeps' fused estimates gives each job's
+//      F and theta; jobs that start, were just promoted, or whose estimate
+//      says converged get a batched exact measurement instead (one
+//      device->host copy for all jobs);
 //   4. per job, the same ladder decisions as lgt_fix (Sec. 4 driver): bulk FP32
 //      until theta < theta_switch (or the FP32 floor), promotion, polishing to
 //      theta < theta_tol, or max_sweeps; finished jobs are measured once more,
@@ -108,7 +110,8 @@ struct lgt_server {
   std::vector<int> free_slots;
   BatchSweep *d_sweep = nullptr, *h_sweep = nullptr;
   BatchMeas *d_meas = nullptr, *h_meas = nullptr;
-  size_t sweep_cap = 0, meas_cap = 0;
+  BatchFused *d_fused = nullptr, *h_fused = nullptr;
+  size_t sweep_cap = 0, meas_cap = 0, fused_cap = 0;
   cudaError_t fatal = cudaSuccess;
 };
 
@@ -170,6 +173,7 @@ cudaError_t admit(lgt_server *s, Job *j, int *bad_input) {
   if ((e = cudaMemsetAsync(j->ws_base, 0, wsb, s->stream)) != cudaSuccess) return e;
   workspace_carve(j->ws_base, g, 64, &j->ws);
   j->ws.totals = s->d_totals + (size_t)j->slot * TOT_N;
+  j->ws.fused_totals = s->d_totals + ((size_t)kMaxSlots + j->slot) * TOT_N;
   if ((e = cudaMemsetAsync(j->ws.active, 1, (size_t)g.nt, s->stream)) != cudaSuccess) return e;
   void *stage = nullptr;
   if ((e = dev_alloc(s, &stage, aos_bytes_of(g))) != cudaSuccess) return e;
@@ -197,8 +201,18 @@ struct Segment {
   int n, blocks;
 };
 
-cudaError_t ensure_tables(lgt_server *s, size_t nsweep, size_t nmeas) {
+cudaError_t ensure_tables(lgt_server *s, size_t nsweep, size_t nmeas, size_t nfused) {
   cudaError_t e = cudaSuccess;
+  if (nfused > s->fused_cap) {
+    size_t cap = std::max(nfused, 2 * s->fused_cap);
+    if (s->d_fused) cudaFree(s->d_fused);
+    if (s->h_fused) cudaFreeHost(s->h_fused);
+    s->d_fused = nullptr;
+    s->h_fused = nullptr;
+    if ((e = cudaMalloc(&s->d_fused, cap * sizeof(BatchFused))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&s->h_fused, cap * sizeof(BatchFused))) != cudaSuccess) return e;
+    s->fused_cap = cap;
+  }
   if (nsweep > s->sweep_cap) {
     size_t cap = std::max(nsweep, 2 * s->sweep_cap);
     if (s->d_sweep) cudaFree(s->d_sweep);
@@ -264,10 +278,24 @@ cudaError_t tick(lgt_server *s) {
       i = k;
     }
   }
-  // measurement segments: one per storage format
+  // fused-estimate rows: every job that sweeps this tick (one block per slice)
+  std::vector<BatchFused> frows;
+  int fblocks = 0;
+  for (Job *j : live) {
+    if (j->measure_only) continue;
+    BatchFused r;
+    fill_fused_args(&r.a, j->g, j->ws, j->cfg.gauge, kServerBlock, coulomb_target(j));
+    r.block_begin = fblocks;
+    r.nbx = 0;
+    frows.push_back(r);
+    fblocks += j->g.nt;
+  }
+  // exact-measurement segments (jobs in a measurement-only tick): one per storage format
   std::vector<Segment> msegs;
   std::vector<BatchMeas> mrows;
-  std::vector<Job *> morder(live);
+  std::vector<Job *> morder;
+  for (Job *j : live)
+    if (j->measure_only) morder.push_back(j);
   std::stable_sort(morder.begin(), morder.end(),
                    [](const Job *a, const Job *b) { return a->work_fmt() < b->work_fmt(); });
   for (size_t i = 0; i < morder.size();) {
@@ -286,18 +314,26 @@ cudaError_t tick(lgt_server *s) {
     msegs.push_back(seg);
     i = k;
   }
-  cudaError_t e = ensure_tables(s, rows.size(), mrows.size());
+  cudaError_t e = ensure_tables(s, rows.size(), mrows.size(), frows.size());
   if (e != cudaSuccess) return e;
+  if (!frows.empty()) {
+    memcpy(s->h_fused, frows.data(), frows.size() * sizeof(BatchFused));
+    if ((e = cudaMemcpyAsync(s->d_fused, s->h_fused, frows.size() * sizeof(BatchFused), cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
+      return e;
+  }
   if (!rows.empty()) {
     memcpy(s->h_sweep, rows.data(), rows.size() * sizeof(BatchSweep));
     if ((e = cudaMemcpyAsync(s->d_sweep, s->h_sweep, rows.size() * sizeof(BatchSweep), cudaMemcpyHostToDevice,
                              s->stream)) != cudaSuccess)
       return e;
   }
-  memcpy(s->h_meas, mrows.data(), mrows.size() * sizeof(BatchMeas));
-  if ((e = cudaMemcpyAsync(s->d_meas, s->h_meas, mrows.size() * sizeof(BatchMeas), cudaMemcpyHostToDevice,
-                           s->stream)) != cudaSuccess)
-    return e;
+  if (!mrows.empty()) {
+    memcpy(s->h_meas, mrows.data(), mrows.size() * sizeof(BatchMeas));
+    if ((e = cudaMemcpyAsync(s->d_meas, s->h_meas, mrows.size() * sizeof(BatchMeas), cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
+      return e;
+  }
   // sweeps: for each sweep offset, both parities, every variant
   size_t si = 0;
   for (int sw = 0; sw < kmax; sw++) {
@@ -311,11 +347,15 @@ cudaError_t tick(lgt_server *s) {
         if (e != cudaSuccess) return e;
       }
   }
+  if (!frows.empty()) {
+    e = launch_fused_finish_batch(s->d_fused, (int)frows.size(), fblocks, s->stream);
+    if (e != cudaSuccess) return e;
+  }
   for (const Segment &g : msegs) {
     e = launch_measure_batch(g.fmt, s->d_meas + g.offset, g.n, g.blocks, kServerBlock, s->stream);
     if (e != cudaSuccess) return e;
   }
-  e = cudaMemcpyAsync(s->h_totals, s->d_totals, sizeof(double) * TOT_N * kMaxSlots, cudaMemcpyDeviceToHost,
+  e = cudaMemcpyAsync(s->h_totals, s->d_totals, sizeof(double) * TOT_N * 2 * kMaxSlots, cudaMemcpyDeviceToHost,
                       s->stream);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(s->stream);
@@ -417,11 +457,14 @@ void worker_main(lgt_server *s) {
     std::vector<Job *> finished;
     std::vector<int> fstatus;
     if (e == cudaSuccess) {
+      // the same decisions as lgt_fix: exact measurements (measure-only ticks) at
+      // the start, after promotion and to certify; the sweeps' fused estimate
+      // otherwise
       for (Job *j : s->live) {
-        const double *tot = s->h_totals + (size_t)j->slot * TOT_N;
+        const bool exact = j->measure_only;
+        const double *tot = s->h_totals + ((exact ? 0 : (size_t)kMaxSlots) + j->slot) * TOT_N;
         const double theta = j->theta_of(tot);
-        const bool was_measure_only = j->measure_only;
-        if (!was_measure_only) {
+        if (!exact) {
           if (j->phase == 0) j->sweeps_bulk += j->nthis;
           else j->sweeps_fp64 += j->nthis;
           j->remaining -= j->nthis;
@@ -429,7 +472,7 @@ void worker_main(lgt_server *s) {
         }
         j->measure_only = false;
         if (j->phase == 0) {
-          if (was_measure_only) {
+          if (exact) {
             j->best = theta;
             j->stall = 0;
           } else if (theta < j->best) {
@@ -442,8 +485,12 @@ void worker_main(lgt_server *s) {
             if ((e = promote_job(s, j)) != cudaSuccess) break;
           }
         } else if (theta < j->prm.theta_tol) {
-          finished.push_back(j);
-          fstatus.push_back(LGT_OK);
+          if (exact) {
+            finished.push_back(j);
+            fstatus.push_back(LGT_OK);
+          } else {
+            j->measure_only = true;  // certify next tick
+          }
         } else if (j->remaining <= 0) {
           finished.push_back(j);
           fstatus.push_back(LGT_ENOTCONV);
@@ -514,9 +561,10 @@ extern "C" lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt
     uint64_t thr = UINT64_MAX;  // keep freed blocks cached for the next admissions
     e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_totals, sizeof(double) * TOT_N * kMaxSlots);
-  if (e == cudaSuccess) e = cudaMemset(s->d_totals, 0, sizeof(double) * TOT_N * kMaxSlots);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_totals, sizeof(double) * TOT_N * kMaxSlots);
+  // exact totals in slots [0, kMaxSlots), fused estimates in [kMaxSlots, 2 kMaxSlots)
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_totals, sizeof(double) * TOT_N * 2 * kMaxSlots);
+  if (e == cudaSuccess) e = cudaMemset(s->d_totals, 0, sizeof(double) * TOT_N * 2 * kMaxSlots);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_totals, sizeof(double) * TOT_N * 2 * kMaxSlots);
   if (e != cudaSuccess) {
     lgt_set_error("lgt_server_create: %s", cudaGetErrorString(e));
     if (s->d_totals) cudaFree(s->d_totals);
@@ -626,6 +674,8 @@ extern "C" void lgt_server_destroy(lgt_server *s) {
   if (s->h_sweep) cudaFreeHost(s->h_sweep);
   if (s->d_meas) cudaFree(s->d_meas);
   if (s->h_meas) cudaFreeHost(s->h_meas);
+  if (s->d_fused) cudaFree(s->d_fused);
+  if (s->h_fused) cudaFreeHost(s->h_fused);
   if (s->d_totals) cudaFree(s->d_totals);
   if (s->h_totals) cudaFreeHost(s->h_totals);
   if (s->pool) cudaMemPoolDestroy(s->pool);

@@ -350,13 +350,14 @@ def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo, theta0
         lgt.lgt_destroy(ctx)
     ref = U.copy()
     O.sweeps(ref, 2, gauge=kw["gauge"], algo=kw["algo"], omega=1.7, p=0.8, seed=80)
-    assert np.abs(got - ref).max() < 1e-12
+    assert np.abs(got - ref).max() < tol
 
 
 @pytest.mark.parametrize("gauge", list(GAUGES))
 def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
     """Even far from convergence (FP32-accurate angles) every pair update is a gauge
-    transformation to ~2^-48: plaquettes and unitarity hold to 1e-13 after 20 sweeps."""
+    transformation to ~2^-48: after 20 sweeps plaquettes hold to 1e-13 and unitarity to
+    5e-13 (FP32 storage would be ~1e-7)."""
     U = synth.field(DIMS_RAGGED, 0.5, 14)
     ctx = promoted_ctx(lgt, U, gauge=GAUGES[gauge], omega=1.7)
     try:
@@ -372,7 +373,7 @@ def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
     assert np.abs(half - ref).max() < 5e-6
     assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-13
     e, d = unitarity_error(V)
-    assert e < 1e-13 and d < 1e-13
+    assert e < 5e-13 and d < 5e-13
 
 
 @pytest.mark.parametrize("polish", ["pair", "fp64"])

@@ -136,11 +136,11 @@ def test_server_admission_respects_budget(lgt):
 
 
 def test_server_errors_and_cancel(lgt):
-    srv = lgt.lgt_server_create(64 << 20, 0)
+    srv = lgt.lgt_server_create(256 << 20, 0)
     try:
-        big = lgt.lgt_params_default(dims=(16, 16, 16, 16))
+        big = lgt.lgt_params_default(dims=(32, 32, 32, 32))
         with pytest.raises(lgt.LgtError) as e:
-            lgt.lgt_submit(srv, big, synth.field((16, 16, 16, 16), 0.3, 1))
+            lgt.lgt_submit(srv, big, np.zeros((32, 32, 32, 32, 4, 3, 3), np.complex128))
         assert e.value.status == lgt.LGT_ENOMEM
         bad = lgt.lgt_params_default(dims=(4, 4, 4, 5))
         with pytest.raises(lgt.LgtError) as e:
@@ -153,11 +153,12 @@ def test_server_errors_and_cancel(lgt):
         U = synth.field((4, 4, 4, 4), 0.3, 2)
         U[0, 0, 0, 0, 0] *= 2
         j_bad = lgt.lgt_submit(srv, lgt.lgt_params_default(dims=(4, 4, 4, 4)), U)
-        p_long = lgt.lgt_params_default(dims=(8, 8, 8, 8), theta_tol=1e-30, max_sweeps=10**9, bulk=0)
-        j_long = lgt.lgt_submit(srv, p_long, synth.field((8, 8, 8, 8), 0.3, 3))
-        time.sleep(0.2)
+        # theta cannot reach 1e-300 (FP64 rounding leaves ~1e-32): the job runs until cancelled
+        p_long = lgt.lgt_params_default(dims=(16, 16, 16, 16), theta_tol=1e-300, max_sweeps=2**31 - 1, bulk=0)
+        j_long = lgt.lgt_submit(srv, p_long, synth.field((16, 16, 16, 16), 0.3, 3))
+        time.sleep(0.5)
         lgt.lgt_cancel(srv, j_long)
-        res = wait_all(lgt, srv, [j_bad, j_long], {j_bad: (4, 4, 4, 4), j_long: (8, 8, 8, 8)}, timeout=60)
+        res = wait_all(lgt, srv, [j_bad, j_long], {j_bad: (4, 4, 4, 4), j_long: (16, 16, 16, 16)}, timeout=60)
         assert res[j_bad][0] == lgt.LGT_EINVAL
         assert res[j_long][0] == lgt.LGT_ECANCELLED
     finally:
