@@ -212,6 +212,33 @@ LGT_API lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out);
 /* Release every resource of the context.  NULL is ignored. */
 LGT_API void lgt_destroy(lgt_ctx *ctx);
 
+/* Exact measurement that allocates nothing: F, theta and the average
+ * plaquette (as lgt_measure) and the per-timeslice F_t, theta_t (as
+ * lgt_measure_slices) of links given directly in the public layout in device
+ * memory.  The paper has no counterpart; it exists for callers that cannot
+ * allocate device memory -- an application that hands out every byte of HBM
+ * through its own memory plan or pool, or code that must measure where no
+ * allocation may happen -- and so cannot create a context.
+ * links_device: V*4*9*2 doubles, device memory of the current device.
+ * out_device: at least 8 + 2*N_t doubles of device memory, receiving
+ *   [0] F, [1] theta, [2] plaquette, [3] mean F_t, [4] max theta_t,
+ *   [5] mean theta_t, [6..7] 0, [8 .. 8+N_t) F_t, [8+N_t .. 8+2N_t) theta_t.
+ * cuda_stream: stream to run on (NULL: default stream).  The call is
+ *   asynchronous: synchronise the stream before reading out_device.
+ * Scratch: one fixed array of about 700 KB in device memory, compiled into the
+ *   library (every GPU that loads the library holds it until exit), which
+ *   limits N_t to at most 1024 (larger N_t: LGT_EINVAL).  Every call shares
+ *   it and it keeps the last call's contents; the call clears what must start
+ *   at zero.  Calls that overlap on the GPU (on different streams or devices
+ *   sharing nothing else) race on it on the same device: run them in order.
+ * Set-up: the first call on a device looks up the device address of the
+ *   scratch with that device current; make that first call before any
+ *   stream capture.
+ * Errors: LGT_EINVAL for NULL pointers, odd or too-small dims, N_t > 1024;
+ *   LGT_ECUDA for launch or set-up failures.  Calls no allocator. */
+LGT_API lgt_status lgt_measure_noalloc(const int32_t dims[4], const double *links_device, double *out_device,
+                                       void *cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 /* A continuous-batching server: jobs are admitted while the device memory
  * they need fits hbm_budget_bytes, their lattices stay resident, and one

@@ -89,6 +89,7 @@ _sigs = {
     "lgt_load": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "lgt_get_stats": ([_vp, _P(lgt_stats)], ctypes.c_int),
     "lgt_destroy": ([_vp], None),
+    "lgt_measure_noalloc": ([_P(ctypes.c_int32), _vp, _vp, _vp], ctypes.c_int),
     "lgt_server_create": ([ctypes.c_size_t, ctypes.c_int, _P(_vp)], ctypes.c_int),
     "lgt_submit": ([_vp, _P(lgt_params), _vp, _P(ctypes.c_uint64)], ctypes.c_int),
     "lgt_poll": ([_vp, ctypes.c_uint64, _P(lgt_result), _vp], ctypes.c_int),
@@ -236,6 +237,19 @@ def lgt_get_stats(ctx) -> lgt_stats:
     st = lgt_stats()
     _check(_lib.lgt_get_stats(ctx, ctypes.byref(st)))
     return st
+
+
+def lgt_measure_noalloc(dims, links_device, out_device, stream=None) -> None:
+    """Asynchronous exact measurement of device links into a device buffer of at
+    least 8 + 2*N_t doubles (see include/lgt.h); nothing is allocated."""
+    d = (ctypes.c_int32 * 4)(*[int(x) for x in dims])
+    ptr, on_dev, _ = _links_arg(links_device)
+    if not on_dev:
+        raise TypeError("lgt_measure_noalloc takes device links")
+    if not getattr(out_device, "is_cuda", False):
+        raise TypeError("lgt_measure_noalloc writes a device buffer")
+    optr = out_device.data_ptr()
+    _check(_lib.lgt_measure_noalloc(d, ptr, optr, _stream_arg(stream)))
 
 
 def lgt_destroy(ctx) -> None:
