@@ -1,10 +1,11 @@
 """Benchmark: SU(3) Landau gauge fixing on 32^4 (eps = 0.5, seed 2), FP32 bulk
-sweeps (12-real links, omega = 1.7) + FP64 polish to theta < 1e-14.
+sweeps (12-real links, omega = 1.7) + FP32-pair polish to theta < 1e-14.
 
 One step = the whole hot path on one field: ingest (layout + precision
-conversion), bulk FP32 sweeps with the accumulated transformation G, exact
-theta checks, promotion (G applied to the FP64 input), FP64 polishing sweeps
-to theta < 1e-14, and egress of the fixed field.  The metric is site updates
+conversion), bulk FP32 sweeps with the accumulated transformation G and the
+sweeps' fused theta estimate, promotion (G applied in FP64 to the FP64 input),
+FP32-pair polishing sweeps to theta < 1e-14 certified by the exact FP64
+measurement, and egress of the fixed field.  The metric is site updates
 per second (sweeps x V / time).  Inputs (604 MB complex128 links; 201 MB of
 FP32 working links) are larger than the 129 MB L2, so no L2 flush is needed.
 
@@ -32,8 +33,9 @@ if ROOT not in sys.path:
 
 DIMS = (32, 32, 32, 32)
 EPS, SEED, OMEGA, TOL = 0.5, 2, 1.7, 1e-14
-METRIC = "site updates/s (Landau 32^4, FP32-12 bulk + FP64 polish to theta<1e-14)"
-WORKLOAD = "SU(3) Landau 32^4, eps=0.5, seed 2, OR omega=1.7, FP32-12 bulk + FP64 polish to theta<1e-14"
+METRIC = "site updates/s (Landau 32^4 to theta<1e-14, mixed precision)"
+WORKLOAD = ("SU(3) Landau 32^4, eps=0.5, seed 2, OR omega=1.7, FP32-12 bulk + FP32-pair polish to theta<1e-14 "
+            "(exact FP64 measurement certifies)")
 
 
 def parse():
@@ -44,6 +46,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--workload", default="landau32", choices=["landau32", "coulomb", "landau64", "serve"],
+                    help="landau32 (default; the headline line), or one of the other workloads, each "
+                         "printing its own line")
+    ap.add_argument("--jobs", type=int, default=256, help="serve: number of jobs in the stream")
     return ap.parse_args()
 
 
@@ -120,7 +126,8 @@ class ClockSampler:
 
 def algorithmic_bytes_per_site(kind: str) -> int:
     """Bytes one site update must move: its 8 links in and out, plus G(x) in and
-    out during the FP32 bulk phase (FP32-12 links 48 B, FP64 links 144 B, G 72 B)."""
+    out during the FP32 bulk phase (FP32-12 links 48 B, FP32-18 72 B, FP32-pair
+    and FP64 links 144 B, G 72 B)."""
     if kind == "fp32_12":
         return 16 * 48 + 2 * 72
     if kind == "fp32_18":
@@ -145,6 +152,19 @@ def cpu_baseline(budget_s: float = 12.0):
     dt = time.perf_counter() - t0
     return {"value": n * vol / dt, "unit": "site updates/s", "cores": O.max_threads(), "kind": "oracle",
             "sample": f"{n} FP64 OR sweeps of the 32^4 field ({n * vol} site updates, {dt:.1f} s)"}
+
+
+def aggregate_over_ranks(elapsed_s: float, units: float, device=None):
+    """(max elapsed over ranks, sum of units over ranks); plain values on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed_s, units
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def run_reference(args):
@@ -225,6 +245,7 @@ def run_ours(args):
             stats_kernel["fp64_ms"] += st.sweep_ms[1]
             stats_kernel["fp64_launches"] += st.sweep_launches[1]
             stats_kernel["launches"] += st.launches
+            stats_kernel["launch_config"] = list(st.launch_config)
             sweeps += res.sweeps_bulk + res.sweeps_fp64
             results.append(res.as_dict())
         ev1.record(stream)
@@ -232,16 +253,7 @@ def run_ours(args):
     clocks = clk.summary()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     barrier()
-    t_max = elapsed
-    upd = float(sweeps * vol)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([upd], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        upd = float(u.item())
+    t_max, upd = aggregate_over_ranks(elapsed, float(sweeps * vol), device=f"cuda:{local}")
     value = upd / t_max
 
     # ---- end to end through the C ABI with host buffers (copies timed)
@@ -263,7 +275,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
     peaks, src = measured_peaks()
     kinds = {"fp32_12": (stats_kernel["bulk_ms"], stats_kernel["bulk_launches"]),
-             "fp64": (stats_kernel["fp64_ms"], stats_kernel["fp64_launches"])}
+             "pair": (stats_kernel["fp64_ms"], stats_kernel["fp64_launches"])}
     dom = max(kinds, key=lambda k: kinds[k][0])
     kernels = {}
     for k, (ms, n) in kinds.items():
@@ -272,11 +284,13 @@ def run_ours(args):
         avg_s = ms / 1e3 / n
         bytes_launch = algorithmic_bytes_per_site(k) * (vol // 2)
         kernels[k] = {"avg_launch_us": avg_s * 1e6, "launches": n, "total_ms": ms,
-                      "achieved_gbs": bytes_launch / avg_s / 1e9, "bytes_per_launch": bytes_launch}
+                      "achieved_gbs": bytes_launch / avg_s / 1e9, "bytes_per_launch": bytes_launch,
+                      "launch_config": stats_kernel["launch_config"][0 if k == "fp32_12" else 1]}
     d = kernels[dom]
     roofline = {"bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": d["achieved_gbs"] / peaks["hbm_gbs"], "traffic": None,
-                "kernel": f"half-sweep {dom}", "peak_source": src}
+                "kernel": f"half-sweep {dom}", "peak_source": src,
+                "bytes_per_site_update": algorithmic_bytes_per_site(dom), "units_per_launch": vol // 2}
 
     # ---- all-FP64 time to theta < 1e-14 on the same field, for the ladder comparison
     ttt = {"mixed_s": elapsed / args.steps}
@@ -296,8 +310,9 @@ def run_ours(args):
             s64 = lgt.lgt_get_stats(c64)
             if s64.sweep_launches[1]:
                 avg = s64.sweep_ms[1] / 1e3 / s64.sweep_launches[1]
-                kernels["fp64_only_run"] = {"avg_launch_us": avg * 1e6, "launches": s64.sweep_launches[1],
-                                            "site_updates_per_s": (vol // 2) / avg}
+                kernels["fp64"] = {"avg_launch_us": avg * 1e6, "launches": s64.sweep_launches[1],
+                                   "achieved_gbs": algorithmic_bytes_per_site("fp64") * (vol // 2) / avg / 1e9,
+                                   "site_updates_per_s": (vol // 2) / avg, "run": "all-FP64 comparison"}
         finally:
             lgt.lgt_destroy(c64)
     lgt.lgt_destroy(ctx)
@@ -313,7 +328,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "dims": list(DIMS), "bulk": "fp32_12", "omega": OMEGA,
                            "theta_tol": TOL, "l2": "inputs larger than L2 (604 MB FP64 + 201 MB FP32 links)",
                            "parallelism": f"replicas x{world}"},
-                "sweeps_per_step": {"bulk": last["sweeps_bulk"], "fp64": last["sweeps_fp64"]},
+                "sweeps_per_step": {"bulk_fp32": last["sweeps_bulk"], "polish": last["sweeps_fp64"]},
                 "result": {"F": last["F"], "theta": last["theta"], "plaquette": last["plaquette"]},
                 "time_to_theta_1e-14": ttt, "kernels": kernels, "roofline": roofline, "e2e": e2e,
                 "gpu_launches": stats_kernel["launches"], "clocks": clocks, "cpu_baseline": cpu}
@@ -322,10 +337,201 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------ other workloads
+def _timed_fix(lgt, ctx, src, stream):
+    import torch
+    lgt.lgt_load(ctx, src)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st, res = lgt.lgt_fix(ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, st, res, lgt.lgt_get_stats(ctx)
+
+
+def _kernel_summary(stats, bytes_bulk, bytes_polish, vol):
+    out = {}
+    for idx, (name, b) in enumerate([("bulk", bytes_bulk), ("polish", bytes_polish)]):
+        if stats.sweep_launches[idx]:
+            avg = stats.sweep_ms[idx] / 1e3 / stats.sweep_launches[idx]
+            out[name] = {"avg_launch_us": avg * 1e6, "launches": stats.sweep_launches[idx],
+                         "achieved_gbs": b * (vol // 2) / avg / 1e9}
+    return out
+
+
+def run_coulomb(args):
+    """48^3 x 96 Coulomb gauge: 96 timeslice problems in one launch per half-sweep,
+    per-slice convergence theta_t < 1e-14 (converged slices masked off)."""
+    import torch
+    from paper_1305_3440_gb300 import lgt, synth
+    dims = (96, 48, 48, 48)
+    vol = int(np.prod(dims))
+    U = synth.field(dims, 0.5, 3)
+    dev = torch.from_numpy(U).cuda()
+    del U
+    stream = torch.cuda.Stream()
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_COULOMB, omega=1.7, bulk=lgt.LGT_FP32_12, max_sweeps=50000)
+    ctx = lgt.lgt_create(p, dev, stream=stream)
+    for _ in range(args.warmup):
+        _timed_fix(lgt, ctx, dev, stream)
+    times, res, stats = [], None, None
+    for _ in range(args.steps):
+        t, st, res, stats = _timed_fix(lgt, ctx, dev, stream)
+        assert st == lgt.LGT_OK, res.as_dict()
+        times.append(t)
+    F_t, th_t = lgt.lgt_measure_slices(ctx, dims[0])
+    lgt.lgt_destroy(ctx)
+    # slice-sweeps actually done are fewer than sweeps x V (converged slices are skipped)
+    t = float(np.median(times))
+    sweeps = res.sweeps_bulk + res.sweeps_fp64
+    peaks, src = measured_peaks()
+    kern = _kernel_summary(stats, 12 * 48 + 2 * 72 + 4 * 48, 12 * 144 + 4 * 144, vol)
+    line = {"workload": "coulomb", "metric": "time to max_t theta_t<1e-14 (s)", "value": t, "unit": "s",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "SU(3) Coulomb 48^3x96, eps=0.5, seed 3, OR omega=1.7, FP32-12 bulk + "
+                                   "FP32-pair polish, 96 slices per launch, per-slice convergence",
+                       "block_sizes": "autotuned"},
+            "sweeps": {"bulk_fp32": res.sweeps_bulk, "polish": res.sweeps_fp64},
+            "upper_bound_site_updates_per_s": sweeps * vol / t,
+            "result": {"F_mean": res.F, "theta_max": res.theta, "theta_t_max": float(th_t.max()),
+                       "theta_t_min": float(th_t.min()), "plaquette": res.plaquette},
+            "kernels": kern, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}
+    print(json.dumps(line), flush=True)
+
+
+def run_landau64(args):
+    """64^4 Landau, eps 0.7, seed 5: OR omega 1.8 vs SR p 0.9 through the ladder
+    to theta < 1e-14, and the all-FP64 sweep rate (50 sweeps) for the same field."""
+    import torch
+    from paper_1305_3440_gb300 import lgt, synth
+    dims = (64, 64, 64, 64)
+    vol = int(np.prod(dims))
+    U = synth.field(dims, 0.7, 5)
+    dev = torch.from_numpy(U).cuda()
+    del U
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, kw in [("or_1.8", dict(algo=lgt.LGT_OR, omega=1.8)), ("sr_0.9", dict(algo=lgt.LGT_SR, p=0.9, seed=5))]:
+        p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, max_sweeps=100000, **kw)
+        ctx = lgt.lgt_create(p, dev, stream=stream)
+        t, st, res, stats = _timed_fix(lgt, ctx, dev, stream)
+        lgt.lgt_destroy(ctx)
+        out[name] = {"status": st, "seconds": t, "sweeps_bulk": res.sweeps_bulk, "sweeps_polish": res.sweeps_fp64,
+                     "F": res.F, "theta": res.theta, "site_updates_per_s": (res.sweeps_bulk + res.sweeps_fp64) * vol / t,
+                     "kernels": _kernel_summary(stats, 16 * 48 + 2 * 72, 16 * 144, vol)}
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP64, omega=1.8)
+    ctx = lgt.lgt_create(p, dev, stream=stream)
+    lgt.lgt_sweep(ctx, 2)
+    s0 = lgt.lgt_get_stats(ctx)
+    lgt.lgt_sweep(ctx, 50)
+    s1 = lgt.lgt_get_stats(ctx)
+    lgt.lgt_destroy(ctx)
+    avg = (s1.sweep_ms[1] - s0.sweep_ms[1]) / 1e3 / (s1.sweep_launches[1] - s0.sweep_launches[1])
+    out["fp64_rate"] = {"avg_launch_us": avg * 1e6, "site_updates_per_s": (vol // 2) / avg,
+                        "achieved_gbs": 2304 * (vol // 2) / avg / 1e9}
+    for name in ("or_1.8", "sr_0.9"):
+        n = out[name]["sweeps_bulk"] + out[name]["sweeps_polish"]
+        out[name]["fp64_estimate_s"] = n * 2 * avg
+    peaks, src = measured_peaks()
+    print(json.dumps({"workload": "landau64", "config": {"workload": "SU(3) Landau 64^4, eps=0.7, seed 5"},
+                      "runs": out, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}), flush=True)
+
+
+def serve_specs(n_jobs: int, seed: int = 4):
+    """The served stream: dims uniform over six lattices, Landau/Coulomb 50/50,
+    tol 1e-12/1e-14, eps ~ U[0.3, 0.7], job seed 1000 + j."""
+    rng = np.random.default_rng(seed)
+    shapes = [(16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32), (32, 16, 16, 16), (64, 32, 32, 32),
+              (48, 48, 48, 48)]
+    specs = []
+    for j in range(n_jobs):
+        specs.append(dict(dims=shapes[rng.integers(len(shapes))], gauge=int(rng.integers(2)),
+                          tol=[1e-12, 1e-14][rng.integers(2)], eps=float(rng.uniform(0.3, 0.7)), seed=1000 + j))
+    gaps = rng.exponential(1.0, size=n_jobs)  # unit-rate inter-arrival times, scaled later
+    return specs, gaps
+
+
+def run_serve(args):
+    """Continuous batching: capacity from the whole stream submitted at once, then
+    Poisson arrivals at 80% of it; p50/p99 latency (submit to completion)."""
+    import queue
+    import threading
+    from paper_1305_3440_gb300 import lgt, synth
+    specs, gaps = serve_specs(args.jobs)
+
+    def params(sp):
+        return lgt.lgt_params_default(dims=sp["dims"], gauge=sp["gauge"], theta_tol=sp["tol"],
+                                      bulk=lgt.LGT_FP32_12, max_sweeps=100000)
+
+    def producer(qu):
+        for sp in specs:
+            qu.put((sp, synth.field(sp["dims"], sp["eps"], sp["seed"])))
+        qu.put(None)
+
+    def run_stream(rate):
+        srv = lgt.lgt_server_create(150 << 30, 0)
+        qu = queue.Queue(maxsize=6)
+        threading.Thread(target=producer, args=(qu,), daemon=True).start()
+        ids, lat, status = {}, [], []
+        t0 = time.perf_counter()
+        t_next = t0
+        k = 0
+        pending = set()
+        while True:
+            item = qu.get()
+            if item is None:
+                break
+            sp, U = item
+            if rate:
+                t_next += gaps[k] / rate
+                while time.perf_counter() < t_next:
+                    time.sleep(0.0005)
+            jid = lgt.lgt_submit(srv, params(sp), U)
+            pending.add(jid)
+            k += 1
+            for j in list(pending):
+                st, res = lgt.lgt_poll(srv, j)
+                if st != lgt.LGT_EAGAIN:
+                    pending.discard(j)
+                    lat.append(res.seconds)
+                    status.append(st)
+        while pending:
+            for j in list(pending):
+                st, res = lgt.lgt_poll(srv, j)
+                if st != lgt.LGT_EAGAIN:
+                    pending.discard(j)
+                    lat.append(res.seconds)
+                    status.append(st)
+            time.sleep(0.001)
+        wall = time.perf_counter() - t0
+        lgt.lgt_server_destroy(srv)
+        return wall, np.array(lat), status
+
+    wall_c, lat_c, st_c = run_stream(None)
+    capacity = len(specs) / wall_c
+    rate = 0.8 * capacity
+    wall, lat, st = run_stream(rate)
+    print(json.dumps({"workload": "serve", "metric": "p50/p99 job latency (s) at 80% of capacity",
+                      "jobs": len(specs), "capacity_jobs_per_s": capacity, "offered_rate_jobs_per_s": rate,
+                      "jobs_per_s": len(specs) / wall, "p50_s": float(np.percentile(lat, 50)),
+                      "p99_s": float(np.percentile(lat, 99)), "closed_loop_p50_s": float(np.percentile(lat_c, 50)),
+                      "all_converged": all(x == lgt.LGT_OK for x in st + st_c),
+                      "config": {"workload": "256 jobs, dims in {16^4, 24^4, 32^4, 16^3x32, 32^3x64, 48^4}, "
+                                             "Landau/Coulomb 50/50, tol 1e-12/1e-14, eps U[0.3,0.7], seeds 1000+j, "
+                                             "150 GB budget, FP32-12 bulk + pair polish"}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "coulomb":
+        run_coulomb(args)
+    elif args.workload == "landau64":
+        run_landau64(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

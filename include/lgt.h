@@ -107,9 +107,11 @@ typedef struct {
   int32_t max_sweeps;         /* cap on sweeps of one lgt_fix call (all phases) */
   int32_t check_every;        /* exact theta check every k sweeps */
   int32_t reunit_every;       /* reunitarise FP32 links / G every n sweeps (0: never) */
-  int32_t block_size;         /* threads per block of the sweep kernel (0: autotuned) */
+  int32_t block_size;         /* threads per block of the sweep kernels, 64/128/256 (0: autotuned
+                                 over block sizes and register budgets) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
   int32_t reserved;           /* must be 0 */
+  double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
 } lgt_params;
 
 typedef struct {
@@ -125,7 +127,8 @@ typedef struct {
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR.  dims are zeroed.  Never fails for p != NULL. */
+ * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR, omega_polish 0.
+ * dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);
 
 /* Create a context for one lattice (Sec. 2 problem statement).
@@ -202,6 +205,9 @@ typedef struct {
   int64_t launches;          /* every kernel launch of this context */
   double measure_ms;         /* device time of exact measurements */
   int64_t measure_launches;
+  int32_t launch_config[2];  /* launch configuration of the bulk / polish sweep kernels:
+                                0: 128 threads, <= 255 registers; 1: 128, <= 170;
+                                2: 256, <= 255; 3: 64, <= 128 */
 } lgt_stats;
 
 /* Counters since creation (or the last lgt_load).  Sweep-kernel times come

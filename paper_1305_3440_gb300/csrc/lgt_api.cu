@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -30,6 +31,20 @@ void lgt_set_error(const char *fmt, ...) {
 }
 
 extern "C" const char *lgt_last_error(void) { return g_last_error.c_str(); }
+
+// Host-side fault injection for tests: LGT_FAULT is a comma-separated list of
+// failure names ("alloc": device allocations of contexts and servers fail).
+bool lgt_fault_injected(const char *what) {
+  const char *f = getenv("LGT_FAULT");
+  if (!f || !*f) return false;
+  const size_t n = strlen(what);
+  for (const char *p = f; (p = strstr(p, what)) != nullptr; p += n) {
+    const bool start = p == f || p[-1] == ',';
+    const bool end = p[n] == '\0' || p[n] == ',';
+    if (start && end) return true;
+  }
+  return false;
+}
 
 extern "C" const char *lgt_version(void) { return "liblgt 0.1 (sm_103a)"; }
 
@@ -65,6 +80,7 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->block_size = 0;
   p->polish = LGT_POLISH_PAIR;
   p->reserved = 0;
+  p->omega_polish = 0.0;
   return LGT_OK;
 }
 
@@ -97,6 +113,10 @@ lgt_status lgt_validate_params(const lgt_params *p) {
   }
   if (p->algo == LGT_OR && !(p->omega >= 1.0 && p->omega < 2.0)) {
     lgt_set_error("omega = %g outside [1, 2)", p->omega);
+    return LGT_EINVAL;
+  }
+  if (p->algo == LGT_OR && p->omega_polish != 0.0 && !(p->omega_polish >= 1.0 && p->omega_polish < 2.0)) {
+    lgt_set_error("omega_polish = %g outside [1, 2) (0: same as omega)", p->omega_polish);
     return LGT_EINVAL;
   }
   if (p->algo == LGT_SR && !(p->p >= 0.0 && p->p <= 1.0)) {
@@ -162,7 +182,8 @@ struct lgt_ctx {
   void *ws_base;  // workspace allocation
   Workspace ws;
   double *host;   // pinned readback buffer
-  int block;
+  int cfg_bulk, cfg_polish;  // launch configurations of the bulk / polish sweep kernels
+  int last_block;            // threads per block of the sweeps behind the current fused estimate
   int64_t sweeps_bulk, sweeps_fp64;
   uint64_t sweep_index;  // number of the next sweep (RNG counter)
   SweepCfg cfg;
@@ -250,10 +271,6 @@ static lgt_status read_back(lgt_ctx *c, const void *dev, size_t bytes) {
   return sync_stream(c);
 }
 
-int lgt_pick_block(const lgt_params *p) {
-  if (p->block_size) return p->block_size;
-  return lgt_autotuned_block(p);
-}
 
 // (re)load a field: ingest into FP64 (and the bulk format), G = 1, reset counters
 static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_device) {
@@ -285,6 +302,7 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
     return LGT_EINVAL;
   }
   c->phase = c->prm.bulk == LGT_FP64 ? 1 : 0;
+  c->cfg.omega = c->prm.omega;  // omega_polish takes over at promotion
   c->sweeps_bulk = c->sweeps_fp64 = 0;
   c->sweep_index = c->prm.sweep_offset;
   return LGT_OK;
@@ -303,6 +321,10 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
     lgt_set_error("links is NULL");
     return LGT_EINVAL;
   }
+  if (lgt_fault_injected("alloc")) {
+    lgt_set_error("lgt_create: device allocation failed (injected by LGT_FAULT)");
+    return LGT_ENOMEM;
+  }
   lgt_ctx *c = new lgt_ctx();
   memset((void *)c, 0, sizeof *c);
   c->pending = new std::vector<lgt_ctx::Pending>();
@@ -311,7 +333,6 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   c->g = lgt_make_geom(params->dims);
   c->stream = (cudaStream_t)cuda_stream;
   c->bulk_fmt = fmt_of(params->bulk);
-  c->block = lgt_pick_block(params);
   c->cfg.gauge = params->gauge == LGT_COULOMB ? GAUGE_COULOMB : GAUGE_LANDAU;
   c->cfg.algo = params->algo == LGT_SR ? ALGO_SR : ALGO_OR;
   c->cfg.omega = params->omega;
@@ -338,6 +359,17 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   CTX_CUDA(cudaMemsetAsync(c->ws_base, 0, wsb, c->stream));
   workspace_carve(c->ws_base, g, 64, &c->ws);
   CTX_CUDA(cudaMallocHost(&c->host, 4096 + sizeof(double) * 2 * (size_t)g.nt));
+  // block sizes: given, or timed on the still-empty buffers
+  const int polish_fmt = params->bulk == LGT_FP64 ? (int)FMT_F64 : (params->polish == LGT_POLISH_PAIR ? (int)FMT_PAIR : (int)FMT_F64);
+  c->cfg_bulk = c->cfg_polish = lgt_cfg_of_block(params->block_size);
+  if (!params->block_size) {
+    cudaError_t te = cudaSuccess;
+    if (c->u32) c->cfg_bulk = lgt_tune_sweep(g, c->bulk_fmt, c->cfg, c->u32, c->G, c->ws, c->stream, &te);
+    if (te == cudaSuccess) c->cfg_polish = lgt_tune_sweep(g, polish_fmt, c->cfg, c->u64, nullptr, c->ws, c->stream, &te);
+    CTX_CUDA(te);
+    if (!c->u32) c->cfg_bulk = c->cfg_polish;
+  }
+  c->last_block = lgt_cfg_threads(c->cfg_bulk);
 #undef CTX_CUDA
   st = load_field(c, links, links_on_device);
   if (st != LGT_OK) {
@@ -365,6 +397,8 @@ extern "C" lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out) {
   lgt_status st = sync_stream(ctx);
   if (st != LGT_OK) return st;
   *out = ctx->stats;
+  out->launch_config[0] = ctx->cfg_bulk;
+  out->launch_config[1] = ctx->cfg_polish;
   return LGT_OK;
 }
 
@@ -393,8 +427,10 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
     const int parity = (first_parity + h) & 1;
     int reunit = 0;
     if (c->phase == 0 && c->prm.reunit_every > 0) reunit = ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
-    LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask,
-                               c->block, c->stream));
+    const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
+    LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask, lc,
+                               c->stream));
+    c->last_block = lgt_cfg_threads(lc);
     if (parity == 1) {
       c->sweep_index++;
       if (c->phase == 0) c->sweeps_bulk++;
@@ -467,7 +503,7 @@ static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas
 
 // fused estimate from the last sweep's own K(x) (theta lagged by half a sweep)
 static lgt_status estimate(lgt_ctx *c, double coulomb_target, Meas *m) {
-  LGT_CUDA(launch_fused_finish(c->g, c->ws, c->cfg.gauge, c->block, coulomb_target, c->stream));
+  LGT_CUDA(launch_fused_finish(c->g, c->ws, c->cfg.gauge, c->last_block, coulomb_target, c->stream));
   c->stats.launches++;
   lgt_status st = read_back(c, c->ws.fused_totals, sizeof(double) * TOT_N);
   if (st != LGT_OK) return st;
@@ -514,6 +550,7 @@ static lgt_status promote(lgt_ctx *c) {
   LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_t, c->stream));
   c->stats.launches++;
   c->phase = 1;
+  if (c->prm.omega_polish != 0.0) c->cfg.omega = c->prm.omega_polish;
   if (c->prm.polish == LGT_POLISH_PAIR) {
     LGT_CUDA(launch_convert_pair(c->g, c->u64, 1, c->stream));
     c->stats.launches++;

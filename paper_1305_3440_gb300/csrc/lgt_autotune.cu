@@ -1,7 +1,117 @@
-// lgt_autotune.cu -- block-size choice for the sweep kernel.
-#include "lgt_api_internal.h"
+// lgt_autotune.cu -- launch-configuration choice for the half-sweep kernels.
+//
+// Each sweep kernel is compiled for several launch configurations (threads per
+// block and a register budget, see lgt_internal.h), which trade occupancy
+// against register spills; the best one depends on the kernel variant and the
+// lattice shape.  The tuner times every configuration on a scratch field of
+// unit links (the kernels' work does not depend on the link values), keeps the
+// fastest per (format, gauge, algorithm, dims, GPU) for the life of the
+// process, and, if the environment variable LGT_AUTOTUNE_CACHE names a file,
+// reads earlier results from it and appends new ones.
+#include <cuda_runtime.h>
 
-int lgt_autotuned_block(const lgt_params *p) {
-  (void)p;
-  return 128;
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "lgt_api_internal.h"
+#include "lgt_internal.h"
+
+using namespace lgt;
+
+namespace {
+
+typedef std::tuple<int, int, int, int, int, int, int, std::string> TuneKey;
+
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+bool g_file_loaded = false;
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+  std::string n = prop.name;
+  for (char &ch : n)
+    if (ch == ' ') ch = '_';
+  return n;
+}
+
+void load_file_locked() {
+  if (g_file_loaded) return;
+  g_file_loaded = true;
+  const char *path = getenv("LGT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  int fmt, gauge, algo, nt, n3, n2, n1, block;
+  char name[256];
+  while (fscanf(f, "%d %d %d %d %d %d %d %255s %d", &fmt, &gauge, &algo, &nt, &n3, &n2, &n1, name, &block) == 9)
+    if (block >= 0 && block < LGT_NCFG) g_tuned[TuneKey(fmt, gauge, algo, nt, n3, n2, n1, name)] = block;
+  fclose(f);
+}
+
+void append_file_locked(const TuneKey &k, int block) {
+  const char *path = getenv("LGT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%d %d %d %d %d %d %d %s %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+          std::get<4>(k), std::get<5>(k), std::get<6>(k), std::get<7>(k).c_str(), block);
+  fclose(f);
+}
+
+}  // namespace
+
+int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, void *G, const Workspace &ws,
+                   cudaStream_t st, cudaError_t *err) {
+  *err = cudaSuccess;
+  const TuneKey key(fmt, cfg.gauge, cfg.algo, g.nt, g.n3, g.n2, g.n1, device_name());
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_file_locked();
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaError_t e = launch_fill_unit(fmt, g, links, st);
+  if (e == cudaSuccess && G) e = launch_g_identity(g, G, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // each configuration: 2 warm-up half-sweeps, then the best of 3 timings of 4
+  float best_ms = 1e30f;
+  int best = 0;
+  for (int k = 0; k < LGT_NCFG && e == cudaSuccess; k++) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++)
+      e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st);
+    for (int trial = 0; trial < 3 && e == cudaSuccess; trial++) {
+      e = cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 4 && e == cudaSuccess; rep++)
+        e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = k;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    *err = e;
+    return 0;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tuned.find(key) == g_tuned.end()) {
+    g_tuned[key] = best;
+    append_file_locked(key, best);
+  }
+  return best;
 }

@@ -122,10 +122,26 @@ struct SweepCfg {
   int transform_temporal;
 };
 
-// One half-sweep of parity p on a field of format fmt.  G (nullable) is
-// multiplied by g at every updated site.  use_mask: skip inactive slices.
+// Single-lattice half-sweep kernels, one per (format, gauge, algorithm,
+// launch configuration).  A launch configuration is a block size with a
+// register budget (__launch_bounds__(threads, min blocks per SM)), i.e. an
+// occupancy/spill trade-off; the autotuner times them.
+//   0: 128 threads, <= 255 registers     1: 128 threads, <= 170 registers
+//   2: 256 threads, <= 255 registers     3:  64 threads, <= 128 registers
+constexpr int LGT_NCFG = 4;
+__host__ __device__ constexpr int lgt_cfg_threads(int c) { return c == 2 ? 256 : (c == 3 ? 64 : 128); }
+__host__ __device__ constexpr int lgt_cfg_minblocks(int c) { return c == 1 ? 3 : (c == 3 ? 8 : 1); }
+// configuration for a requested block size (lgt_params.block_size)
+inline int lgt_cfg_of_block(int block) { return block == 256 ? 2 : (block == 64 ? 3 : 0); }
+typedef void (*sweep_fn)(SweepArgs, int);
+sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg);  // FP32-18, FP32-12
+sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg);   // FP64, FP32-pair
+
+// One half-sweep of parity p on a field of format fmt with launch
+// configuration cfg.  G (nullable) is multiplied by g at every updated site.
+// use_mask: skip inactive slices.
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
-                              int parity, unsigned long long sweep, int reunit, int use_mask, int block,
+                              int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
                               cudaStream_t st);
 
 // Fused estimate of F and theta from the last two half-sweeps (each sweep
@@ -160,6 +176,9 @@ cudaError_t launch_g_identity(const Geom &g, void *G, cudaStream_t st);
 // to AoS.  skip_temporal: leave mu = 0 untouched.
 cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, void *u64_out, double *aos_out,
                            int skip_temporal, cudaStream_t st);
+
+// Every link of a field of format fmt set to the unit matrix.
+cudaError_t launch_fill_unit(int fmt, const Geom &g, void *soa, cudaStream_t st);
 
 // In-place conversion of an FP64 field to FP32-pair storage (to_pair = 1)
 // or back (to_pair = 0).

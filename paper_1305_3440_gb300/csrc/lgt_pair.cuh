@@ -98,26 +98,34 @@ __device__ __forceinline__ f2 pair_dot4(f2 c0, f2 x0, f2 c1, f2 x1, f2 c2, f2 x2
   return quick_two_sum(s.hi, e);
 }
 
-// sum of six products of pairs (absolute error ~2^-48 of the largest term)
-__device__ __forceinline__ f2 pair_dot6(const f2 c[6], const f2 x[6]) {
-  float ph[6];
-  float e = 0.0f;
+// base + sum of six products of pairs, in one compensated chain
+__device__ __forceinline__ f2 pair_axpy6(f2 base, const f2 c[6], const f2 x[6]) {
+  float s = base.hi, e = base.lo;
 #pragma unroll
   for (int k = 0; k < 6; k++) {
-    ph[k] = __fmul_rn(c[k].hi, x[k].hi);
-    e = __fadd_rn(e, __fmaf_rn(c[k].hi, x[k].hi, -ph[k]));
+    const float p = __fmul_rn(c[k].hi, x[k].hi);
+    e = __fadd_rn(e, __fmaf_rn(c[k].hi, x[k].hi, -p));
     e = __fmaf_rn(c[k].hi, x[k].lo, e);
     e = __fmaf_rn(c[k].lo, x[k].hi, e);
+    const f2 t = two_sum(s, p);
+    s = t.hi;
+    e = __fadd_rn(e, t.lo);
   }
-  f2 s = two_sum(ph[0], ph[1]);
-  e = __fadd_rn(e, s.lo);
-#pragma unroll
-  for (int k = 2; k < 6; k++) {
-    s = two_sum(s.hi, ph[k]);
-    e = __fadd_rn(e, s.lo);
-  }
-  return quick_two_sum(s.hi, e);
+  return quick_two_sum(s, e);
 }
+
+// Running pair sum with the normalisation deferred to the end.
+struct PairAcc {
+  float s, e;
+};
+
+__device__ __forceinline__ void acc_add_pair(PairAcc &a, f2 x) {
+  const f2 t = two_sum(a.s, x.hi);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, x.lo));
+}
+
+__device__ __forceinline__ f2 acc_value(const PairAcc &a) { return quick_two_sum(a.s, a.e); }
 
 template <>
 struct LinkIO<FMT_PAIR> {
@@ -255,16 +263,55 @@ __device__ __forceinline__ void pair_local_update(f2 W[18], Rot rot[3], float om
   }
 }
 
-// delta = g - 1 for g = R2 R1 R0, in pair precision (g unitary to ~2^-48)
+// complex pair numbers
+struct c2 {
+  f2 re, im;
+};
+
+__device__ __forceinline__ c2 cmul2(c2 a, c2 b) {
+  return {pair_add(pair_mul(a.re, b.re), pair_neg(pair_mul(a.im, b.im))),
+          pair_add(pair_mul(a.re, b.im), pair_mul(a.im, b.re))};
+}
+
+__device__ __forceinline__ c2 cadd2(c2 a, c2 b) { return {pair_add(a.re, b.re), pair_add(a.im, b.im)}; }
+
+// The 2x2 block [[A, B], [C, D]] of a subgroup element r:
+// A = r0 + i r3, B = r2 + i r1, C = -r2 + i r1, D = r0 - i r3.
+__device__ __forceinline__ void rot_block(const Rot &r, c2 &A, c2 &B, c2 &C, c2 &D) {
+  const f2 r0 = pair_add(r.e0, f2{1.0f, 0.0f});
+  A = {r0, r.r3};
+  B = {r.r2, r.r1};
+  C = {pair_neg(r.r2), r.r1};
+  D = {r0, pair_neg(r.r3)};
+}
+
+// delta = g - 1 for g = R2 R1 R0 (subgroups (0,1), (0,2), (1,2)), in pair
+// precision, multiplied out in closed form:
+//   R1 R0 = [[A1 A0, A1 B0, B1], [C0, D0, 0], [C1 A0, C1 B0, D1]]
+//   g     = rows: R1R0 row 0;  A2 (row 1) + B2 (row 2);  C2 (row 1) + D2 (row 2)
 __device__ __forceinline__ void pair_delta(const Rot rot[3], f2 d[18]) {
+  c2 A0, B0, C0, D0, A1, B1, C1, D1, A2, B2, C2, D2;
+  rot_block(rot[0], A0, B0, C0, D0);
+  rot_block(rot[1], A1, B1, C1, D1);
+  rot_block(rot[2], A2, B2, C2, D2);
+  const c2 a1a0 = cmul2(A1, A0), a1b0 = cmul2(A1, B0), c1a0 = cmul2(C1, A0), c1b0 = cmul2(C1, B0);
+  c2 g[3][3];
+  g[0][0] = a1a0;
+  g[0][1] = a1b0;
+  g[0][2] = B1;
+  g[1][0] = cadd2(cmul2(A2, C0), cmul2(B2, c1a0));
+  g[1][1] = cadd2(cmul2(A2, D0), cmul2(B2, c1b0));
+  g[1][2] = cmul2(B2, D1);
+  g[2][0] = cadd2(cmul2(C2, C0), cmul2(D2, c1a0));
+  g[2][1] = cadd2(cmul2(C2, D0), cmul2(D2, c1b0));
+  g[2][2] = cmul2(D2, D1);
 #pragma unroll
-  for (int e = 0; e < 18; e++) d[e] = f2{0.0f, 0.0f};
-  d[LGT_RE(0, 0)] = d[LGT_RE(1, 1)] = d[LGT_RE(2, 2)] = f2{1.0f, 0.0f};
-  rotate_rows<0, 1>(d, rot[0]);
-  rotate_rows<0, 2>(d, rot[1]);
-  rotate_rows<1, 2>(d, rot[2]);
+  for (int i = 0; i < 3; i++)
 #pragma unroll
-  for (int a = 0; a < 3; a++) d[LGT_RE(a, a)] = pair_add(d[LGT_RE(a, a)], f2{-1.0f, 0.0f});
+    for (int j = 0; j < 3; j++) {
+      d[LGT_RE(i, j)] = i == j ? pair_add(g[i][j].re, f2{-1.0f, 0.0f}) : g[i][j].re;
+      d[LGT_IM(i, j)] = g[i][j].im;
+    }
 }
 
 // U <- g U = U + delta U  (pair arithmetic)
@@ -282,7 +329,7 @@ __device__ __forceinline__ void pair_apply_left(f2 u[18], const f2 d[18]) {
         c[2 * k + 1] = pair_neg(d[LGT_IM(i, k)]);
         x[2 * k + 1] = u[LGT_IM(k, j)];
       }
-      r[LGT_RE(i, j)] = pair_add(u[LGT_RE(i, j)], pair_dot6(c, x));
+      r[LGT_RE(i, j)] = pair_axpy6(u[LGT_RE(i, j)], c, x);
 #pragma unroll
       for (int k = 0; k < 3; k++) {  // im: d_re u_im + d_im u_re
         c[2 * k] = d[LGT_RE(i, k)];
@@ -290,7 +337,7 @@ __device__ __forceinline__ void pair_apply_left(f2 u[18], const f2 d[18]) {
         c[2 * k + 1] = d[LGT_IM(i, k)];
         x[2 * k + 1] = u[LGT_RE(k, j)];
       }
-      r[LGT_IM(i, j)] = pair_add(u[LGT_IM(i, j)], pair_dot6(c, x));
+      r[LGT_IM(i, j)] = pair_axpy6(u[LGT_IM(i, j)], c, x);
     }
 #pragma unroll
   for (int e = 0; e < 18; e++) u[e] = r[e];
@@ -311,7 +358,7 @@ __device__ __forceinline__ void pair_apply_right_dag(f2 u[18], const f2 d[18]) {
         c[2 * k + 1] = d[LGT_IM(j, k)];
         x[2 * k + 1] = u[LGT_IM(i, k)];
       }
-      r[LGT_RE(i, j)] = pair_add(u[LGT_RE(i, j)], pair_dot6(c, x));
+      r[LGT_RE(i, j)] = pair_axpy6(u[LGT_RE(i, j)], c, x);
 #pragma unroll
       for (int k = 0; k < 3; k++) {  // im: u_im d_re - u_re d_im
         c[2 * k] = d[LGT_RE(j, k)];
@@ -319,7 +366,7 @@ __device__ __forceinline__ void pair_apply_right_dag(f2 u[18], const f2 d[18]) {
         c[2 * k + 1] = pair_neg(d[LGT_IM(j, k)]);
         x[2 * k + 1] = u[LGT_RE(i, k)];
       }
-      r[LGT_IM(i, j)] = pair_add(u[LGT_IM(i, j)], pair_dot6(c, x));
+      r[LGT_IM(i, j)] = pair_axpy6(u[LGT_IM(i, j)], c, x);
     }
 #pragma unroll
   for (int e = 0; e < 18; e++) u[e] = r[e];

@@ -155,7 +155,7 @@ cudaError_t admit(lgt_server *s, Job *j, int *bad_input) {
   j->phase = p.bulk == LGT_FP64 ? 1 : 0;
   j->cfg.gauge = p.gauge == LGT_COULOMB ? GAUGE_COULOMB : GAUGE_LANDAU;
   j->cfg.algo = p.algo == LGT_SR ? ALGO_SR : ALGO_OR;
-  j->cfg.omega = p.omega;
+  j->cfg.omega = p.omega;  // omega_polish takes over at promotion
   j->cfg.sr_thr = sr_thr_of(p.p);
   j->cfg.seed = p.seed;
   j->cfg.transform_temporal = p.transform_temporal ? 1 : 0;
@@ -388,6 +388,7 @@ cudaError_t promote_job(lgt_server *s, Job *j) {
   const int skip_t = (j->prm.gauge == LGT_COULOMB && !j->prm.transform_temporal) ? 1 : 0;
   cudaError_t e = launch_apply_G(j->g, j->G, j->u64, j->u64, nullptr, skip_t, s->stream);
   j->phase = 1;
+  if (j->prm.omega_polish != 0.0) j->cfg.omega = j->prm.omega_polish;
   if (e == cudaSuccess && j->prm.polish == LGT_POLISH_PAIR) {
     e = launch_convert_pair(j->g, j->u64, 1, s->stream);
     j->phase = 2;
@@ -538,6 +539,10 @@ extern "C" lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt
     return LGT_EINVAL;
   }
   *out = nullptr;
+  if (lgt_fault_injected("alloc")) {
+    lgt_set_error("lgt_server_create: device allocation failed (injected by LGT_FAULT)");
+    return LGT_ENOMEM;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || device < 0 || device >= ndev) {

@@ -1,0 +1,38 @@
+// lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
+// storage), one instantiation per gauge, algorithm and launch configuration.
+#include "lgt_sweep.cuh"
+
+namespace lgt {
+
+template <int FMT, int GAUGE, int ALGO, int CFG>
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs a, int p) {
+  sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+template <int CFG>
+static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
+#define LGT_PICK(F, G, A) \
+  if (fmt == F && gauge == G && algo == A) return k_sweep_f32<F, G, A, CFG>;
+  LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_OR)
+  LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_SR)
+  LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_OR)
+  LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_SR)
+  LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_OR)
+  LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_SR)
+  LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_OR)
+  LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_SR)
+#undef LGT_PICK
+  return nullptr;
+}
+
+sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
+  switch (cfg) {
+    case 0: return pick_cfg<0>(fmt, gauge, algo);
+    case 1: return pick_cfg<1>(fmt, gauge, algo);
+    case 2: return pick_cfg<2>(fmt, gauge, algo);
+    case 3: return pick_cfg<3>(fmt, gauge, algo);
+  }
+  return nullptr;
+}
+
+}  // namespace lgt

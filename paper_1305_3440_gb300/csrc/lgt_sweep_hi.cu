@@ -1,0 +1,41 @@
+// lgt_sweep_hi.cu -- the higher-precision half-sweep kernels: FP64 (every
+// operation in FP64) and FP32-pair (the polishing sweeps), one instantiation
+// per gauge, algorithm and launch configuration.
+#include "lgt_sweep.cuh"
+
+namespace lgt {
+
+template <int GAUGE, int ALGO, int CFG>
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs a, int p) {
+  sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+template <int GAUGE, int ALGO, int CFG>
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_pair(SweepArgs a, int p) {
+  sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+template <int CFG>
+static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
+  if (fmt == FMT_F64) {
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_f64<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_f64<GAUGE_LANDAU, ALGO_OR, CFG>;
+    return algo == ALGO_SR ? k_sweep_f64<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_f64<GAUGE_COULOMB, ALGO_OR, CFG>;
+  }
+  if (fmt == FMT_PAIR) {
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_pair<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_pair<GAUGE_LANDAU, ALGO_OR, CFG>;
+    return algo == ALGO_SR ? k_sweep_pair<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_pair<GAUGE_COULOMB, ALGO_OR, CFG>;
+  }
+  return nullptr;
+}
+
+sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg) {
+  switch (cfg) {
+    case 0: return pick_cfg<0>(fmt, gauge, algo);
+    case 1: return pick_cfg<1>(fmt, gauge, algo);
+    case 2: return pick_cfg<2>(fmt, gauge, algo);
+    case 3: return pick_cfg<3>(fmt, gauge, algo);
+  }
+  return nullptr;
+}
+
+}  // namespace lgt

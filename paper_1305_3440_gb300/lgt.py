@@ -38,7 +38,7 @@ class lgt_params(ctypes.Structure):
                 ("theta_tol", ctypes.c_double), ("theta_switch", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reunit_every", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("polish", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("polish", ctypes.c_int32), ("reserved", ctypes.c_int32), ("omega_polish", ctypes.c_double)]
 
 
 class lgt_result(ctypes.Structure):
@@ -53,12 +53,14 @@ class lgt_result(ctypes.Structure):
 class lgt_stats(ctypes.Structure):
     _fields_ = [("sweep_ms", ctypes.c_double * 2), ("sweep_launches", ctypes.c_int64 * 2),
                 ("site_updates", ctypes.c_int64 * 2), ("launches", ctypes.c_int64),
-                ("measure_ms", ctypes.c_double), ("measure_launches", ctypes.c_int64)]
+                ("measure_ms", ctypes.c_double), ("measure_launches", ctypes.c_int64),
+                ("launch_config", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return dict(sweep_ms=list(self.sweep_ms), sweep_launches=list(self.sweep_launches),
                     site_updates=list(self.site_updates), launches=self.launches,
-                    measure_ms=self.measure_ms, measure_launches=self.measure_launches)
+                    measure_ms=self.measure_ms, measure_launches=self.measure_launches,
+                    launch_config=list(self.launch_config))
 
 
 class LgtError(RuntimeError):

@@ -87,3 +87,30 @@ def test_sr_probability_range(lgt):
 
 def test_version(lgt):
     assert "sm_103a" in lgt.lgt_version()
+
+
+def test_injected_allocation_failure_is_reported(lgt):
+    """LGT_FAULT=alloc makes context and server creation fail with LGT_ENOMEM, with no
+    device work (the failure is made on the host)."""
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np\n"
+        "from paper_1305_3440_gb300 import lgt\n"
+        "p = lgt.lgt_params_default(dims=(4, 4, 4, 4))\n"
+        "try:\n"
+        "    lgt.lgt_create(p, np.zeros((4, 4, 4, 4, 4, 3, 3), np.complex128))\n"
+        "except lgt.LgtError as e:\n"
+        "    assert e.status == lgt.LGT_ENOMEM and 'injected' in lgt.lgt_last_error(), e\n"
+        "else:\n"
+        "    raise SystemExit('no failure')\n"
+        "try:\n"
+        "    lgt.lgt_server_create(1 << 30, 0)\n"
+        "except lgt.LgtError as e:\n"
+        "    assert e.status == lgt.LGT_ENOMEM\n"
+        "else:\n"
+        "    raise SystemExit('no failure')\n"
+        "print('ok')\n")
+    env = dict(os.environ, LGT_FAULT="nan,alloc", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr

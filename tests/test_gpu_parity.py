@@ -441,3 +441,92 @@ def test_full_size_fix_32_properties(lgt, field_32):
     assert np.abs(plaquettes(V) - plaquettes(field_32)).max() < 1e-12
     e, d = unitarity_error(V)
     assert e < 1e-12 and d < 1e-12
+
+
+def test_resume_is_bit_identical(lgt):
+    """A job's state is its links and its sweep counter: stopping after 10 sweeps and
+    restarting from the saved links with sweep_offset = 10 gives the same bits."""
+    dims = (4, 6, 4, 8)
+    U = synth.field(dims, 0.5, 31)
+    kw = dict(dims=dims, algo=lgt.LGT_SR, p=0.8, seed=9)
+    ctx = lgt.lgt_create(lgt.lgt_params_default(**kw), U)
+    try:
+        lgt.lgt_sweep(ctx, 10)
+        mid = lgt.lgt_get_links(ctx, dims)
+        lgt.lgt_sweep(ctx, 5)
+        straight = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    ctx = lgt.lgt_create(lgt.lgt_params_default(sweep_offset=10, **kw), mid)
+    try:
+        lgt.lgt_sweep(ctx, 5)
+        resumed = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert np.array_equal(straight, resumed)
+
+
+# ------------------------------------------------ full size, sampled sites
+def _sampled_half_sweep_check(lgt, U, gauge, n_samples, seed):
+    """Even half-sweep on the GPU (FP32-12 bulk and FP32-pair polish kernels) against
+    the oracle's update of randomly sampled even sites from the same input."""
+    from lattice_np import AXIS
+    dims = U.shape[:4]
+    rng = np.random.default_rng(seed)
+    V = int(np.prod(dims))
+    sites = []
+    while len(sites) < n_samples:
+        s = int(rng.integers(V))
+        t, x3, x2, x1 = np.unravel_index(s, dims)
+        if (t + x3 + x2 + x1) % 2 == 0:
+            sites.append(s)
+    ref = {s: O.site_new_links(U, s, gauge=gauge, omega=1.7) for s in sites}
+    for bulk, promote in [(lgt.LGT_FP32_12, False), (lgt.LGT_FP32_12, True)]:
+        p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=1.7, bulk=bulk, reunit_every=0)
+        ctx = lgt.lgt_create(p, U)
+        try:
+            if promote:
+                lgt.lgt_promote(ctx)
+            lgt.lgt_half_sweep(ctx, 0)
+            got = lgt.lgt_get_working_links(ctx, dims)
+        finally:
+            lgt.lgt_destroy(ctx)
+        worst = 0.0
+        for s in sites:
+            fwd, bwd = ref[s]
+            c = np.unravel_index(s, dims)
+            worst = max(worst, np.abs(got[c] - fwd).max())
+            for mu in range(4):
+                cb = list(c)
+                cb[AXIS[mu]] = (cb[AXIS[mu]] - 1) % dims[AXIS[mu]]
+                worst = max(worst, np.abs(got[tuple(cb)][mu] - bwd[mu]).max())
+        assert worst < 5e-6, (bulk, promote, worst)
+        del got
+
+
+def test_full_size_64x4_sampled(lgt):
+    """SU(3) Landau 64^4, eps = 0.7, seed 5: 400 sampled sites."""
+    U = synth.field((64, 64, 64, 64), 0.7, 5)
+    _sampled_half_sweep_check(lgt, U, O.LANDAU, 400, 1)
+
+
+def test_full_size_coulomb_48x3x96_sampled(lgt):
+    """SU(3) Coulomb 48^3 x 96, eps = 0.5, seed 3 (96 slices in one launch): 400 sampled sites."""
+    U = synth.field((96, 48, 48, 48), 0.5, 3)
+    _sampled_half_sweep_check(lgt, U, O.COULOMB, 400, 2)
+
+
+def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
+    U = near_fixed_8[(O.LANDAU, 1e-12)]
+    ctx = promoted_ctx(lgt, U, omega=1.7, omega_polish=1.9)
+    try:
+        lgt.lgt_sweep(ctx, 2)
+        got = lgt.lgt_get_links(ctx, U.shape[:4])
+    finally:
+        lgt.lgt_destroy(ctx)
+    ref = U.copy()
+    O.sweeps(ref, 2, omega=1.9)
+    assert np.abs(got - ref).max() < 1e-12
+    ref17 = U.copy()
+    O.sweeps(ref17, 2, omega=1.7)
+    assert np.abs(got - ref17).max() > 1e-11
