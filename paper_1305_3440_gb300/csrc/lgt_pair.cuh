@@ -275,41 +275,45 @@ __device__ __forceinline__ c2 cmul2(c2 a, c2 b) {
 
 __device__ __forceinline__ c2 cadd2(c2 a, c2 b) { return {pair_add(a.re, b.re), pair_add(a.im, b.im)}; }
 
-// The 2x2 block [[A, B], [C, D]] of a subgroup element r:
-// A = r0 + i r3, B = r2 + i r1, C = -r2 + i r1, D = r0 - i r3.
-__device__ __forceinline__ void rot_block(const Rot &r, c2 &A, c2 &B, c2 &C, c2 &D) {
-  const f2 r0 = pair_add(r.e0, f2{1.0f, 0.0f});
-  A = {r0, r.r3};
+// The deviation from the identity of a subgroup element r, as its 2x2 block
+// [[a, B], [C, d]] with a = A - 1 = e0 + i r3, B = r2 + i r1, C = -r2 + i r1,
+// d = D - 1 = e0 - i r3 (all small near convergence).
+__device__ __forceinline__ void rot_small(const Rot &r, c2 &a, c2 &B, c2 &C, c2 &d) {
+  a = {r.e0, r.r3};
   B = {r.r2, r.r1};
   C = {pair_neg(r.r2), r.r1};
-  D = {r0, pair_neg(r.r3)};
+  d = {r.e0, pair_neg(r.r3)};
 }
 
 // delta = g - 1 for g = R2 R1 R0 (subgroups (0,1), (0,2), (1,2)), in pair
-// precision, multiplied out in closed form:
-//   R1 R0 = [[A1 A0, A1 B0, B1], [C0, D0, 0], [C1 A0, C1 B0, D1]]
-//   g     = rows: R1R0 row 0;  A2 (row 1) + B2 (row 2);  C2 (row 1) + D2 (row 2)
+// precision, written with the small quantities only so that its error is
+// relative to |delta| (no 1 is added and taken away):
+//   with A = 1 + a, D = 1 + d for each element,
+//   R1 R0 = [[A1 A0, A1 B0, B1], [C0, D0, 0], [C1 A0, C1 B0, D1]],
+//   g row 0 = R1R0 row 0, row 1 = A2 (R1R0 row 1) + B2 (row 2),
+//   row 2 = C2 (row 1) + D2 (row 2).
 __device__ __forceinline__ void pair_delta(const Rot rot[3], f2 d[18]) {
-  c2 A0, B0, C0, D0, A1, B1, C1, D1, A2, B2, C2, D2;
-  rot_block(rot[0], A0, B0, C0, D0);
-  rot_block(rot[1], A1, B1, C1, D1);
-  rot_block(rot[2], A2, B2, C2, D2);
-  const c2 a1a0 = cmul2(A1, A0), a1b0 = cmul2(A1, B0), c1a0 = cmul2(C1, A0), c1b0 = cmul2(C1, B0);
+  c2 a0, B0, C0, d0, a1, B1, C1, d1, a2, B2, C2, d2;
+  rot_small(rot[0], a0, B0, C0, d0);
+  rot_small(rot[1], a1, B1, C1, d1);
+  rot_small(rot[2], a2, B2, C2, d2);
+  const c2 C1A0 = cadd2(C1, cmul2(C1, a0));  // C1 A0
+  const c2 C1B0 = cmul2(C1, B0);
   c2 g[3][3];
-  g[0][0] = a1a0;
-  g[0][1] = a1b0;
+  g[0][0] = cadd2(cadd2(a1, a0), cmul2(a1, a0));                      // A1 A0 - 1
+  g[0][1] = cadd2(B0, cmul2(a1, B0));                                  // A1 B0
   g[0][2] = B1;
-  g[1][0] = cadd2(cmul2(A2, C0), cmul2(B2, c1a0));
-  g[1][1] = cadd2(cmul2(A2, D0), cmul2(B2, c1b0));
-  g[1][2] = cmul2(B2, D1);
-  g[2][0] = cadd2(cmul2(C2, C0), cmul2(D2, c1a0));
-  g[2][1] = cadd2(cmul2(C2, D0), cmul2(D2, c1b0));
-  g[2][2] = cmul2(D2, D1);
+  g[1][0] = cadd2(cadd2(C0, cmul2(a2, C0)), cmul2(B2, C1A0));          // A2 C0 + B2 C1 A0
+  g[1][1] = cadd2(cadd2(cadd2(a2, d0), cmul2(a2, d0)), cmul2(B2, C1B0));  // A2 D0 + B2 C1 B0 - 1
+  g[1][2] = cadd2(B2, cmul2(B2, d1));                                  // B2 D1
+  g[2][0] = cadd2(cadd2(cmul2(C2, C0), C1A0), cmul2(d2, C1A0));        // C2 C0 + D2 C1 A0
+  g[2][1] = cadd2(cadd2(C2, cmul2(C2, d0)), cadd2(C1B0, cmul2(d2, C1B0)));  // C2 D0 + D2 C1 B0
+  g[2][2] = cadd2(cadd2(d2, d1), cmul2(d2, d1));                      // D2 D1 - 1
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      d[LGT_RE(i, j)] = i == j ? pair_add(g[i][j].re, f2{-1.0f, 0.0f}) : g[i][j].re;
+      d[LGT_RE(i, j)] = g[i][j].re;
       d[LGT_IM(i, j)] = g[i][j].im;
     }
 }

@@ -356,8 +356,9 @@ def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo, theta0
 @pytest.mark.parametrize("gauge", list(GAUGES))
 def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
     """Even far from convergence (FP32-accurate angles) every pair update is a gauge
-    transformation to ~2^-48: after 20 sweeps plaquettes hold to 1e-13 and unitarity to
-    5e-13 (FP32 storage would be ~1e-7)."""
+    transformation up to the ~2^-48 rounding of pair storage (~1e-14 per update, a
+    random walk): after 20 sweeps plaquettes and unitarity hold to 3e-13 (FP32
+    storage would give ~1e-7)."""
     U = synth.field(DIMS_RAGGED, 0.5, 14)
     ctx = promoted_ctx(lgt, U, gauge=GAUGES[gauge], omega=1.7)
     try:
@@ -371,9 +372,9 @@ def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
     ref = U.copy()
     O.half_sweep(ref, 0, gauge=GAUGES[gauge], omega=1.7)
     assert np.abs(half - ref).max() < 5e-6
-    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-13
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 3e-13
     e, d = unitarity_error(V)
-    assert e < 5e-13 and d < 5e-13
+    assert e < 3e-13 and d < 3e-13
 
 
 @pytest.mark.parametrize("polish", ["pair", "fp64"])
@@ -425,8 +426,10 @@ def test_full_size_one_sweep_32(lgt, field_32, bulk):
 
 
 def test_full_size_fix_32_properties(lgt, field_32):
-    """The benchmark's run (FP32-12 bulk + FP64 polish to 1e-14): the oracle certifies
-    theta < 1e-14 on the returned field; every plaquette and unitarity are kept."""
+    """The benchmark's run (FP32-12 bulk + FP32-pair polish to 1e-14): the oracle
+    certifies theta < 1e-14 on the returned field; every plaquette and unitarity are
+    kept to 3e-12 (pair storage rounds each link to ~2^-48 per update: ~1e-13 after
+    the ~1000 polish updates of a link, ~1e-12 at the extreme of 4e7 entries)."""
     dims = (32, 32, 32, 32)
     p = lgt.lgt_params_default(dims=dims, omega=1.7, bulk=lgt.LGT_FP32_12, max_sweeps=20000)
     ctx = lgt.lgt_create(p, field_32)
@@ -438,9 +441,9 @@ def test_full_size_fix_32_properties(lgt, field_32):
     assert st == lgt.LGT_OK and res.theta < 1e-14
     m = O.measure(V)
     assert m["theta"] < 1e-14 and abs(m["F"] - res.F) < 1e-12
-    assert np.abs(plaquettes(V) - plaquettes(field_32)).max() < 1e-12
+    assert np.abs(plaquettes(V) - plaquettes(field_32)).max() < 3e-12
     e, d = unitarity_error(V)
-    assert e < 1e-12 and d < 1e-12
+    assert e < 3e-12 and d < 3e-12
 
 
 def test_resume_is_bit_identical(lgt):
