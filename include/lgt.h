@@ -127,8 +127,9 @@ typedef struct {
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR, omega_polish 0.
- * dims are zeroed.  Never fails for p != NULL. */
+ * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR, omega_polish 1.3
+ * (after promotion the residual is short-wavelength noise, which a smaller
+ * omega removes fastest).  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);
 
 /* Create a context for one lattice (Sec. 2 problem statement).
@@ -201,7 +202,7 @@ LGT_API lgt_status lgt_load(lgt_ctx *ctx, const double *links, int links_on_devi
 typedef struct {
   double sweep_ms[2];        /* device time of the sweep kernels: [0] bulk FP32, [1] FP64 */
   int64_t sweep_launches[2]; /* half-sweep kernel launches in each precision */
-  int64_t site_updates[2];   /* site updates done in each precision */
+  int64_t site_updates[2];   /* site updates done in each precision (converged Coulomb slices excluded) */
   int64_t launches;          /* every kernel launch of this context */
   double measure_ms;         /* device time of exact measurements */
   int64_t measure_launches;

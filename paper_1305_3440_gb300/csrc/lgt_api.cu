@@ -80,7 +80,7 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->block_size = 0;
   p->polish = LGT_POLISH_PAIR;
   p->reserved = 0;
-  p->omega_polish = 0.0;
+  p->omega_polish = 1.3;
   return LGT_OK;
 }
 
@@ -183,6 +183,7 @@ struct lgt_ctx {
   Workspace ws;
   double *host;   // pinned readback buffer
   int cfg_bulk, cfg_polish;  // launch configurations of the bulk / polish sweep kernels
+  int active_slices;         // slices updated by masked sweeps (from the last estimate/measurement)
   int last_block;            // threads per block of the sweeps behind the current fused estimate
   int64_t sweeps_bulk, sweeps_fp64;
   uint64_t sweep_index;  // number of the next sweep (RNG counter)
@@ -302,6 +303,7 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
     return LGT_EINVAL;
   }
   c->phase = c->prm.bulk == LGT_FP64 ? 1 : 0;
+  c->active_slices = g.nt;
   c->cfg.omega = c->prm.omega;  // omega_polish takes over at promotion
   c->sweeps_bulk = c->sweeps_fp64 = 0;
   c->sweep_index = c->prm.sweep_offset;
@@ -440,7 +442,8 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
   batch_end(c, bt);
   c->stats.sweep_launches[kind] += n_half;
   c->stats.launches += n_half;
-  c->stats.site_updates[kind] += (int64_t)n_half * (int64_t)c->g.vh;
+  const int64_t slices = use_mask ? c->active_slices : c->g.nt;
+  c->stats.site_updates[kind] += (int64_t)n_half * (int64_t)c->g.vs_half * slices;
   return LGT_OK;
 }
 
@@ -498,6 +501,7 @@ static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas
   lgt_status st = read_back(c, c->ws.totals, sizeof(double) * TOT_N);
   if (st != LGT_OK) return st;
   fill_meas(c, c->host, m);
+  c->active_slices = m->active;
   return LGT_OK;
 }
 
@@ -508,6 +512,7 @@ static lgt_status estimate(lgt_ctx *c, double coulomb_target, Meas *m) {
   lgt_status st = read_back(c, c->ws.fused_totals, sizeof(double) * TOT_N);
   if (st != LGT_OK) return st;
   fill_meas(c, c->host, m);
+  c->active_slices = m->active;
   return LGT_OK;
 }
 
@@ -624,6 +629,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   }
   // all slices active again for later calls
   LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)c->g.nt, c->stream));
+  c->active_slices = c->g.nt;
   Meas fin;
   st = measure(c, 1, -1.0, &fin);
   if (st != LGT_OK) return st;
