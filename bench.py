@@ -127,11 +127,11 @@ class ClockSampler:
 def algorithmic_bytes_per_site(kind: str) -> int:
     """Bytes one site update must move: its 8 links in and out, plus G(x) in and
     out during the FP32 bulk phase (FP32-12 links 48 B, FP32-18 72 B, FP32-pair
-    and FP64 links 144 B, G 72 B)."""
+    and FP64 links 144 B, G stored as 2 rows: 48 B)."""
     if kind == "fp32_12":
-        return 16 * 48 + 2 * 72
+        return 16 * 48 + 2 * 48
     if kind == "fp32_18":
-        return 16 * 72 + 2 * 72
+        return 16 * 72 + 2 * 48
     return 16 * 144
 
 
@@ -393,7 +393,7 @@ def run_coulomb(args):
     t = float(np.median(times))
     updates = stats.site_updates[0] + stats.site_updates[1]
     peaks, src = measured_peaks()
-    kern = _kernel_summary(stats, 12 * 48 + 2 * 72 + 4 * 48, 12 * 144 + 4 * 144, vol)
+    kern = _kernel_summary(stats, 12 * 48 + 2 * 48 + 4 * 48, 12 * 144 + 4 * 144, vol)
     line = {"workload": "coulomb", "metric": "time to max_t theta_t<1e-14 (s)", "value": t, "unit": "s",
             "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "SU(3) Coulomb 48^3x96, eps=0.5, seed 3, OR omega=1.7, FP32-12 bulk + "
@@ -426,7 +426,7 @@ def run_landau64(args):
         lgt.lgt_destroy(ctx)
         out[name] = {"status": st, "seconds": t, "sweeps_bulk": res.sweeps_bulk, "sweeps_polish": res.sweeps_fp64,
                      "F": res.F, "theta": res.theta, "site_updates_per_s": (res.sweeps_bulk + res.sweeps_fp64) * vol / t,
-                     "kernels": _kernel_summary(stats, 16 * 48 + 2 * 72, 16 * 144, vol)}
+                     "kernels": _kernel_summary(stats, 16 * 48 + 2 * 48, 16 * 144, vol)}
     p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP64, omega=1.8)
     ctx = lgt.lgt_create(p, dev, stream=stream)
     lgt.lgt_sweep(ctx, 2)

@@ -190,34 +190,29 @@ struct LinkIO<FMT_F32_12> {
 };
 
 // The accumulated gauge transformation G(x) of the FP32 phase: one SU(3) per
-// site, FP32, 4 float4 chunks + 1 float2 per parity stream.
+// site in FP32, stored as rows 0 and 1 (3 float4 chunks per parity stream);
+// row 2 = conj(row0 x row1) is rebuilt on load.
 struct GIO {
   static __device__ __forceinline__ void load(const void *base, int vh, int p, int i, float m[18]) {
-    const float4 *b4 = reinterpret_cast<const float4 *>(base) + (size_t)(p * 4) * vh + i;
+    const float4 *b4 = reinterpret_cast<const float4 *>(base) + (size_t)(p * 3) * vh + i;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < 3; k++) {
       float4 v = __ldg(b4 + (size_t)k * vh);
       m[4 * k] = v.x;
       m[4 * k + 1] = v.y;
       m[4 * k + 2] = v.z;
       m[4 * k + 3] = v.w;
     }
-    const float2 *b2 = reinterpret_cast<const float2 *>(reinterpret_cast<const float4 *>(base) + (size_t)8 * vh) +
-                       (size_t)p * vh + i;
-    float2 w = __ldg(b2);
-    m[16] = w.x;
-    m[17] = w.y;
+    rebuild_row2(m);
   }
   static __device__ __forceinline__ void store(void *base, int vh, int p, int i, const float m[18]) {
-    float4 *b4 = reinterpret_cast<float4 *>(base) + (size_t)(p * 4) * vh + i;
+    float4 *b4 = reinterpret_cast<float4 *>(base) + (size_t)(p * 3) * vh + i;
 #pragma unroll
-    for (int k = 0; k < 4; k++) b4[(size_t)k * vh] = make_float4(m[4 * k], m[4 * k + 1], m[4 * k + 2], m[4 * k + 3]);
-    float2 *b2 = reinterpret_cast<float2 *>(reinterpret_cast<float4 *>(base) + (size_t)8 * vh) + (size_t)p * vh + i;
-    *b2 = make_float2(m[16], m[17]);
+    for (int k = 0; k < 3; k++) b4[(size_t)k * vh] = make_float4(m[4 * k], m[4 * k + 1], m[4 * k + 2], m[4 * k + 3]);
   }
 };
 
-__host__ __device__ __forceinline__ size_t g_bytes(int vh) { return (size_t)vh * 2 * (4 * 16 + 8); }
+__host__ __device__ __forceinline__ size_t g_bytes(int vh) { return (size_t)vh * 2 * 3 * 16; }
 
 __host__ __device__ __forceinline__ size_t field_bytes(int fmt, int vh) {
   return (size_t)vh * 2 * link_bytes_per_half_site(fmt);

@@ -312,6 +312,7 @@ def near_fixed_8():
 
 
 def promoted_ctx(lgt, U, **kw):
+    kw.setdefault("omega_polish", 0.0)  # polish at the same omega as the oracle below
     p = lgt.lgt_params_default(dims=U.shape[:4], bulk=lgt.LGT_FP32_12, polish=lgt.LGT_POLISH_PAIR, **kw)
     ctx = lgt.lgt_create(p, U)
     lgt.lgt_promote(ctx)  # G = 1: the pair field is the input to ~2^-48
@@ -485,7 +486,8 @@ def _sampled_half_sweep_check(lgt, U, gauge, n_samples, seed):
             sites.append(s)
     ref = {s: O.site_new_links(U, s, gauge=gauge, omega=1.7) for s in sites}
     for bulk, promote in [(lgt.LGT_FP32_12, False), (lgt.LGT_FP32_12, True)]:
-        p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=1.7, bulk=bulk, reunit_every=0)
+        p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=1.7, omega_polish=0.0, bulk=bulk,
+                                   reunit_every=0)
         ctx = lgt.lgt_create(p, U)
         try:
             if promote:
