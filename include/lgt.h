@@ -251,7 +251,13 @@ LGT_API lgt_status lgt_measure_noalloc(const int32_t dims[4], const double *link
  * they need fits hbm_budget_bytes, their lattices stay resident, and one
  * worker thread advances every live job through the sweep kernels, checking
  * each job's exact theta every check_every sweeps and retiring it when
- * converged (Sec. 4 driver, per job).  device: CUDA device ordinal. */
+ * converged (Sec. 4 driver, per job).  device: CUDA device ordinal.
+ * One tick = up to check_every sweeps of every live job (one batched launch
+ * per sweep, parity and kernel variant) plus one batched theta check.  A tick
+ * whose launch shape repeats the previous tick's is captured once into a CUDA
+ * graph and replayed for as long as the shape lasts (at most 16 shapes kept);
+ * the environment variable LGT_SERVER_GRAPHS=0, read at creation, issues
+ * every tick's launches directly instead.  Results do not depend on it. */
 LGT_API lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt_server **out);
 
 /* Queue a job; links (host, public layout) are copied before return.
@@ -269,6 +275,12 @@ LGT_API lgt_status lgt_cancel(lgt_server *s, uint64_t job_id);
 
 /* Server counters: jobs done, jobs live, device bytes in use. */
 LGT_API lgt_status lgt_server_stats(lgt_server *s, uint64_t *jobs_done, uint64_t *jobs_live, size_t *bytes_in_use);
+
+/* Worker counters since creation: ticks run, ticks replayed from a captured
+ * graph, graphs captured, and kernel launches the ticks issued (directly or
+ * inside graphs).  Any pointer may be NULL. */
+LGT_API lgt_status lgt_server_counters(lgt_server *s, uint64_t *ticks, uint64_t *graph_launches,
+                                       uint64_t *graph_captures, uint64_t *kernel_launches);
 
 /* Stop the worker (queued jobs are cancelled) and release everything. */
 LGT_API void lgt_server_destroy(lgt_server *s);

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -89,6 +90,15 @@ struct Job {
 
 size_t aos_bytes_of(const Geom &g) { return (size_t)g.vh * 2 * 4 * 18 * sizeof(double); }
 
+constexpr size_t kMaxGraphs = 16;
+
+// One captured tick: its launch shape and executable graph.
+struct TickGraph {
+  std::vector<long long> sig;
+  cudaGraphExec_t exec;
+  uint64_t used;
+};
+
 }  // namespace
 
 struct lgt_server {
@@ -112,6 +122,11 @@ struct lgt_server {
   BatchMeas *d_meas = nullptr, *h_meas = nullptr;
   BatchFused *d_fused = nullptr, *h_fused = nullptr;
   size_t sweep_cap = 0, meas_cap = 0, fused_cap = 0;
+  // captured ticks (worker-owned) and counters (read under mu)
+  std::vector<TickGraph> graphs;
+  std::vector<long long> prev_sig;
+  bool use_graphs = true;
+  uint64_t ticks = 0, graph_launches = 0, graph_captures = 0, kernel_launches = 0;
   cudaError_t fatal = cudaSuccess;
 };
 
@@ -201,8 +216,15 @@ struct Segment {
   int n, blocks;
 };
 
+void drop_graphs(lgt_server *s) {
+  for (TickGraph &t : s->graphs) cudaGraphExecDestroy(t.exec);
+  s->graphs.clear();
+  s->prev_sig.clear();
+}
+
 cudaError_t ensure_tables(lgt_server *s, size_t nsweep, size_t nmeas, size_t nfused) {
   cudaError_t e = cudaSuccess;
+  if (nfused > s->fused_cap || nsweep > s->sweep_cap || nmeas > s->meas_cap) drop_graphs(s);  // tables move
   if (nfused > s->fused_cap) {
     size_t cap = std::max(nfused, 2 * s->fused_cap);
     if (s->d_fused) cudaFree(s->d_fused);
@@ -234,6 +256,69 @@ cudaError_t ensure_tables(lgt_server *s, size_t nsweep, size_t nmeas, size_t nfu
     s->meas_cap = cap;
   }
   return e;
+}
+
+// The launch shape of one tick: which batched launches, over how many rows
+// and blocks.  The rows themselves live in the pinned host tables and are
+// copied to the device by the tick's first operations, so two ticks with the
+// same shape run the same operations on different table contents.
+struct TickPlan {
+  int kmax, hi_slot, fblocks;
+  size_t nrows, nmrows, nfrows;
+  std::vector<Segment> segs, msegs;
+
+  std::vector<long long> signature() const {
+    std::vector<long long> v = {kmax, hi_slot, fblocks, (long long)nrows, (long long)nmrows, (long long)nfrows};
+    for (const std::vector<Segment> *L : {&segs, &msegs})
+      for (const Segment &g : *L) {
+        const long long f[] = {g.fmt, g.gauge, g.algo, g.s, (long long)g.offset, g.n, g.blocks};
+        v.insert(v.end(), f, f + 7);
+      }
+    return v;
+  }
+  long long launches() const { return 2 * (long long)segs.size() + (nfrows ? 1 : 0) + (long long)msegs.size(); }
+};
+
+// Stream operations of one tick: table uploads, the batched sweeps (for each
+// sweep offset both parities, every kernel variant), the batched fused
+// estimate, the batched exact measurements, and the totals read-back.
+cudaError_t issue(lgt_server *s, const TickPlan &P) {
+  cudaError_t e = cudaSuccess;
+  if (P.nfrows &&
+      (e = cudaMemcpyAsync(s->d_fused, s->h_fused, P.nfrows * sizeof(BatchFused), cudaMemcpyHostToDevice,
+                           s->stream)) != cudaSuccess)
+    return e;
+  if (P.nrows &&
+      (e = cudaMemcpyAsync(s->d_sweep, s->h_sweep, P.nrows * sizeof(BatchSweep), cudaMemcpyHostToDevice,
+                           s->stream)) != cudaSuccess)
+    return e;
+  if (P.nmrows &&
+      (e = cudaMemcpyAsync(s->d_meas, s->h_meas, P.nmrows * sizeof(BatchMeas), cudaMemcpyHostToDevice,
+                           s->stream)) != cudaSuccess)
+    return e;
+  size_t si = 0;
+  for (int sw = 0; sw < P.kmax; sw++) {
+    const size_t first = si;
+    while (si < P.segs.size() && P.segs[si].s == sw) si++;
+    for (int parity = 0; parity < 2; parity++)
+      for (size_t q = first; q < si; q++) {
+        const Segment &g = P.segs[q];
+        e = launch_half_sweep_batch(g.fmt, g.gauge, g.algo, s->d_sweep + g.offset, g.n, g.blocks, parity, sw,
+                                    kServerBlock, s->stream);
+        if (e != cudaSuccess) return e;
+      }
+  }
+  if (P.nfrows && (e = launch_fused_finish_batch(s->d_fused, (int)P.nfrows, P.fblocks, s->stream)) != cudaSuccess)
+    return e;
+  for (const Segment &g : P.msegs)
+    if ((e = launch_measure_batch(g.fmt, s->d_meas + g.offset, g.n, g.blocks, kServerBlock, s->stream)) !=
+        cudaSuccess)
+      return e;
+  // exact totals of slots [0, hi_slot), then the fused estimates of the same slots
+  const size_t n = sizeof(double) * TOT_N * (size_t)P.hi_slot;
+  if ((e = cudaMemcpyAsync(s->h_totals, s->d_totals, n, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess) return e;
+  return cudaMemcpyAsync(s->h_totals + (size_t)kMaxSlots * TOT_N, s->d_totals + (size_t)kMaxSlots * TOT_N, n,
+                         cudaMemcpyDeviceToHost, s->stream);
 }
 
 // One tick over the live jobs: sweeps, measurement, read back.
@@ -314,49 +399,49 @@ cudaError_t tick(lgt_server *s) {
     msegs.push_back(seg);
     i = k;
   }
+  int hi_slot = 0;  // totals of slots [0, hi_slot) come back to the host
+  for (Job *j : live) hi_slot = std::max(hi_slot, j->slot + 1);
   cudaError_t e = ensure_tables(s, rows.size(), mrows.size(), frows.size());
   if (e != cudaSuccess) return e;
-  if (!frows.empty()) {
-    memcpy(s->h_fused, frows.data(), frows.size() * sizeof(BatchFused));
-    if ((e = cudaMemcpyAsync(s->d_fused, s->h_fused, frows.size() * sizeof(BatchFused), cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess)
-      return e;
-  }
-  if (!rows.empty()) {
-    memcpy(s->h_sweep, rows.data(), rows.size() * sizeof(BatchSweep));
-    if ((e = cudaMemcpyAsync(s->d_sweep, s->h_sweep, rows.size() * sizeof(BatchSweep), cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess)
-      return e;
-  }
-  if (!mrows.empty()) {
-    memcpy(s->h_meas, mrows.data(), mrows.size() * sizeof(BatchMeas));
-    if ((e = cudaMemcpyAsync(s->d_meas, s->h_meas, mrows.size() * sizeof(BatchMeas), cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess)
-      return e;
-  }
-  // sweeps: for each sweep offset, both parities, every variant
-  size_t si = 0;
-  for (int sw = 0; sw < kmax; sw++) {
-    size_t first = si;
-    while (si < segs.size() && segs[si].s == sw) si++;
-    for (int parity = 0; parity < 2; parity++)
-      for (size_t q = first; q < si; q++) {
-        const Segment &g = segs[q];
-        e = launch_half_sweep_batch(g.fmt, g.gauge, g.algo, s->d_sweep + g.offset, g.n, g.blocks, parity, sw,
-                                    kServerBlock, s->stream);
-        if (e != cudaSuccess) return e;
-      }
-  }
-  if (!frows.empty()) {
-    e = launch_fused_finish_batch(s->d_fused, (int)frows.size(), fblocks, s->stream);
+  if (!frows.empty()) memcpy(s->h_fused, frows.data(), frows.size() * sizeof(BatchFused));
+  if (!rows.empty()) memcpy(s->h_sweep, rows.data(), rows.size() * sizeof(BatchSweep));
+  if (!mrows.empty()) memcpy(s->h_meas, mrows.data(), mrows.size() * sizeof(BatchMeas));
+  TickPlan P{kmax, hi_slot, fblocks, rows.size(), mrows.size(), frows.size(), std::move(segs), std::move(msegs)};
+  const std::vector<long long> sig = P.signature();
+  s->ticks++;
+  s->kernel_launches += P.launches();
+  TickGraph *hit = nullptr;
+  for (TickGraph &t : s->graphs)
+    if (t.sig == sig) hit = &t;
+  if (!hit && s->use_graphs && sig == s->prev_sig) {
+    // the same launch shape two ticks in a row: capture it once, replay it while it lasts
+    if ((e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    const cudaError_t ei = issue(s, P);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s->stream, &graph);
+    if (ei != cudaSuccess) e = ei;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
+    if (s->graphs.size() >= kMaxGraphs) {
+      auto lru = std::min_element(s->graphs.begin(), s->graphs.end(),
+                                  [](const TickGraph &x, const TickGraph &y) { return x.used < y.used; });
+      cudaGraphExecDestroy(lru->exec);
+      s->graphs.erase(lru);
+    }
+    s->graphs.push_back({sig, exec, 0});
+    s->graph_captures++;
+    hit = &s->graphs.back();
   }
-  for (const Segment &g : msegs) {
-    e = launch_measure_batch(g.fmt, s->d_meas + g.offset, g.n, g.blocks, kServerBlock, s->stream);
-    if (e != cudaSuccess) return e;
+  s->prev_sig = sig;
+  if (hit) {
+    hit->used = s->ticks;
+    s->graph_launches++;
+    e = cudaGraphLaunch(hit->exec, s->stream);
+  } else {
+    e = issue(s, P);
   }
-  e = cudaMemcpyAsync(s->h_totals, s->d_totals, sizeof(double) * TOT_N * 2 * kMaxSlots, cudaMemcpyDeviceToHost,
-                      s->stream);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(s->stream);
 }
@@ -550,6 +635,8 @@ extern "C" lgt_status lgt_server_create(size_t hbm_budget_bytes, int device, lgt
     return e == cudaSuccess ? LGT_EINVAL : LGT_ECUDA;
   }
   lgt_server *s = new lgt_server();
+  const char *gv = getenv("LGT_SERVER_GRAPHS");  // "0": issue every tick's launches directly
+  s->use_graphs = !(gv && gv[0] == '0');
   s->budget = hbm_budget_bytes;
   s->device = device;
   e = cudaSetDevice(device);
@@ -666,6 +753,20 @@ extern "C" lgt_status lgt_server_stats(lgt_server *s, uint64_t *jobs_done, uint6
   return s->fatal == cudaSuccess ? LGT_OK : LGT_ECUDA;
 }
 
+extern "C" lgt_status lgt_server_counters(lgt_server *s, uint64_t *ticks, uint64_t *graph_launches,
+                                          uint64_t *graph_captures, uint64_t *kernel_launches) {
+  if (!s) {
+    lgt_set_error("lgt_server_counters: NULL server");
+    return LGT_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (ticks) *ticks = s->ticks;
+  if (graph_launches) *graph_launches = s->graph_launches;
+  if (graph_captures) *graph_captures = s->graph_captures;
+  if (kernel_launches) *kernel_launches = s->kernel_launches;
+  return s->fatal == cudaSuccess ? LGT_OK : LGT_ECUDA;
+}
+
 extern "C" void lgt_server_destroy(lgt_server *s) {
   if (!s) return;
   {
@@ -675,6 +776,7 @@ extern "C" void lgt_server_destroy(lgt_server *s) {
   }
   if (s->worker.joinable()) s->worker.join();
   for (auto &kv : s->jobs) delete kv.second;
+  drop_graphs(s);
   if (s->d_sweep) cudaFree(s->d_sweep);
   if (s->h_sweep) cudaFreeHost(s->h_sweep);
   if (s->d_meas) cudaFree(s->d_meas);

@@ -97,6 +97,7 @@ _sigs = {
     "lgt_poll": ([_vp, ctypes.c_uint64, _P(lgt_result), _vp], ctypes.c_int),
     "lgt_cancel": ([_vp, ctypes.c_uint64], ctypes.c_int),
     "lgt_server_stats": ([_vp, _P(ctypes.c_uint64), _P(ctypes.c_uint64), _P(ctypes.c_size_t)], ctypes.c_int),
+    "lgt_server_counters": ([_vp] + [_P(ctypes.c_uint64)] * 4, ctypes.c_int),
     "lgt_server_destroy": ([_vp], None),
     "lgt_last_error": ([], ctypes.c_char_p),
     "lgt_version": ([], ctypes.c_char_p),
@@ -296,6 +297,13 @@ def lgt_server_stats(server):
     a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t()
     _check(_lib.lgt_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def lgt_server_counters(server) -> dict:
+    """Ticks run, ticks replayed from captured CUDA graphs, graphs captured, kernel launches."""
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(_lib.lgt_server_counters(server, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("ticks", "graph_launches", "graph_captures", "kernel_launches"), (x.value for x in v)))
 
 
 def lgt_server_destroy(server) -> None:

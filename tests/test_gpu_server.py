@@ -57,8 +57,17 @@ def wait_all(lgt, srv, ids, dims_of, timeout=300):
     return out
 
 
-def run_server(lgt, specs, budget=8 << 30):
-    srv = lgt.lgt_server_create(budget, 0)
+def run_server(lgt, specs, budget=8 << 30, graphs=True, counters=None):
+    import os
+    old = os.environ.get("LGT_SERVER_GRAPHS")
+    os.environ["LGT_SERVER_GRAPHS"] = "1" if graphs else "0"
+    try:
+        srv = lgt.lgt_server_create(budget, 0)
+    finally:
+        if old is None:
+            del os.environ["LGT_SERVER_GRAPHS"]
+        else:
+            os.environ["LGT_SERVER_GRAPHS"] = old
     try:
         ids, dims_of = [], {}
         for spec in specs:
@@ -69,6 +78,8 @@ def run_server(lgt, specs, budget=8 << 30):
         res = wait_all(lgt, srv, ids, dims_of)
         done, live, used = lgt.lgt_server_stats(srv)
         assert done == len(specs) and live == 0 and used == 0
+        if counters is not None:
+            counters.update(lgt.lgt_server_counters(srv))
     finally:
         lgt.lgt_server_destroy(srv)
     return [res[j] for j in ids]
@@ -83,6 +94,23 @@ def test_server_results_same_alone_and_in_mix(lgt):
         assert res1["F"] == res["F"] and res1["theta"] == res["theta"]
         assert res1["sweeps_bulk"] == res["sweeps_bulk"] and res1["sweeps_fp64"] == res["sweeps_fp64"]
         assert np.array_equal(links1, links)
+
+
+def test_server_graph_replay_changes_nothing(lgt):
+    """Ticks replayed from captured CUDA graphs run the same kernels on the same
+    tables as directly issued ticks: every job's result and links are bit-identical
+    with and without graphs, and with graphs most ticks are replays."""
+    cg, cd = {}, {}
+    with_g = run_server(lgt, JOBS, counters=cg)
+    without = run_server(lgt, JOBS, graphs=False, counters=cd)
+    for (s1, r1, l1), (s2, r2, l2) in zip(with_g, without):
+        assert s1 == s2 == lgt.LGT_OK
+        assert r1["F"] == r2["F"] and r1["theta"] == r2["theta"]
+        assert r1["sweeps_bulk"] == r2["sweeps_bulk"] and r1["sweeps_fp64"] == r2["sweeps_fp64"]
+        assert np.array_equal(l1, l2)
+    assert cd["graph_launches"] == 0 and cd["graph_captures"] == 0
+    assert cg["ticks"] == cd["ticks"] and cg["kernel_launches"] == cd["kernel_launches"]
+    assert 0 < cg["graph_captures"] <= 16 and cg["graph_launches"] > cg["ticks"] // 2, cg
 
 
 def test_server_matches_single_context_and_oracle(lgt):
