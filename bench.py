@@ -1,10 +1,11 @@
 """Benchmark: SU(3) Landau gauge fixing on 32^4 (eps = 0.5, seed 2), FP32 bulk
-sweeps (12-real links, omega = 1.7) + FP32-pair polish to theta < 1e-14.
+sweeps (12-real links, omega = 1.7) + anchored polish to theta < 1e-14.
 
 One step = the whole hot path on one field: ingest (layout + precision
 conversion), bulk FP32 sweeps with the accumulated transformation G and the
 sweeps' fused theta estimate, promotion (G applied in FP64 to the FP64 input),
-FP32-pair polishing sweeps to theta < 1e-14 certified by the exact FP64
+anchored polishing sweeps (the promoted field fixed, only G = 1 + D relaxed,
+in FP32-pair precision) to theta < 1e-14 certified by the exact FP64
 measurement, and egress of the fixed field.  The metric is site updates
 per second (sweeps x V / time).  Inputs (604 MB complex128 links; 201 MB of
 FP32 working links) are larger than the 129 MB L2, so no L2 flush is needed.
@@ -34,7 +35,7 @@ if ROOT not in sys.path:
 DIMS = (32, 32, 32, 32)
 EPS, SEED, OMEGA, TOL = 0.5, 2, 1.7, 1e-14
 METRIC = "site updates/s (Landau 32^4 to theta<1e-14, mixed precision)"
-WORKLOAD = ("SU(3) Landau 32^4, eps=0.5, seed 2, OR omega=1.7, FP32-12 bulk + FP32-pair polish to theta<1e-14 "
+WORKLOAD = ("SU(3) Landau 32^4, eps=0.5, seed 2, OR omega=1.7, FP32-12 bulk + anchored polish to theta<1e-14 "
             "(exact FP64 measurement certifies)")
 
 
@@ -125,13 +126,19 @@ class ClockSampler:
 
 
 def algorithmic_bytes_per_site(kind: str) -> int:
-    """Bytes one site update must move: its 8 links in and out, plus G(x) in and
-    out during the FP32 bulk phase (FP32-12 links 48 B, FP32-18 72 B, FP32-pair
-    and FP64 links 144 B, G stored as 2 rows: 48 B)."""
+    """Bytes one site update must move.  Bulk: its 8 links in and out plus G(x) in
+    and out (FP32-12 links 48 B, FP32-18 72 B, G stored as 2 rows: 48 B).
+    FP32-pair and FP64 polish: 8 links of 144 B in and out.  Anchored polish:
+    K0(x) (144 B), the 8 links' FP32-12 copies (384 B) and the 8 neighbours'
+    D high parts (384 B) in, its own D (96 B: rows 0, 1 as pairs) in and out."""
     if kind == "fp32_12":
         return 16 * 48 + 2 * 48
     if kind == "fp32_18":
         return 16 * 72 + 2 * 48
+    if kind == "anchor":
+        return 144 + 8 * 48 + 8 * 48 + 2 * 96
+    if kind == "anchor_coulomb":  # spatial directions only
+        return 144 + 6 * 48 + 6 * 48 + 2 * 96
     return 16 * 144
 
 
@@ -150,8 +157,18 @@ def cpu_baseline(budget_s: float = 12.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n * vol / dt, "unit": "site updates/s", "cores": O.max_threads(), "kind": "oracle",
-            "sample": f"{n} FP64 OR sweeps of the 32^4 field ({n * vol} site updates, {dt:.1f} s)"}
+    cores = O.max_threads()
+    # one core, one sweep, for the per-core rate
+    O.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        O.sweeps(U, 1, omega=OMEGA, sweep0=n)
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": n * vol / dt, "unit": "site updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} FP64 OR sweeps of the 32^4 field ({n * vol} site updates, {dt:.1f} s)",
+            "single_core": {"value": vol / dt1, "sample": "1 sweep of the 32^4 field on 1 thread"}}
 
 
 def aggregate_over_ranks(elapsed_s: float, units: float, device=None):
@@ -280,7 +297,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
     peaks, src = measured_peaks()
     kinds = {"fp32_12": (stats_kernel["bulk_ms"], stats_kernel["bulk_launches"]),
-             "pair": (stats_kernel["fp64_ms"], stats_kernel["fp64_launches"])}
+             "anchor": (stats_kernel["fp64_ms"], stats_kernel["fp64_launches"])}
     dom = max(kinds, key=lambda k: kinds[k][0])
     kernels = {}
     for k, (ms, n) in kinds.items():
@@ -320,6 +337,30 @@ def run_ours(args):
                                    "site_updates_per_s": (vol // 2) / avg, "run": "all-FP64 comparison"}
         finally:
             lgt.lgt_destroy(c64)
+    # ---- the other runs of the 32^4 workload (FP32-18 bulk; SR p = 0.8 on the same
+    # ladder) and the 8^4 latency case, one timed lgt_fix each, reported beside
+    variants = {}
+    if not args.no_fp64_compare and rank == 0:
+        runs = [("fp32_18_bulk", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_18, omega=OMEGA)),
+                ("sr_p0.8", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_12, algo=lgt.LGT_SR, p=0.8, seed=SEED))]
+        small = torch.from_numpy(synth.field((8, 8, 8, 8), 0.3, 1)).to(f"cuda:{local}")
+        runs += [("8x4_fp64", (8, 8, 8, 8), small, dict(bulk=lgt.LGT_FP64, omega=OMEGA, max_sweeps=1000)),
+                 ("8x4_mixed", (8, 8, 8, 8), small, dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, max_sweeps=1000))]
+        for name, dims, src, kw in runs:
+            kw = dict(dict(theta_tol=TOL, max_sweeps=50000), **kw)
+            cv = lgt.lgt_create(lgt.lgt_params_default(dims=dims, **kw), src, stream=stream)
+            try:
+                times = []
+                for _ in range(3 if dims != DIMS else 1):
+                    sec, stv, rv, sv = _timed_fix(lgt, cv, src, stream)
+                    times.append(sec)
+                variants[name] = {"seconds": float(np.median(times)), "status": stv, "sweeps_bulk": rv.sweeps_bulk,
+                                  "sweeps_polish": rv.sweeps_fp64, "F": rv.F, "theta": rv.theta,
+                                  "launch_config": list(sv.launch_config)}
+                if dims == DIMS:
+                    variants[name]["F_minus_headline_F"] = rv.F - results[-1]["F"]
+            finally:
+                lgt.lgt_destroy(cv)
     lgt.lgt_destroy(ctx)
 
     cpu = None
@@ -336,7 +377,8 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}"},
                 "sweeps_per_step": {"bulk_fp32": last["sweeps_bulk"], "polish": last["sweeps_fp64"]},
                 "result": {"F": last["F"], "theta": last["theta"], "plaquette": last["plaquette"]},
-                "time_to_theta_1e-14": ttt, "kernels": kernels, "roofline": roofline, "e2e": e2e,
+                "time_to_theta_1e-14": ttt, "other_runs": variants, "kernels": kernels, "roofline": roofline,
+                "e2e": e2e,
                 "gpu_launches": stats_kernel["launches"], "clocks": clocks, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -396,11 +438,11 @@ def run_coulomb(args):
     t = float(np.median(times))
     updates = stats.site_updates[0] + stats.site_updates[1]
     peaks, src = measured_peaks()
-    kern = _kernel_summary(stats, 12 * 48 + 2 * 48 + 4 * 48, 12 * 144 + 4 * 144, vol)
+    kern = _kernel_summary(stats, 12 * 48 + 2 * 48 + 4 * 48, algorithmic_bytes_per_site("anchor_coulomb"), vol)
     line = {"workload": "coulomb", "metric": "time to max_t theta_t<1e-14 (s)", "value": t, "unit": "s",
             "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "SU(3) Coulomb 48^3x96, eps=0.5, seed 3, OR omega=1.7, FP32-12 bulk + "
-                                   "FP32-pair polish, 96 slices per launch, per-slice convergence",
+                                   "anchored polish, 96 slices per launch, per-slice convergence",
                        "block_sizes": "autotuned"},
             "sweeps": {"bulk_fp32": res.sweeps_bulk, "polish": res.sweeps_fp64},
             "site_updates_per_s": updates / t, "site_updates": updates,
@@ -429,7 +471,7 @@ def run_landau64(args):
         lgt.lgt_destroy(ctx)
         out[name] = {"status": st, "seconds": t, "sweeps_bulk": res.sweeps_bulk, "sweeps_polish": res.sweeps_fp64,
                      "F": res.F, "theta": res.theta, "site_updates_per_s": (res.sweeps_bulk + res.sweeps_fp64) * vol / t,
-                     "kernels": _kernel_summary(stats, 16 * 48 + 2 * 48, 16 * 144, vol)}
+                     "kernels": _kernel_summary(stats, 16 * 48 + 2 * 48, algorithmic_bytes_per_site("anchor"), vol)}
     p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP64, omega=1.8)
     ctx = lgt.lgt_create(p, dev, stream=stream)
     lgt.lgt_sweep(ctx, 2)
@@ -535,7 +577,7 @@ def run_serve(args):
                       "all_converged": all(x == lgt.LGT_OK for x in list(st) + list(st_c)),
                       "config": {"workload": f"{len(specs)} jobs, dims in {{16^4, 24^4, 32^4, 16^3x32, 32^3x64, "
                                              "48^4}, Landau/Coulomb 50/50, tol 1e-12/1e-14, eps U[0.3,0.7], "
-                                             "seeds 1000+j, 150 GB budget, FP32-12 bulk + pair polish; capacity "
+                                             "seeds 1000+j, 150 GB budget, FP32-12 bulk + anchored polish; capacity "
                                              "from the first 64 jobs in a closed loop (12 outstanding)"}}),
           flush=True)
 

@@ -89,8 +89,18 @@ typedef enum {
  *   arithmetic, so every update is a gauge transformation to ~2^-48.
  *   Runs on the FP32 pipe.
  * FP64: every operation in FP64.
+ * ANCHOR: the promoted field U' (FP64) is kept fixed as an anchor and the
+ *   sweeps relax the gauge transformation G = 1 + D alone: the local update
+ *   at x sees K(x) = G(x) [K0(x) + C(x)], the K(x) of the same sweep on the
+ *   transformed links G U' G^+ (Sec. 3), with the constant
+ *   K0 = sum_mu U'_mu(x) + U'_mu(x-mu)^+ stored once as FP32 pairs and the
+ *   small C = sum_mu U'_mu(x) D(x+mu)^+ + U'_mu(x-mu)^+ D(x-mu)^+ formed in
+ *   FP32; rotations as in PAIR; D kept as FP32 pairs, so G is unitary to
+ *   ~2^-48.  Only D is written (1104 bytes moved per site update against
+ *   2304 for PAIR).  Measurements and output form G U' G^+ in FP64; a
+ *   measurement makes it the new anchor.
  * With bulk = LGT_FP64 every sweep uses the FP64 kernel. */
-typedef enum { LGT_POLISH_PAIR = 0, LGT_POLISH_FP64 = 1 } lgt_polish;
+typedef enum { LGT_POLISH_PAIR = 0, LGT_POLISH_FP64 = 1, LGT_POLISH_ANCHOR = 2 } lgt_polish;
 
 typedef struct {
   int32_t dims[4];            /* N_t, N_3, N_2, N_1 */
@@ -107,10 +117,12 @@ typedef struct {
   int32_t max_sweeps;         /* cap on sweeps of one lgt_fix call (all phases) */
   int32_t check_every;        /* exact theta check every k sweeps */
   int32_t reunit_every;       /* reunitarise FP32 links / G every n sweeps (0: never) */
-  int32_t block_size;         /* threads per block of the sweep kernels, 64/128/256 (0: autotuned
-                                 over block sizes and register budgets) */
+  int32_t block_size;         /* threads per block of the sweep kernels, 64/128/256, one thread per
+                                 site (0: autotuned over block sizes, register budgets and site
+                                 layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t reserved;           /* must be 0 */
+  int32_t launch_config;      /* 0: as block_size says; k = 1..7: launch configuration k-1 of the
+                                 sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
 } lgt_params;
 
@@ -125,9 +137,20 @@ typedef struct {
   int32_t reserved;
 } lgt_result;
 
+/* Launch configurations of the sweep kernels (lgt_params.launch_config - 1):
+ *   one thread per site:  0: 128 threads, <= 255 registers; 1: 128, <= 170;
+ *                         2: 256, <= 255; 3: 64, <= 128;
+ *   four threads per site (one per direction; FP32 bulk sweeps only):
+ *                         4: 128 threads, <= 128 registers; 5: 256, <= 128;
+ *                         6: 128, <= 80.
+ * A four-threads-per-site configuration applies to the bulk FP32 sweeps; the
+ * sweeps after promotion then use configuration 0.  Every configuration forms
+ * K(x) and the fused estimate in the same order, so results do not depend on
+ * it, only the time does. */
+
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0, polish LGT_POLISH_PAIR, omega_polish 1.3
+ * transform_temporal 1, block_size 0, launch_config 0, polish LGT_POLISH_ANCHOR, omega_polish 1.3
  * (after promotion the residual is short-wavelength noise, which a smaller
  * omega removes fastest).  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);

@@ -78,8 +78,8 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->check_every = 10;
   p->reunit_every = 50;
   p->block_size = 0;
-  p->polish = LGT_POLISH_PAIR;
-  p->reserved = 0;
+  p->polish = LGT_POLISH_ANCHOR;
+  p->launch_config = 0;
   p->omega_polish = 1.3;
   return LGT_OK;
 }
@@ -131,12 +131,16 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("max_sweeps >= 0, check_every >= 1, reunit_every >= 0 required");
     return LGT_EINVAL;
   }
-  if (p->polish != LGT_POLISH_PAIR && p->polish != LGT_POLISH_FP64) {
+  if (p->polish != LGT_POLISH_PAIR && p->polish != LGT_POLISH_FP64 && p->polish != LGT_POLISH_ANCHOR) {
     lgt_set_error("polish %d unknown", p->polish);
     return LGT_EINVAL;
   }
   if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) {
     lgt_set_error("block_size must be 0, 64, 128 or 256");
+    return LGT_EINVAL;
+  }
+  if (p->launch_config < 0 || p->launch_config > LGT_NCFG) {
+    lgt_set_error("launch_config must be in [0, %d]", LGT_NCFG);
     return LGT_EINVAL;
   }
   return LGT_OK;
@@ -166,6 +170,7 @@ size_t lgt_ctx_device_bytes(const lgt_params *p) {
   const Geom g = lgt_make_geom(p->dims);
   size_t b = field_bytes(FMT_F64, g.vh) + workspace_bytes(g, 64) + 4096;
   if (p->bulk != LGT_FP64) b += field_bytes(fmt_of(p->bulk), g.vh) + g_bytes(g.vh);
+  if (p->bulk != LGT_FP64 && p->polish == LGT_POLISH_ANCHOR) b += k0_bytes(g.vh) + d_bytes(g.vh) - g_bytes(g.vh);
   return b;
 }
 
@@ -174,17 +179,20 @@ struct lgt_ctx {
   lgt_params prm;
   Geom g;
   cudaStream_t stream;
-  int phase;      // 0 bulk (FP32), 1 FP64 storage, 2 FP32-pair storage (in u64)
+  int phase;      // 0 bulk (FP32), 1 FP64 storage, 2 FP32-pair storage (in u64), 3 anchored polish
   int bulk_fmt;   // FMT_* of the bulk phase
   void *u64;      // FP64 links (the input while in the bulk phase)
   void *u32;      // bulk working links
-  void *G;        // accumulated transformation of the bulk phase
+  void *G;        // accumulated transformation of the bulk phase; D = G - 1 of the anchored polish
+  void *k0;       // anchored polish: K0 (pairs)
+  int anchored;   // anchored polish: K0, the FP32-12 copy in u32 and D refer to the field in u64
+  int d_dirty;    // anchored polish: D != 0 (sweeps since the field in u64 was last formed)
   void *ws_base;  // workspace allocation
   Workspace ws;
   double *host;   // pinned readback buffer
   int cfg_bulk, cfg_polish;  // launch configurations of the bulk / polish sweep kernels
   int active_slices;         // slices updated by masked sweeps (from the last estimate/measurement)
-  int last_block;            // threads per block of the sweeps behind the current fused estimate
+  int last_sites;            // sites per block of the sweeps behind the current fused estimate
   int64_t sweeps_bulk, sweeps_fp64;
   uint64_t sweep_index;  // number of the next sweep (RNG counter)
   SweepCfg cfg;
@@ -218,6 +226,7 @@ static void ctx_free(lgt_ctx *c) {
   if (c->u64) cudaFree(c->u64);
   if (c->u32) cudaFree(c->u32);
   if (c->G) cudaFree(c->G);
+  if (c->k0) cudaFree(c->k0);
   if (c->ws_base) cudaFree(c->ws_base);
   if (c->host) cudaFreeHost(c->host);
   delete c;
@@ -303,6 +312,7 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
     return LGT_EINVAL;
   }
   c->phase = c->prm.bulk == LGT_FP64 ? 1 : 0;
+  c->anchored = c->d_dirty = 0;
   c->active_slices = g.nt;
   c->cfg.omega = c->prm.omega;  // omega_polish takes over at promotion
   c->sweeps_bulk = c->sweeps_fp64 = 0;
@@ -354,7 +364,12 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   CTX_CUDA(cudaMalloc(&c->u64, field_bytes(FMT_F64, g.vh)));
   if (params->bulk != LGT_FP64) {
     CTX_CUDA(cudaMalloc(&c->u32, field_bytes(c->bulk_fmt, g.vh)));
-    CTX_CUDA(cudaMalloc(&c->G, g_bytes(g.vh)));
+    if (params->polish == LGT_POLISH_ANCHOR) {
+      CTX_CUDA(cudaMalloc(&c->G, d_bytes(g.vh)));  // G of the bulk phase, then D
+      CTX_CUDA(cudaMalloc(&c->k0, k0_bytes(g.vh)));
+    } else {
+      CTX_CUDA(cudaMalloc(&c->G, g_bytes(g.vh)));
+    }
   }
   const size_t wsb = workspace_bytes(g, 64);
   CTX_CUDA(cudaMalloc(&c->ws_base, wsb));
@@ -362,16 +377,27 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   workspace_carve(c->ws_base, g, 64, &c->ws);
   CTX_CUDA(cudaMallocHost(&c->host, 4096 + sizeof(double) * 2 * (size_t)g.nt));
   // block sizes: given, or timed on the still-empty buffers
-  const int polish_fmt = params->bulk == LGT_FP64 ? (int)FMT_F64 : (params->polish == LGT_POLISH_PAIR ? (int)FMT_PAIR : (int)FMT_F64);
+  const int polish_fmt = params->bulk == LGT_FP64 ? (int)FMT_F64
+                         : (params->polish == LGT_POLISH_PAIR ? (int)FMT_PAIR
+                            : (params->polish == LGT_POLISH_ANCHOR ? (int)FMT_ANCHOR : (int)FMT_F64));
   c->cfg_bulk = c->cfg_polish = lgt_cfg_of_block(params->block_size);
-  if (!params->block_size) {
+  if (params->launch_config > 0) {
+    const int k = params->launch_config - 1;
+    c->cfg_bulk = lgt_cfg_supported(c->u32 ? c->bulk_fmt : (int)FMT_F64, k) ? k : 0;
+    c->cfg_polish = lgt_cfg_supported(polish_fmt, k) ? k : 0;
+  } else if (!params->block_size) {
     cudaError_t te = cudaSuccess;
     if (c->u32) c->cfg_bulk = lgt_tune_sweep(g, c->bulk_fmt, c->cfg, c->u32, c->G, c->ws, c->stream, &te);
-    if (te == cudaSuccess) c->cfg_polish = lgt_tune_sweep(g, polish_fmt, c->cfg, c->u64, nullptr, c->ws, c->stream, &te);
+    if (te == cudaSuccess) {
+      if (polish_fmt == FMT_ANCHOR)
+        c->cfg_polish = lgt_tune_sweep(g, polish_fmt, c->cfg, c->u32, c->G, c->ws, c->stream, &te, c->k0);
+      else
+        c->cfg_polish = lgt_tune_sweep(g, polish_fmt, c->cfg, c->u64, nullptr, c->ws, c->stream, &te);
+    }
     CTX_CUDA(te);
     if (!c->u32) c->cfg_bulk = c->cfg_polish;
   }
-  c->last_block = lgt_cfg_threads(c->cfg_bulk);
+  c->last_sites = lgt_cfg_sites(c->cfg_bulk);
 #undef CTX_CUDA
   st = load_field(c, links, links_on_device);
   if (st != LGT_OK) {
@@ -414,16 +440,47 @@ extern "C" void lgt_destroy(lgt_ctx *ctx) {
 // half-sweeps [first_parity .. first_parity + n_half) (parity alternating);
 // the sweep counter advances after each odd half
 // storage format (and kernel) of the working field in the current phase
+// storage format of the working field (the anchored polish measures the
+// formed field in u64, FP64)
 static int work_fmt(const lgt_ctx *c) {
   return c->phase == 0 ? c->bulk_fmt : (c->phase == 2 ? (int)FMT_PAIR : (int)FMT_F64);
 }
 
+static int skip_temporal(const lgt_ctx *c) {
+  return (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
+}
+
+// anchored polish: form U <- G U G^+ in u64 from the anchor and D (then D is
+// spent: the next sweep re-anchors)
+static lgt_status anchor_materialise(lgt_ctx *c) {
+  if (c->phase != 3 || !c->d_dirty) return LGT_OK;
+  LGT_CUDA(launch_apply_D(c->g, c->G, c->u64, c->u64, nullptr, skip_temporal(c), c->stream));
+  c->stats.launches++;
+  c->d_dirty = 0;
+  c->anchored = 0;
+  return LGT_OK;
+}
+
+static lgt_status anchor_setup(lgt_ctx *c) {
+  if (c->phase != 3 || c->anchored) return LGT_OK;
+  LGT_CUDA(launch_anchor_setup(c->g, c->u64, c->u32, c->k0, c->G, c->cfg.gauge, c->stream));
+  c->stats.launches++;
+  c->anchored = 1;
+  return LGT_OK;
+}
+
 static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_mask) {
-  const int fmt = work_fmt(c);
-  void *links = c->phase == 0 ? c->u32 : c->u64;
-  void *G = c->phase == 0 ? c->G : nullptr;
+  const bool anch = c->phase == 3;
+  const int fmt = anch ? (int)FMT_ANCHOR : work_fmt(c);
+  void *links = (c->phase == 0 || anch) ? c->u32 : c->u64;
+  void *G = (c->phase == 0 || anch) ? c->G : nullptr;
   const int kind = c->phase == 0 ? 0 : 1;
   if (n_half <= 0) return LGT_OK;
+  if (anch) {
+    lgt_status st = anchor_setup(c);
+    if (st != LGT_OK) return st;
+    c->d_dirty = 1;
+  }
   const int bt = batch_begin(c, kind);
   for (int h = 0; h < n_half; h++) {
     const int parity = (first_parity + h) & 1;
@@ -431,8 +488,8 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
     if (c->phase == 0 && c->prm.reunit_every > 0) reunit = ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
     const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
     LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask, lc,
-                               c->stream));
-    c->last_block = lgt_cfg_threads(lc);
+                               c->stream, anch ? c->k0 : nullptr));
+    c->last_sites = lgt_cfg_sites(lc);
     if (parity == 1) {
       c->sweep_index++;
       if (c->phase == 0) c->sweeps_bulk++;
@@ -491,6 +548,8 @@ static void fill_meas(const lgt_ctx *c, const double *t, Meas *m) {
 
 // exact measurement of the working field; coulomb_target >= 0 updates masks
 static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas *m) {
+  lgt_status mst = anchor_materialise(c);
+  if (mst != LGT_OK) return mst;
   const int fmt = work_fmt(c);
   const void *links = c->phase == 0 ? c->u32 : c->u64;
   const int bt = batch_begin(c, 2);
@@ -507,7 +566,7 @@ static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas
 
 // fused estimate from the last sweep's own K(x) (theta lagged by half a sweep)
 static lgt_status estimate(lgt_ctx *c, double coulomb_target, Meas *m) {
-  LGT_CUDA(launch_fused_finish(c->g, c->ws, c->cfg.gauge, c->last_block, coulomb_target, c->stream));
+  LGT_CUDA(launch_fused_finish(c->g, c->ws, c->cfg.gauge, c->last_sites, coulomb_target, c->stream));
   c->stats.launches++;
   lgt_status st = read_back(c, c->ws.fused_totals, sizeof(double) * TOT_N);
   if (st != LGT_OK) return st;
@@ -551,8 +610,7 @@ extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *thet
 // --------------------------------------------------------------- promotion
 static lgt_status promote(lgt_ctx *c) {
   if (c->phase != 0) return LGT_OK;
-  const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
-  LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_t, c->stream));
+  LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_temporal(c), c->stream));
   c->stats.launches++;
   c->phase = 1;
   if (c->prm.omega_polish != 0.0) c->cfg.omega = c->prm.omega_polish;
@@ -560,6 +618,11 @@ static lgt_status promote(lgt_ctx *c) {
     LGT_CUDA(launch_convert_pair(c->g, c->u64, 1, c->stream));
     c->stats.launches++;
     c->phase = 2;
+  } else if (c->prm.polish == LGT_POLISH_ANCHOR) {
+    c->phase = 3;
+    c->anchored = c->d_dirty = 0;
+    lgt_status st = anchor_setup(c);
+    if (st != LGT_OK) return st;
   }
   return sync_stream(c);
 }
@@ -669,12 +732,10 @@ static lgt_status to_output(lgt_ctx *c, double *out, int out_on_device, int work
     dst = tmp;
   }
   cudaError_t e;
-  if (c->phase >= 1) e = launch_egress(work_fmt(c), g, c->u64, dst, c->stream);
+  if (c->phase == 3 && c->d_dirty) e = launch_apply_D(g, c->G, c->u64, nullptr, dst, skip_temporal(c), c->stream);
+  else if (c->phase >= 1) e = launch_egress(work_fmt(c), g, c->u64, dst, c->stream);
   else if (working) e = launch_egress(c->bulk_fmt, g, c->u32, dst, c->stream);
-  else {
-    const int skip_t = (c->prm.gauge == LGT_COULOMB && !c->prm.transform_temporal) ? 1 : 0;
-    e = launch_apply_G(g, c->G, c->u64, nullptr, dst, skip_t, c->stream);
-  }
+  else e = launch_apply_G(g, c->G, c->u64, nullptr, dst, skip_temporal(c), c->stream);
   c->stats.launches++;
   if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, aos_bytes, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -19,4 +19,4 @@ size_t lgt_ctx_device_bytes(const lgt_params *p);
 // the compiled configurations, timed on `links` (overwritten with unit links)
 // and cached per (format, gauge, algorithm, dims, GPU).
 int lgt_tune_sweep(const lgt::Geom &g, int fmt, const lgt::SweepCfg &cfg, void *links, void *G,
-                   const lgt::Workspace &ws, cudaStream_t st, cudaError_t *err);
+                   const lgt::Workspace &ws, cudaStream_t st, cudaError_t *err, void *aux = nullptr);

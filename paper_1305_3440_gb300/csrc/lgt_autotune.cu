@@ -68,7 +68,7 @@ void append_file_locked(const TuneKey &k, int block) {
 }  // namespace
 
 int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, void *G, const Workspace &ws,
-                   cudaStream_t st, cudaError_t *err) {
+                   cudaStream_t st, cudaError_t *err, void *aux) {
   *err = cudaSuccess;
   const TuneKey key(fmt, cfg.gauge, cfg.algo, g.nt, g.n3, g.n2, g.n1, device_name());
   {
@@ -77,8 +77,15 @@ int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, voi
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) return it->second;
   }
-  cudaError_t e = launch_fill_unit(fmt, g, links, st);
-  if (e == cudaSuccess && G) e = launch_g_identity(g, G, st);
+  cudaError_t e;
+  if (fmt == FMT_ANCHOR) {  // unit FP32-12 anchor, K0 = 0, D = 0
+    e = launch_fill_unit(FMT_F32_12, g, links, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aux, 0, k0_bytes(g.vh), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, d_bytes(g.vh), st);
+  } else {
+    e = launch_fill_unit(fmt, g, links, st);
+    if (e == cudaSuccess && G) e = launch_g_identity(g, G, st);
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -86,12 +93,13 @@ int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, voi
   float best_ms = 1e30f;
   int best = 0;
   for (int k = 0; k < LGT_NCFG && e == cudaSuccess; k++) {
+    if (!lgt_cfg_supported(fmt, k)) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; rep++)
-      e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st);
+      e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st, aux);
     for (int trial = 0; trial < 3 && e == cudaSuccess; trial++) {
       e = cudaEventRecord(e0, st);
       for (int rep = 0; rep < 4 && e == cudaSuccess; rep++)
-        e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st);
+        e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st, aux);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;

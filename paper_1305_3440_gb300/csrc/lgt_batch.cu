@@ -64,6 +64,7 @@ cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSwe
   else if (fmt == FMT_F32_18) fn = pick_batch_fmt<FMT_F32_18>(gauge, algo);
   else if (fmt == FMT_F32_12) fn = pick_batch_fmt<FMT_F32_12>(gauge, algo);
   else if (fmt == FMT_PAIR) fn = pick_batch_fmt<FMT_PAIR>(gauge, algo);
+  else if (fmt == FMT_ANCHOR) fn = pick_batch_fmt<FMT_ANCHOR>(gauge, algo);
   if (!fn) return cudaErrorInvalidValue;
   fn<<<total_blocks, block, 0, st>>>(jobs, n, parity & 1, s);
   return cudaGetLastError();

@@ -25,6 +25,9 @@ enum { FMT_F64 = 0, FMT_F32_18 = 1, FMT_F32_12 = 2 };
 // of element c in chunk c -- the same 16 B per element as FMT_F64, so a field
 // converts in place.
 enum { FMT_PAIR = 3 };
+// Anchored polish (lgt_anchor.cuh): not a link format but the sweep over a
+// fixed anchor field (FP32-12 copy + K0 pairs) with D = G - 1 as pairs.
+enum { FMT_ANCHOR = 4 };
 enum { GAUGE_LANDAU = 0, GAUGE_COULOMB = 1 };
 enum { ALGO_OR = 0, ALGO_SR = 1 };
 

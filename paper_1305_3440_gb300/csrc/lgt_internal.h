@@ -28,8 +28,8 @@ enum {
 
 // Device workspace of one lattice (one allocation, carved up).
 struct Workspace {
-  double2 *warp_part;       // [2][nt][wps] per-warp (Re tr K, tr Delta^2) of each parity's last half-sweep
-  int wps;                  // warps per timeslice (stride of warp_part)
+  double2 *warp_part;       // [2][nt][wps] per 8-site group (Re tr K, tr Delta^2) of each parity's last half-sweep
+  int wps;                  // group slots per timeslice (stride of warp_part)
   double *fused_slice;      // [nt][2] per-slice fused sums (parity-0 Re tr K, both parities' tr Delta^2)
   unsigned *fused_counter;  // [1]
   double *fused_totals;     // [TOT_N] fused estimate, layout of totals
@@ -52,6 +52,8 @@ struct SweepArgs {
   Geom g;
   void *links;
   void *G;
+  const void *aux;  // anchored polish: K0
+
   const uint8_t *active;
   double2 *warp_part;  // [2][nt][wps]
   int wps;
@@ -125,14 +127,32 @@ struct SweepCfg {
 // Single-lattice half-sweep kernels, one per (format, gauge, algorithm,
 // launch configuration).  A launch configuration is a block size with a
 // register budget (__launch_bounds__(threads, min blocks per SM)), i.e. an
-// occupancy/spill trade-off; the autotuner times them.
-//   0: 128 threads, <= 255 registers     1: 128 threads, <= 170 registers
-//   2: 256 threads, <= 255 registers     3:  64 threads, <= 128 registers
-constexpr int LGT_NCFG = 4;
-__host__ __device__ constexpr int lgt_cfg_threads(int c) { return c == 2 ? 256 : (c == 3 ? 64 : 128); }
-__host__ __device__ constexpr int lgt_cfg_minblocks(int c) { return c == 1 ? 3 : (c == 3 ? 8 : 1); }
+// occupancy/spill trade-off, and a site layout; the autotuner times them.
+//   one thread per site (every format):
+//     0: 128 threads, <= 255 registers     1: 128 threads, <= 170 registers
+//     2: 256 threads, <= 255 registers     3:  64 threads, <= 128 registers
+//   four threads per site, one per direction (FP32 formats only):
+//     4: 128 threads (32 sites), <= 128 registers
+//     5: 256 threads (64 sites), <= 128 registers
+//     6: 128 threads (32 sites), <= 80 registers
+// Every configuration forms K(x) in the same order and groups the fused
+// estimate by the same 8 sites, so results do not depend on the choice.
+constexpr int LGT_NCFG = 7;
+__host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
+__host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
+  return c == 1 ? 3 : (c == 3 ? 8 : (c == 4 ? 4 : (c == 5 ? 2 : (c == 6 ? 6 : 1))));
+}
+__host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4; }
+// sites covered by one block
+__host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
+// whether a storage format has kernels for a configuration
+__host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
+  return c >= 0 && c < LGT_NCFG && (!lgt_cfg_quad(c) || fmt == FMT_F32_18 || fmt == FMT_F32_12);
+}
 // configuration for a requested block size (lgt_params.block_size)
 inline int lgt_cfg_of_block(int block) { return block == 256 ? 2 : (block == 64 ? 3 : 0); }
+// fused-estimate slots: one per 8 consecutive sites of a slice
+constexpr int LGT_FUSED_GROUP = 8;
 typedef void (*sweep_fn)(SweepArgs, int);
 sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg);  // FP32-18, FP32-12
 sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg);   // FP64, FP32-pair
@@ -142,16 +162,16 @@ sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg);   // FP64, FP32-p
 // use_mask: skip inactive slices.
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
-                              cudaStream_t st);
+                              cudaStream_t st, const void *aux = nullptr);
 
 // Fused estimate of F and theta from the last two half-sweeps (each sweep
 // kernel leaves per-warp sums of Re tr K and tr Delta^2 computed from the K it
 // used, so theta is lagged by half a sweep).  Reduced in fixed order into
 // w.fused_totals; if coulomb_target >= 0 the slice mask is set to
-// (theta_t >= coulomb_target).  sweep_block: block size of those sweeps.
-cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_block, double coulomb_target,
+// (theta_t >= coulomb_target).  sweep_sites: sites per block of those sweeps.
+cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_sites, double coulomb_target,
                                 cudaStream_t st);
-void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_block,
+void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_sites,
                      double coulomb_target);
 cudaError_t launch_fused_finish_batch(const BatchFused *jobs, int n, int total_blocks, cudaStream_t st);
 
@@ -182,6 +202,16 @@ cudaError_t launch_fill_unit(int fmt, const Geom &g, void *soa, cudaStream_t st)
 
 // In-place conversion of an FP64 field to FP32-pair storage (to_pair = 1)
 // or back (to_pair = 0).
+// Anchored polish: G = 1 + D (pairs) applied in FP64 (as launch_apply_G).
+cudaError_t launch_apply_D(const Geom &g, const void *D, const void *u64_in, void *u64_out, double *aos_out,
+                           int skip_temporal, cudaStream_t st);
+// Anchored polish set-up from the FP64 field u64: K0 (pairs), the FP32-12 copy
+// in u32, D = 0.
+cudaError_t launch_anchor_setup(const Geom &g, const void *u64, void *u32, void *K0, void *D, int gauge,
+                                cudaStream_t st);
+// bytes of K0 and of D (hi and lo arrays) for vh sites per parity
+inline size_t k0_bytes(int vh) { return (size_t)vh * 2 * 144; }
+inline size_t d_bytes(int vh) { return (size_t)vh * 2 * 96; }
 cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_t st);
 
 // Batched half-sweep over n lattices of one kernel variant (fmt, gauge,

@@ -16,7 +16,9 @@ namespace lgt {
 
 static inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-static int warps_per_slice(const Geom &g) { return ceil_div(g.vs_half, 32) + 8; }
+// fused-estimate slots per slice: one per 8 sites, plus the ragged last block
+// of the widest launch (256 sites)
+static int warps_per_slice(const Geom &g) { return ceil_div(g.vs_half, LGT_FUSED_GROUP) + 256 / LGT_FUSED_GROUP; }
 
 size_t workspace_bytes(const Geom &g, int min_block) {
   const int gx = ceil_div(g.vs_half, min_block);
@@ -71,6 +73,7 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->g = g;
   a->links = links;
   a->G = G;
+  a->aux = nullptr;
   a->active = use_mask ? w.active : nullptr;
   a->warp_part = w.warp_part;
   a->wps = w.wps;
@@ -86,14 +89,15 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
 
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
-                              cudaStream_t st) {
+                              cudaStream_t st, const void *aux) {
   sweep_fn fn = (fmt == FMT_F32_18 || fmt == FMT_F32_12) ? pick_sweep_f32(fmt, c.gauge, c.algo, cfg)
                                                           : pick_sweep_hi(fmt, c.gauge, c.algo, cfg);
   const int block = lgt_cfg_threads(cfg);
-  if (!fn) return cudaErrorInvalidValue;
+  if (!fn || !lgt_cfg_supported(fmt, cfg)) return cudaErrorInvalidValue;
   SweepArgs a;
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
-  dim3 grid(ceil_div(g.vs_half, block), g.nt);
+  a.aux = aux;
+  dim3 grid(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), g.nt);
   fn<<<grid, block, 0, st>>>(a, parity & 1);
   return cudaGetLastError();
 }
@@ -260,6 +264,21 @@ __device__ __forceinline__ void load_G_fp64(const void *G, int vh, int p, int i,
   reunitarise(m);
 }
 
+// G = 1 + D of the anchored polish in FP64 (pairs widened, row 2 rebuilt in
+// FP64, rows orthonormalised: unitary to FP64 rounding)
+__device__ __forceinline__ void load_G_from_D(const void *D, int vh, int p, int i, double m[18]) {
+  f2 d[18];
+  DIO::load_pair(D, vh, p, i, d);
+#pragma unroll
+  for (int k = 0; k < 12; k++) m[k] = (double)d[k].hi + (double)d[k].lo;
+  m[LGT_RE(0, 0)] += 1.0;
+  m[LGT_RE(1, 1)] += 1.0;
+  reunitarise(m);
+}
+
+// U_mu(x) <- G(x) U_mu(x) G(x+mu)^+ in FP64; SRC 0: G of the bulk phase
+// (FP32), SRC 1: G = 1 + D of the anchored polish (pairs)
+template <int SRC>
 __global__ void k_apply_G(Geom g, const void *G, const void *u_in, void *u_out, double *aos_out, int skip_temporal) {
   int p, mu, i;
   Coords c;
@@ -272,8 +291,13 @@ __global__ void k_apply_G(Geom g, const void *G, const void *u_in, void *u_out, 
 #pragma unroll
     for (int k = 0; k < 18; k++) r[k] = u[k];
   } else {
-    load_G_fp64(G, g.vh, p, i, gx);
-    load_G_fp64(G, g.vh, p ^ 1, cb_shift(g, c, mu, +1), gy);
+    if (SRC == 0) {
+      load_G_fp64(G, g.vh, p, i, gx);
+      load_G_fp64(G, g.vh, p ^ 1, cb_shift(g, c, mu, +1), gy);
+    } else {
+      load_G_from_D(G, g.vh, p, i, gx);
+      load_G_from_D(G, g.vh, p ^ 1, cb_shift(g, c, mu, +1), gy);
+    }
     mat_mul(gx, u, tmp);
     mat_mul_dag(tmp, gy, r);
   }
@@ -290,7 +314,60 @@ cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, voi
                            int skip_temporal, cudaStream_t st) {
   const long long n = (long long)g.vh * 8;
   const int blk = 128;
-  k_apply_G<<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, G, u64_in, u64_out, aos_out, skip_temporal);
+  k_apply_G<0><<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, G, u64_in, u64_out, aos_out, skip_temporal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_D(const Geom &g, const void *D, const void *u64_in, void *u64_out, double *aos_out,
+                           int skip_temporal, cudaStream_t st) {
+  const long long n = (long long)g.vh * 8;
+  const int blk = 128;
+  k_apply_G<1><<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, D, u64_in, u64_out, aos_out, skip_temporal);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ anchored polish set-up
+// For every site of either parity: K0(x) = sum_{mu >= mu0} U_mu(x) + U_mu(x-mu)^+
+// in FP64, stored as FP32 pairs (hi = fl32(v), lo = fl32(v - hi)); the FP32-12
+// copy of the site's forward links; D(x) = 0.
+__global__ void k_anchor_setup(Geom g, const void *u64, void *u32, void *K0, void *D, int mu0) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)g.vh * 2) return;
+  const int p = (int)(gid / g.vh), i = (int)(gid % g.vh);
+  const int t = i / g.vs_half;
+  const Coords c = coords_in_slice(g, p, t, i - t * g.vs_half);
+  double K[18];
+  mat_zero(K);
+  for (int mu = 0; mu < 4; mu++) {
+    double u[18];
+    float uf[18];
+    LinkIO<FMT_F64>::load(u64, g.vh, p, mu, i, u);
+#pragma unroll
+    for (int k = 0; k < 18; k++) uf[k] = __double2float_rn(u[k]);
+    LinkIO<FMT_F32_12>::store(u32, g.vh, p, mu, i, uf);
+    if (mu >= mu0) {
+      acc_add(K, u);
+      LinkIO<FMT_F64>::load(u64, g.vh, p ^ 1, mu, cb_shift(g, c, mu, -1), u);
+      acc_add_dag(K, u);
+    }
+  }
+  f2 k2[18], z[18];
+#pragma unroll
+  for (int k = 0; k < 18; k++) {
+    const float hi = __double2float_rn(K[k]);
+    k2[k] = {hi, __double2float_rn(K[k] - (double)hi)};
+    z[k] = {0.0f, 0.0f};
+  }
+  K0IO::store(K0, g.vh, p, i, k2);
+  DIO::store_pair(D, g.vh, p, i, z);
+}
+
+cudaError_t launch_anchor_setup(const Geom &g, const void *u64, void *u32, void *K0, void *D, int gauge,
+                                cudaStream_t st) {
+  const long long n = (long long)g.vh * 2;
+  const int blk = 128;
+  k_anchor_setup<<<(unsigned)((n + blk - 1) / blk), blk, 0, st>>>(g, u64, u32, K0, D,
+                                                                 gauge == GAUGE_COULOMB ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -359,12 +436,12 @@ cudaError_t launch_convert_pair(const Geom &g, void *u, int to_pair, cudaStream_
 
 
 // ------------------------------------------------- fused estimate, finish
-void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_block,
+void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge, int sweep_sites,
                      double coulomb_target) {
   a->g = g;
   a->warp_part = w.warp_part;
   a->wps = w.wps;
-  a->nw = ceil_div(g.vs_half, sweep_block) * (sweep_block / 32);
+  a->nw = ceil_div(g.vs_half, sweep_sites) * (sweep_sites / LGT_FUSED_GROUP);
   a->gauge = gauge;
   a->slice = w.fused_slice;
   a->counter = w.fused_counter;
@@ -375,10 +452,10 @@ void fill_fused_args(FusedArgs *a, const Geom &g, const Workspace &w, int gauge,
 
 __global__ void __launch_bounds__(256) k_fused_finish(FusedArgs a) { fused_finish_body(a, blockIdx.x); }
 
-cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_block, double coulomb_target,
+cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_sites, double coulomb_target,
                                 cudaStream_t st) {
   FusedArgs a;
-  fill_fused_args(&a, g, w, gauge, sweep_block, coulomb_target);
+  fill_fused_args(&a, g, w, gauge, sweep_sites, coulomb_target);
   k_fused_finish<<<g.nt, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

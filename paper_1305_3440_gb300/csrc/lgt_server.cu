@@ -66,9 +66,10 @@ struct Job {
   int slot = -1;
   // device state
   Geom g;
-  void *u64 = nullptr, *u32 = nullptr, *G = nullptr, *ws_base = nullptr;
+  void *u64 = nullptr, *u32 = nullptr, *G = nullptr, *k0 = nullptr, *ws_base = nullptr;
   Workspace ws;
-  int phase = 0, bulk_fmt = FMT_F64;
+  int phase = 0, bulk_fmt = FMT_F64;  // phase as lgt_get_progress (3: anchored polish)
+  bool anchored = false, d_dirty = false;
   SweepCfg cfg;
   int64_t sweeps_bulk = 0, sweeps_fp64 = 0, remaining = 0;
   uint64_t sweep_index = 0;
@@ -78,8 +79,14 @@ struct Job {
   int nthis = 0;             // sweeps in the current tick
   int nbx = 0;
 
+  // storage of the field that measurements read (the anchored polish measures
+  // the formed field in u64)
   int work_fmt() const { return phase == 0 ? bulk_fmt : (phase == 2 ? (int)FMT_PAIR : (int)FMT_F64); }
   void *work_links() const { return phase == 0 ? u32 : u64; }
+  // kernel variant and links of the sweeps
+  int sweep_fmt() const { return phase == 3 ? (int)FMT_ANCHOR : work_fmt(); }
+  void *sweep_links() const { return (phase == 0 || phase == 3) ? u32 : u64; }
+  int skip_temporal() const { return (prm.gauge == LGT_COULOMB && !prm.transform_temporal) ? 1 : 0; }
   double theta_of(const double *tot) const {
     return prm.gauge == LGT_COULOMB ? tot[TOT_THETA_COULOMB_MAX] : tot[TOT_THETA_LANDAU];
   }
@@ -135,7 +142,7 @@ namespace {
 cudaError_t dev_alloc(lgt_server *s, void **p, size_t n) { return cudaMallocFromPoolAsync(p, n, s->pool, s->stream); }
 
 void release_job_device(lgt_server *s, Job *j) {
-  void **ptrs[] = {&j->u64, &j->u32, &j->G, &j->ws_base};
+  void **ptrs[] = {&j->u64, &j->u32, &j->G, &j->k0, &j->ws_base};
   for (void **p : ptrs)
     if (*p) {
       cudaFreeAsync(*p, s->stream);
@@ -181,7 +188,9 @@ cudaError_t admit(lgt_server *s, Job *j, int *bad_input) {
   if ((e = dev_alloc(s, &j->u64, field_bytes(FMT_F64, g.vh))) != cudaSuccess) return e;
   if (p.bulk != LGT_FP64) {
     if ((e = dev_alloc(s, &j->u32, field_bytes(j->bulk_fmt, g.vh))) != cudaSuccess) return e;
-    if ((e = dev_alloc(s, &j->G, g_bytes(g.vh))) != cudaSuccess) return e;
+    const bool anch = p.polish == LGT_POLISH_ANCHOR;
+    if ((e = dev_alloc(s, &j->G, anch ? d_bytes(g.vh) : g_bytes(g.vh))) != cudaSuccess) return e;
+    if (anch && (e = dev_alloc(s, &j->k0, k0_bytes(g.vh))) != cudaSuccess) return e;
   }
   const size_t wsb = workspace_bytes(g, 64);
   if ((e = dev_alloc(s, &j->ws_base, wsb)) != cudaSuccess) return e;
@@ -203,6 +212,20 @@ cudaError_t admit(lgt_server *s, Job *j, int *bad_input) {
   std::vector<double>().swap(j->input);
   *bad_input = err_h != 0;
   return e;
+}
+
+// anchored polish: form U <- G U' G^+ in u64 (the job's measured field; the
+// next sweep re-anchors), and the anchor set-up
+cudaError_t anchor_materialise(lgt_server *s, Job *j) {
+  if (j->phase != 3 || !j->d_dirty) return cudaSuccess;
+  j->d_dirty = j->anchored = false;
+  return launch_apply_D(j->g, j->G, j->u64, j->u64, nullptr, j->skip_temporal(), s->stream);
+}
+
+cudaError_t anchor_setup(lgt_server *s, Job *j) {
+  if (j->phase != 3 || j->anchored) return cudaSuccess;
+  j->anchored = true;
+  return launch_anchor_setup(j->g, j->u64, j->u32, j->k0, j->G, j->cfg.gauge, s->stream);
 }
 
 double coulomb_target(const Job *j) {
@@ -329,28 +352,37 @@ cudaError_t tick(lgt_server *s) {
     j->nthis = j->measure_only ? 0 : (int)std::min<int64_t>(j->prm.check_every, j->remaining);
     kmax = std::max(kmax, j->nthis);
   }
+  // anchored polish jobs: the exact measurement reads the formed field, the
+  // sweeps need a current anchor (rare: at promotion and certification; issued
+  // before, and outside, the tick's captured sequence)
+  for (Job *j : live) {
+    cudaError_t e = j->measure_only ? anchor_materialise(s, j) : anchor_setup(s, j);
+    if (e != cudaSuccess) return e;
+    if (!j->measure_only && j->phase == 3) j->d_dirty = true;
+  }
   // sweep segments: for each sweep offset s, jobs grouped by kernel variant
   std::vector<Segment> segs;
   std::vector<BatchSweep> rows;
   std::vector<Job *> order(live);
   std::stable_sort(order.begin(), order.end(), [](const Job *a, const Job *b) {
-    const int ka = (a->work_fmt() * 2 + a->cfg.gauge) * 2 + a->cfg.algo;
-    const int kb = (b->work_fmt() * 2 + b->cfg.gauge) * 2 + b->cfg.algo;
+    const int ka = (a->sweep_fmt() * 2 + a->cfg.gauge) * 2 + a->cfg.algo;
+    const int kb = (b->sweep_fmt() * 2 + b->cfg.gauge) * 2 + b->cfg.algo;
     return ka < kb;
   });
   for (int sw = 0; sw < kmax; sw++) {
     size_t i = 0;
     while (i < order.size()) {
       const Job *h = order[i];
-      Segment seg = {h->work_fmt(), h->cfg.gauge, h->cfg.algo, sw, rows.size(), 0, 0};
+      Segment seg = {h->sweep_fmt(), h->cfg.gauge, h->cfg.algo, sw, rows.size(), 0, 0};
       size_t k = i;
       for (; k < order.size(); k++) {
         Job *j = order[k];
-        if (j->work_fmt() != seg.fmt || j->cfg.gauge != seg.gauge || j->cfg.algo != seg.algo) break;
+        if (j->sweep_fmt() != seg.fmt || j->cfg.gauge != seg.gauge || j->cfg.algo != seg.algo) break;
         if (sw >= j->nthis) continue;
         BatchSweep r;
-        fill_sweep_args(&r.a, j->g, j->work_links(), j->phase == 0 ? j->G : nullptr, j->ws, j->cfg, j->sweep_index,
-                        0, j->prm.gauge == LGT_COULOMB ? 1 : 0);
+        fill_sweep_args(&r.a, j->g, j->sweep_links(), (j->phase == 0 || j->phase == 3) ? j->G : nullptr, j->ws,
+                        j->cfg, j->sweep_index, 0, j->prm.gauge == LGT_COULOMB ? 1 : 0);
+        r.a.aux = j->phase == 3 ? j->k0 : nullptr;
         r.a.reunit_every = j->phase == 0 ? j->prm.reunit_every : 0;
         r.a.count_base = j->sweeps_bulk;
         r.block_begin = seg.blocks;
@@ -369,7 +401,7 @@ cudaError_t tick(lgt_server *s) {
   for (Job *j : live) {
     if (j->measure_only) continue;
     BatchFused r;
-    fill_fused_args(&r.a, j->g, j->ws, j->cfg.gauge, kServerBlock, coulomb_target(j));
+    fill_fused_args(&r.a, j->g, j->ws, j->cfg.gauge, kServerBlock, coulomb_target(j));  // one thread per site
     r.block_begin = fblocks;
     r.nbx = 0;
     frows.push_back(r);
@@ -448,7 +480,9 @@ cudaError_t tick(lgt_server *s) {
 
 // final measurement with plaquette and copy-out of a finished job
 cudaError_t collect(lgt_server *s, Job *j) {
-  cudaError_t e = launch_measure(j->work_fmt(), j->g, j->work_links(), j->ws, 1, -1.0, kServerBlock, s->stream);
+  cudaError_t e = anchor_materialise(s, j);
+  if (e != cudaSuccess) return e;
+  e = launch_measure(j->work_fmt(), j->g, j->work_links(), j->ws, 1, -1.0, kServerBlock, s->stream);
   if (e != cudaSuccess) return e;
   void *stage = nullptr;
   if ((e = dev_alloc(s, &stage, aos_bytes_of(j->g))) != cudaSuccess) return e;
@@ -470,13 +504,15 @@ cudaError_t collect(lgt_server *s, Job *j) {
 }
 
 cudaError_t promote_job(lgt_server *s, Job *j) {
-  const int skip_t = (j->prm.gauge == LGT_COULOMB && !j->prm.transform_temporal) ? 1 : 0;
-  cudaError_t e = launch_apply_G(j->g, j->G, j->u64, j->u64, nullptr, skip_t, s->stream);
+  cudaError_t e = launch_apply_G(j->g, j->G, j->u64, j->u64, nullptr, j->skip_temporal(), s->stream);
   j->phase = 1;
   if (j->prm.omega_polish != 0.0) j->cfg.omega = j->prm.omega_polish;
   if (e == cudaSuccess && j->prm.polish == LGT_POLISH_PAIR) {
     e = launch_convert_pair(j->g, j->u64, 1, s->stream);
     j->phase = 2;
+  } else if (j->prm.polish == LGT_POLISH_ANCHOR) {
+    j->phase = 3;
+    j->anchored = j->d_dirty = false;
   }
   j->measure_only = true;
   return e;

@@ -14,25 +14,40 @@
 
 #include "lgt_device.cuh"
 #include "lgt_internal.h"
+#include "lgt_anchor.cuh"
 #include "lgt_pair.cuh"
 
 namespace lgt {
 
 
 
-// The fused estimate: each warp's sum of (Re tr K, tr Delta^2) over its sites
-// goes to its own slot (xor butterfly: fixed order; no block barrier, no
-// atomics); k_fused_finish reduces the slots when an estimate is wanted.
-template <typename T>
+// The fused estimate: the sum of (Re tr K, tr Delta^2) over each group of
+// LGT_FUSED_GROUP = 8 consecutive sites of a slice goes to the group's slot
+// (xor butterfly: fixed order; no block barrier, no atomics), and
+// k_fused_finish reduces the slots when an estimate is wanted.  STRIDE is the
+// lane distance between consecutive sites (1: one thread per site, 4: four
+// threads per site, the site's value on its thread 0).  The butterfly pairs
+// the same sites in both layouts, so the slots do not depend on it.
+template <typename T, int STRIDE>
 __device__ __forceinline__ void fused_store(const SweepArgs &a, int p, int t, int bx, T acc[2]) {
 #pragma unroll
   for (int k = 0; k < 2; k++)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-  if ((threadIdx.x & 31) == 0) {
-    const int w = bx * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
-    a.warp_part[((size_t)p * a.g.nt + t) * a.wps + w] = make_double2((double)acc[0], (double)acc[1]);
+    for (int off = 4 * STRIDE; off >= STRIDE; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  const int tid = bx * (int)blockDim.x + (int)threadIdx.x;  // thread index within the slice
+  if ((threadIdx.x & (LGT_FUSED_GROUP * STRIDE - 1)) == 0) {
+    const int slot = tid / (LGT_FUSED_GROUP * STRIDE);
+    a.warp_part[((size_t)p * a.g.nt + t) * a.wps + slot] = make_double2((double)acc[0], (double)acc[1]);
   }
+}
+
+// The term of direction mu in K(x): U_mu(x) + U_mu(x - mu)^dagger (Sec. 3),
+// formed from zero so that every site layout rounds it the same way.
+template <typename R>
+__device__ __forceinline__ void k_term(R k[18], const R uf[18], const R ub[18]) {
+  mat_zero(k);
+  acc_add(k, uf);
+  acc_add_dag(k, ub);
 }
 
 __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
@@ -67,25 +82,38 @@ __device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t,
       IO::load_raw(a.links, a.g.vh, p, mu, i, uf[mu]);
       IO::load_raw(a.links, a.g.vh, q, mu, nb[mu], ub[mu]);
     }
-    float W[18];
-    mat_zero(W);
+    // K(x) = (k_0 + k_1) + (k_2 + k_3), k_mu the direction terms (k_0 = 0 for
+    // Coulomb gauge): the order of the four-threads-per-site layout
+    float W[18], k2[18];
 #pragma unroll
-    for (int mu = MU0; mu < 4; mu++) {
-      if (IO::kCompressed) {
-        float full[18];
+    for (int h = 0; h < 2; h++) {
+      float ka[18], kb[18];
 #pragma unroll
-        for (int e = 0; e < 18; e++) full[e] = uf[mu][e];
-        rebuild_row2(full);
-        acc_add(W, full);
+      for (int d = 0; d < 2; d++) {
+        const int mu = 2 * h + d;
+        float *k = d ? kb : ka;
+        if (mu < MU0) {
+          mat_zero(k);
+        } else if (IO::kCompressed) {
+          float ff[18], fb[18];
 #pragma unroll
-        for (int e = 0; e < 18; e++) full[e] = ub[mu][e];
-        rebuild_row2(full);
-        acc_add_dag(W, full);
-      } else {
-        acc_add(W, uf[mu]);
-        acc_add_dag(W, ub[mu]);
+          for (int e = 0; e < 18; e++) {
+            ff[e] = uf[mu][e];
+            fb[e] = ub[mu][e];
+          }
+          rebuild_row2(ff);
+          rebuild_row2(fb);
+          k_term(k, ff, fb);
+        } else {
+          k_term(k, uf[mu], ub[mu]);
+        }
       }
+      float *dst = h ? k2 : W;
+#pragma unroll
+      for (int e = 0; e < 18; e++) dst[e] = ka[e] + kb[e];
     }
+#pragma unroll
+    for (int e = 0; e < 18; e++) W[e] = W[e] + k2[e];
     violation_of_K(W, acc[0], acc[1]);
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
@@ -122,7 +150,92 @@ __device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t,
       GIO::store(a.G, a.g.vh, p, i, r);
     }
   }
-  fused_store<float>(a, p, t, bx, acc);
+  fused_store<float, 1>(a, p, t, bx, acc);
+}
+
+
+// FP32 link formats, four threads per site: thread m of the site's quad owns
+// direction m (for Coulomb gauge thread 0 owns the temporal links, which the
+// transformation also moves).  Each thread loads its forward and backward
+// link and forms its term k_m of K(x); two xor shuffles sum the terms as
+// (k_0 + k_1) + (k_2 + k_3), the order of the one-thread layout, so all four
+// threads hold the same K bit for bit and run the same local update; then
+// each thread writes its own two links (thread 0 also G).  Per thread this
+// holds a quarter of the links, which buys occupancy: more loads in flight.
+template <int FMT, int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_f32_quad(const SweepArgs &a, int p, int t, int bx) {
+  typedef LinkIO<FMT> IO;
+  if (a.active && !a.active[t]) return;  // whole block belongs to one slice
+  constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+  const int m = threadIdx.x & 3;
+  const int j = bx * (int)(blockDim.x >> 2) + (int)(threadIdx.x >> 2);
+  const bool valid = j < a.g.vs_half;  // the shuffles below need every lane
+  const bool in_K = m >= MU0;
+  const Coords c = coords_in_slice(a.g, p, t, valid ? j : 0);
+  const int i = t * a.g.vs_half + (valid ? j : 0);
+  const int q = p ^ 1;
+  const int nb = cb_shift(a.g, c, m, -1);
+  float uf[18], ub[18], W[18];
+  mat_zero(W);
+  if (valid && in_K) {
+    IO::load_raw(a.links, a.g.vh, p, m, i, uf);
+    IO::load_raw(a.links, a.g.vh, q, m, nb, ub);
+    if (IO::kCompressed) {
+      float fb[18];
+#pragma unroll
+      for (int e = 0; e < 18; e++) fb[e] = ub[e];
+      rebuild_row2(uf);  // g U needs row 2 of U
+      rebuild_row2(fb);
+      k_term(W, uf, fb);
+    } else {
+      k_term(W, uf, ub);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 18; e++) W[e] = W[e] + __shfl_xor_sync(0xffffffffu, W[e], 1);
+#pragma unroll
+  for (int e = 0; e < 18; e++) W[e] = W[e] + __shfl_xor_sync(0xffffffffu, W[e], 2);
+  float acc[2] = {0.0f, 0.0f};
+  {
+    float vr, vd;
+    violation_of_K(W, vr, vd);
+    if (valid && m == 0) {
+      acc[0] = vr;
+      acc[1] = vd;
+    }
+  }
+  uint4 draws = make_uint4(0, 0, 0, 0);
+  if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+  float gm[18];
+  local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+  if (valid && in_K) {
+    float r[18];
+    mat_mul(gm, uf, r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, p, m, i, r);
+    mat_mul_dag(ub, gm, r);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, q, m, nb, r);
+  }
+  if (GAUGE == GAUGE_COULOMB && valid && m == 0 && a.transform_temporal) {
+    float u[18], r[18];
+    IO::load(a.links, a.g.vh, p, 0, i, u);
+    mat_mul(gm, u, r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, p, 0, i, r);
+    IO::load(a.links, a.g.vh, q, 0, nb, u);
+    mat_mul_dag(u, gm, r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, q, 0, nb, r);
+  }
+  if (a.G && valid && m == 0) {
+    float gx[18], r[18];
+    GIO::load(a.G, a.g.vh, p, i, gx);
+    mat_mul(gm, gx, r);
+    if (a.reunit) reunitarise(r);
+    GIO::store(a.G, a.g.vh, p, i, r);
+  }
+  fused_store<float, 4>(a, p, t, bx, acc);
 }
 
 
@@ -167,7 +280,7 @@ __device__ __forceinline__ void sweep_body_f64(const SweepArgs &a, int p, int t,
       IO::store(a.links, a.g.vh, q, mu, nbm, r);
     }
   }
-  fused_store<double>(a, p, t, bx, acc);
+  fused_store<double, 1>(a, p, t, bx, acc);
 }
 
 
@@ -229,7 +342,67 @@ __device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t
       IO::store(a.links, a.g.vh, q, mu, nbm, u);
     }
   }
-  fused_store<float>(a, p, t, bx, acc);
+  fused_store<float, 1>(a, p, t, bx, acc);
+}
+
+
+// Anchored polishing sweep (lgt_anchor.cuh): a.links = FP32-12 copy of the
+// anchor field U', a.G = D = G - 1 (pairs), a.aux = K0 (pairs).  One thread per
+// site; only D(x) is written.
+template <int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_anchor(const SweepArgs &a, int p, int t, int bx, int nbx) {
+  typedef LinkIO<FMT_F32_12> IO;
+  if (a.active && !a.active[t]) return;
+  const int j = bx * blockDim.x + threadIdx.x;
+  float acc[2] = {0.0f, 0.0f};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    // C(x) = sum_mu U'_mu(x) D(x+mu)^+ + U'_mu(x-mu)^+ D(x-mu)^+  (small; FP32)
+    float C[18];
+    mat_zero(C);
+#pragma unroll 1
+    for (int mu = MU0; mu < 4; mu++) {
+      float u[18], dn[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      DIO::load_hi(a.G, a.g.vh, q, cb_shift(a.g, c, mu, +1), dn);
+      acc_mul_dag(u, dn, C);
+      const int nb = cb_shift(a.g, c, mu, -1);
+      IO::load(a.links, a.g.vh, q, mu, nb, u);
+      DIO::load_hi(a.G, a.g.vh, q, nb, dn);
+      acc_dag_mul_dag(u, dn, C);
+    }
+    // M = K0 + C, then K = M + D(x) M (the small product in FP32)
+    f2 K[18];
+    K0IO::load(a.aux, a.g.vh, p, i, K);
+#pragma unroll
+    for (int e = 0; e < 18; e++) K[e] = pair_add(K[e], f2{C[e], 0.0f});
+    f2 D[18];
+    DIO::load_pair(a.G, a.g.vh, p, i, D);
+    {
+      float dh[18], mh[18], dm[18];
+#pragma unroll
+      for (int e = 0; e < 18; e++) {
+        dh[e] = D[e].hi;
+        mh[e] = K[e].hi;
+      }
+      mat_mul(dh, mh, dm);
+#pragma unroll
+      for (int e = 0; e < 18; e++) K[e] = pair_add(K[e], f2{dm[e], 0.0f});
+    }
+    pair_violation(K, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    Rot rot[3];
+    pair_local_update<ALGO>(K, rot, (float)a.omega, a.sr_thr, draws);
+    f2 d[18];
+    pair_delta(rot, d);
+    d_update(D, d);
+    DIO::store_pair(a.G, a.g.vh, p, i, D);
+  }
+  fused_store<float, 1>(a, p, t, bx, acc);
 }
 
 
@@ -237,6 +410,7 @@ template <int FMT, int GAUGE, int ALGO>
 __device__ __forceinline__ void sweep_dispatch(const SweepArgs &a, int p, int t, int bx, int nbx) {
   if (FMT == FMT_F64) sweep_body_f64<GAUGE, ALGO>(a, p, t, bx, nbx);
   else if (FMT == FMT_PAIR) sweep_body_pair<GAUGE, ALGO>(a, p, t, bx, nbx);
+  else if (FMT == FMT_ANCHOR) sweep_body_anchor<GAUGE, ALGO>(a, p, t, bx, nbx);
   else sweep_body_f32<(FMT == FMT_F32_12 ? FMT_F32_12 : FMT_F32_18), GAUGE, ALGO>(a, p, t, bx, nbx);
 }
 

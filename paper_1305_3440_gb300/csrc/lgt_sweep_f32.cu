@@ -1,12 +1,14 @@
 // lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
-// storage), one instantiation per gauge, algorithm and launch configuration.
+// storage), one instantiation per gauge, algorithm and launch configuration
+// (one or four threads per site).
 #include "lgt_sweep.cuh"
 
 namespace lgt {
 
 template <int FMT, int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs a, int p) {
-  sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  if constexpr (lgt_cfg_quad(CFG)) sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
+  else sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <int CFG>
@@ -31,6 +33,9 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 1: return pick_cfg<1>(fmt, gauge, algo);
     case 2: return pick_cfg<2>(fmt, gauge, algo);
     case 3: return pick_cfg<3>(fmt, gauge, algo);
+    case 4: return pick_cfg<4>(fmt, gauge, algo);
+    case 5: return pick_cfg<5>(fmt, gauge, algo);
+    case 6: return pick_cfg<6>(fmt, gauge, algo);
   }
   return nullptr;
 }

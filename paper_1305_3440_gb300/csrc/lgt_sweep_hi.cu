@@ -1,6 +1,6 @@
 // lgt_sweep_hi.cu -- the higher-precision half-sweep kernels: FP64 (every
-// operation in FP64) and FP32-pair (the polishing sweeps), one instantiation
-// per gauge, algorithm and launch configuration.
+// operation in FP64), FP32-pair and anchored (the polishing sweeps), one
+// instantiation per gauge, algorithm and launch configuration.
 #include "lgt_sweep.cuh"
 
 namespace lgt {
@@ -15,6 +15,11 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
   sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
+template <int GAUGE, int ALGO, int CFG>
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_anchor(SweepArgs a, int p) {
+  sweep_body_anchor<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
 template <int CFG>
 static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
   if (fmt == FMT_F64) {
@@ -24,6 +29,10 @@ static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
   if (fmt == FMT_PAIR) {
     if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_pair<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_pair<GAUGE_LANDAU, ALGO_OR, CFG>;
     return algo == ALGO_SR ? k_sweep_pair<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_pair<GAUGE_COULOMB, ALGO_OR, CFG>;
+  }
+  if (fmt == FMT_ANCHOR) {
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_anchor<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_anchor<GAUGE_LANDAU, ALGO_OR, CFG>;
+    return algo == ALGO_SR ? k_sweep_anchor<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_anchor<GAUGE_COULOMB, ALGO_OR, CFG>;
   }
   return nullptr;
 }

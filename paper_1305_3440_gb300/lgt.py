@@ -25,7 +25,7 @@ LGT_OK, LGT_EINVAL, LGT_ENOMEM, LGT_ECUDA, LGT_ENOTCONV, LGT_EAGAIN, LGT_ETIMEOU
 LGT_LANDAU, LGT_COULOMB = 0, 1
 LGT_OR, LGT_SR = 0, 1
 LGT_FP64, LGT_FP32_18, LGT_FP32_12 = 0, 1, 2
-LGT_POLISH_PAIR, LGT_POLISH_FP64 = 0, 1
+LGT_POLISH_PAIR, LGT_POLISH_FP64, LGT_POLISH_ANCHOR = 0, 1, 2
 
 STATUS_NAMES = {0: "LGT_OK", 1: "LGT_EINVAL", 2: "LGT_ENOMEM", 3: "LGT_ECUDA", 4: "LGT_ENOTCONV",
                 5: "LGT_EAGAIN", 6: "LGT_ETIMEOUT", 7: "LGT_EBUSY", 8: "LGT_ECANCELLED", 9: "LGT_ENOTFOUND"}
@@ -38,7 +38,7 @@ class lgt_params(ctypes.Structure):
                 ("theta_tol", ctypes.c_double), ("theta_switch", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reunit_every", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("polish", ctypes.c_int32), ("reserved", ctypes.c_int32), ("omega_polish", ctypes.c_double)]
+                ("polish", ctypes.c_int32), ("launch_config", ctypes.c_int32), ("omega_polish", ctypes.c_double)]
 
 
 class lgt_result(ctypes.Structure):

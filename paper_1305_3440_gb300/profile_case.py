@@ -2,10 +2,13 @@
 
     python -m paper_1305_3440_gb300.profile_case [--dims 32 32 32 32] [--bulk fp32_12]
                                                  [--bulk-sweeps 8] [--polish-sweeps 4]
+                                                 [--polish anchor] [--launch-config K]
 
 Creates one context on cuda:0, runs `--bulk-sweeps` sweeps in the bulk
-precision, promotes (G applied to the FP64 input, pair storage) and runs
-`--polish-sweeps` polish sweeps, then one exact measurement.  A 32^4 lattice
+precision, promotes (G applied to the FP64 input, then the polish set-up) and runs
+`--polish-sweeps` polish sweeps, then one exact measurement.  Profilers
+serialise launches, which misleads the autotuner: pass `--launch-config` to
+profile the configuration a normal run picks.  A 32^4 lattice
 keeps the FP32 links (201 MB for 12 reals) larger than the 129 MB L2 while the
 whole context stays under 2 GB of device memory, and every half-sweep launch
 covers the same 524288 sites as a 32^4 gauge fixing.
@@ -25,6 +28,9 @@ def main(argv=None):
     ap.add_argument("--omega", type=float, default=1.7)
     ap.add_argument("--bulk-sweeps", type=int, default=8)
     ap.add_argument("--polish-sweeps", type=int, default=4)
+    ap.add_argument("--polish", default="anchor", choices=["anchor", "pair", "fp64"])
+    ap.add_argument("--launch-config", type=int, default=-1,
+                    help="force launch configuration k of the sweep kernels (-1: autotuned)")
     args = ap.parse_args(argv)
 
     import torch
@@ -34,7 +40,9 @@ def main(argv=None):
     dev = torch.from_numpy(U).cuda()
     bulk = {"fp32_12": lgt.LGT_FP32_12, "fp32_18": lgt.LGT_FP32_18, "fp64": lgt.LGT_FP64}[args.bulk]
     gauge = lgt.LGT_LANDAU if args.gauge == "landau" else lgt.LGT_COULOMB
-    p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=args.omega, bulk=bulk)
+    polish = {"anchor": lgt.LGT_POLISH_ANCHOR, "pair": lgt.LGT_POLISH_PAIR, "fp64": lgt.LGT_POLISH_FP64}[args.polish]
+    p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=args.omega, bulk=bulk, polish=polish,
+                               launch_config=args.launch_config + 1)
     ctx = lgt.lgt_create(p, dev)
     try:
         lgt.lgt_sweep(ctx, args.bulk_sweeps)

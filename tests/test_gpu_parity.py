@@ -311,12 +311,16 @@ def near_fixed_8():
     return out
 
 
-def promoted_ctx(lgt, U, **kw):
+POLISH = {"pair": (0, 2), "anchor": (2, 3)}  # polish kind -> (lgt_polish, phase after promotion)
+
+
+def promoted_ctx(lgt, U, polish="pair", **kw):
     kw.setdefault("omega_polish", 0.0)  # polish at the same omega as the oracle below
-    p = lgt.lgt_params_default(dims=U.shape[:4], bulk=lgt.LGT_FP32_12, polish=lgt.LGT_POLISH_PAIR, **kw)
+    pk, phase = POLISH[polish]
+    p = lgt.lgt_params_default(dims=U.shape[:4], bulk=lgt.LGT_FP32_12, polish=pk, **kw)
     ctx = lgt.lgt_create(p, U)
-    lgt.lgt_promote(ctx)  # G = 1: the pair field is the input to ~2^-48
-    assert lgt.lgt_get_progress(ctx)[2] == 2
+    lgt.lgt_promote(ctx)  # G = 1: the polish starts from the input (pairs: to ~2^-48)
+    assert lgt.lgt_get_progress(ctx)[2] == phase
     return ctx
 
 
@@ -333,17 +337,18 @@ def test_pair_storage_roundtrip(lgt):
     assert abs(F - m["F"]) < 1e-13 and abs(th - m["theta"]) < 1e-12 * m["theta"]
 
 
+@pytest.mark.parametrize("polish", list(POLISH))
 @pytest.mark.parametrize("gauge", list(GAUGES))
 @pytest.mark.parametrize("algo", list(ALGOS))
 @pytest.mark.parametrize("theta0,tol", [(1e-10, 2e-11), (1e-12, 1e-12)])
-def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo, theta0, tol):
+def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, polish, gauge, algo, theta0, tol):
     """Two polish sweeps against the FP64 oracle.  The rotation angles are FP32, so a
     sweep deviates from the FP64 trajectory by ~|g - 1| 2^-24 (the applied rotations
     stay exact gauge transformations): within 2e-11 at theta ~ 1e-10 (|g - 1| ~ 1e-5,
     SR doubling the angle) and within 1e-12 per link entry at theta ~ 1e-12."""
     U = near_fixed_8[(GAUGES[gauge], theta0)]
     kw = dict(gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=80)
-    ctx = promoted_ctx(lgt, U, **kw)
+    ctx = promoted_ctx(lgt, U, polish, **kw)
     try:
         lgt.lgt_sweep(ctx, 2)
         got = lgt.lgt_get_links(ctx, U.shape[:4])
@@ -354,14 +359,15 @@ def test_pair_polish_sweep_matches_oracle(lgt, near_fixed_8, gauge, algo, theta0
     assert np.abs(got - ref).max() < tol
 
 
+@pytest.mark.parametrize("polish", list(POLISH))
 @pytest.mark.parametrize("gauge", list(GAUGES))
-def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
+def test_pair_polish_is_an_exact_gauge_transformation(lgt, polish, gauge):
     """Even far from convergence (FP32-accurate angles) every pair update is a gauge
     transformation up to the ~2^-48 rounding of pair storage (~1e-14 per update, a
     random walk): after 20 sweeps plaquettes and unitarity hold to 3e-13 (FP32
     storage would give ~1e-7)."""
     U = synth.field(DIMS_RAGGED, 0.5, 14)
-    ctx = promoted_ctx(lgt, U, gauge=GAUGES[gauge], omega=1.7)
+    ctx = promoted_ctx(lgt, U, polish, gauge=GAUGES[gauge], omega=1.7)
     try:
         lgt.lgt_half_sweep(ctx, 0)
         half = lgt.lgt_get_links(ctx, DIMS_RAGGED)
@@ -378,11 +384,11 @@ def test_pair_polish_is_an_exact_gauge_transformation(lgt, gauge):
     assert e < 3e-13 and d < 3e-13
 
 
-@pytest.mark.parametrize("polish", ["pair", "fp64"])
+@pytest.mark.parametrize("polish", ["pair", "fp64", "anchor"])
 def test_fix_with_each_polish_kernel(lgt, polish):
     dims = (4, 8, 8, 8)
     U = synth.field(dims, 0.5, 15)
-    pk = lgt.LGT_POLISH_PAIR if polish == "pair" else lgt.LGT_POLISH_FP64
+    pk = {"pair": lgt.LGT_POLISH_PAIR, "fp64": lgt.LGT_POLISH_FP64, "anchor": lgt.LGT_POLISH_ANCHOR}[polish]
     p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, polish=pk, theta_switch=1e-8, max_sweeps=4000)
     ctx = lgt.lgt_create(p, U)
     try:
@@ -427,10 +433,11 @@ def test_full_size_one_sweep_32(lgt, field_32, bulk):
 
 
 def test_full_size_fix_32_properties(lgt, field_32):
-    """The benchmark's run (FP32-12 bulk + FP32-pair polish to 1e-14): the oracle
+    """The benchmark's run (FP32-12 bulk + anchored polish to 1e-14): the oracle
     certifies theta < 1e-14 on the returned field; every plaquette and unitarity are
-    kept to 3e-12 (pair storage rounds each link to ~2^-48 per update: ~1e-13 after
-    the ~1000 polish updates of a link, ~1e-12 at the extreme of 4e7 entries)."""
+    kept to 3e-12 (the output is G U' G^+ formed in FP64 with G orthonormalised in
+    FP64, so the bound is loose; the pair polish, which rounds each link to ~2^-48
+    per update, stays within it too)."""
     dims = (32, 32, 32, 32)
     p = lgt.lgt_params_default(dims=dims, omega=1.7, bulk=lgt.LGT_FP32_12, max_sweeps=20000)
     ctx = lgt.lgt_create(p, field_32)
@@ -472,8 +479,9 @@ def test_resume_is_bit_identical(lgt):
 
 # ------------------------------------------------ full size, sampled sites
 def _sampled_half_sweep_check(lgt, U, gauge, n_samples, seed):
-    """Even half-sweep on the GPU (FP32-12 bulk and FP32-pair polish kernels) against
-    the oracle's update of randomly sampled even sites from the same input."""
+    """Even half-sweep on the GPU (FP32-12 bulk kernel, and the default polish kernel
+    after promotion) against the oracle's update of randomly sampled even sites from
+    the same input."""
     from lattice_np import AXIS
     dims = U.shape[:4]
     rng = np.random.default_rng(seed)
@@ -535,3 +543,37 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
     ref17 = U.copy()
     O.sweeps(ref17, 2, omega=1.7)
     assert np.abs(got - ref17).max() > 1e-11
+
+
+@pytest.mark.parametrize("bulk", ["fp32_18", "fp32_12"])
+@pytest.mark.parametrize("gauge", list(GAUGES))
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_launch_configurations_are_bit_identical(lgt, bulk, gauge, algo):
+    """Every launch configuration (one or four threads per site, every block size)
+    forms K(x) in the same order and groups the fused estimate by the same 8 sites,
+    so sweeps (with reunitarisation) and whole ladder runs agree bit for bit; the
+    ragged lattice leaves a partial block in every configuration."""
+    U = synth.field(DIMS_RAGGED, 0.5, 21)
+    kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
+              reunit_every=2)
+    ref = None
+    for k in range(7):
+        out = gpu_run(lgt, U, 3, working=True, launch_config=k + 1, **kw)
+        if ref is None:
+            ref = out
+        assert np.array_equal(out, ref), f"launch configuration {k} differs after 3 sweeps"
+    ref = None
+    for k in range(7):
+        p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, theta_tol=1e-12, max_sweeps=3000, **kw)
+        ctx = lgt.lgt_create(p, U)
+        try:
+            st, res = lgt.lgt_fix(ctx)
+            links = lgt.lgt_get_links(ctx, U.shape[:4])
+            cfgs = lgt.lgt_get_stats(ctx).launch_config
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st == lgt.LGT_OK and cfgs[0] == k
+        got = (res.F, res.theta, res.sweeps_bulk, res.sweeps_fp64)
+        if ref is None:
+            ref, ref_links = got, links
+        assert got == ref and np.array_equal(links, ref_links), f"launch configuration {k}: {got} vs {ref}"
