@@ -121,7 +121,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..7: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..8: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
 } lgt_params;
@@ -142,9 +142,13 @@ typedef struct {
  *                         2: 256, <= 255; 3: 64, <= 128;
  *   four threads per site (one per direction; FP32 bulk sweeps only):
  *                         4: 128 threads, <= 128 registers; 5: 256, <= 128;
- *                         6: 128, <= 80.
- * A four-threads-per-site configuration applies to the bulk FP32 sweeps; the
- * sweeps after promotion then use configuration 0.  Every configuration forms
+ *                         6: 128, <= 80;
+ *   one thread per site, pipelined (FP32-12 bulk sweeps only):
+ *                         7: 128 threads, <= 255 registers, persistent blocks
+ *                            (2 per SM) that stage the next site's links and G
+ *                            in shared memory (cp.async) during the update.
+ * A configuration that a phase's kernel lacks (4-7 after promotion; 7 on
+ * FP32-18 links) falls back to configuration 0 for that phase.  Every configuration forms
  * K(x) and the fused estimate in the same order, so results do not depend on
  * it, only the time does. */
 

@@ -97,6 +97,23 @@ cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, cons
   SweepArgs a;
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   a.aux = aux;
+  if (lgt_cfg_pipe(cfg)) {  // persistent: lgt_cfg_minblocks blocks per SM over the (slice, tile) list
+    const int smem = LGT_PIPE_SMEM_PER_THREAD * block;
+    static int sms_of[64];  // per device ordinal, looked up once
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &sms = sms_of[dev & 63];
+    if (!sms) {
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)ceil_div(g.vs_half, block) * g.nt;
+    const int blocks = (int)(tiles < (long long)sms * lgt_cfg_minblocks(cfg) ? tiles : (long long)sms * lgt_cfg_minblocks(cfg));
+    fn<<<blocks, block, smem, st>>>(a, parity & 1);
+    return cudaGetLastError();
+  }
   dim3 grid(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), g.nt);
   fn<<<grid, block, 0, st>>>(a, parity & 1);
   return cudaGetLastError();

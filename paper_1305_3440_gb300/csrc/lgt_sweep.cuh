@@ -61,6 +61,91 @@ __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
   return philox4x32_10(ctr, key);
 }
 
+// The FP32 site update once the site's links are in registers (raw storage:
+// 12-real links with row 2 zero): K(x), the fused estimate terms, the local
+// update, the stores of the 8 links (and, for Coulomb gauge, the temporal
+// links), and G(x) <- g G(x).  gpre: G(x) already loaded (row 2 rebuilt), or
+// nullptr to load it here.
+template <int FMT, int GAUGE, int ALGO>
+__device__ __forceinline__ void site_update_f32(const SweepArgs &a, int p, const Coords &c, int i, const int nb[4],
+                                                float uf[4][18], float ub[4][18], const float *gpre, float acc[2]) {
+  typedef LinkIO<FMT> IO;
+  constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+  const int q = p ^ 1;
+  // K(x) = (k_0 + k_1) + (k_2 + k_3), k_mu the direction terms (k_0 = 0 for
+  // Coulomb gauge): the order of the four-threads-per-site layout
+  float W[18], k2[18];
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    float ka[18], kb[18];
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      const int mu = 2 * h + d;
+      float *k = d ? kb : ka;
+      if (mu < MU0) {
+        mat_zero(k);
+      } else if (IO::kCompressed) {
+        float ff[18], fb[18];
+#pragma unroll
+        for (int e = 0; e < 18; e++) {
+          ff[e] = uf[mu][e];
+          fb[e] = ub[mu][e];
+        }
+        rebuild_row2(ff);
+        rebuild_row2(fb);
+        k_term(k, ff, fb);
+      } else {
+        k_term(k, uf[mu], ub[mu]);
+      }
+    }
+    float *dst = h ? k2 : W;
+#pragma unroll
+    for (int e = 0; e < 18; e++) dst[e] = ka[e] + kb[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 18; e++) W[e] = W[e] + k2[e];
+  violation_of_K(W, acc[0], acc[1]);
+  uint4 draws = make_uint4(0, 0, 0, 0);
+  if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+  float gm[18];
+  local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+#pragma unroll
+  for (int mu = MU0; mu < 4; mu++) {
+    float r[18];
+    if (IO::kCompressed) rebuild_row2(uf[mu]);  // g U needs row 2 of U
+    mat_mul(gm, uf[mu], r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, p, mu, i, r);
+    mat_mul_dag(ub[mu], gm, r);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, q, mu, nb[mu], r);
+  }
+  if (GAUGE == GAUGE_COULOMB && a.transform_temporal) {
+    const int nb0 = cb_shift(a.g, c, 0, -1);
+    float u[18], r[18];
+    IO::load(a.links, a.g.vh, p, 0, i, u);
+    mat_mul(gm, u, r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, p, 0, i, r);
+    IO::load(a.links, a.g.vh, q, 0, nb0, u);
+    mat_mul_dag(u, gm, r);
+    if (a.reunit) reunitarise(r);
+    IO::store(a.links, a.g.vh, q, 0, nb0, r);
+  }
+  if (a.G) {
+    float gx[18], r[18];
+    if (gpre) {
+#pragma unroll
+      for (int e = 0; e < 18; e++) gx[e] = gpre[e];
+    } else {
+      GIO::load(a.G, a.g.vh, p, i, gx);
+    }
+    mat_mul(gm, gx, r);
+    if (a.reunit) reunitarise(r);
+    GIO::store(a.G, a.g.vh, p, i, r);
+  }
+}
+
 // FP32 link formats: all links of the site in registers.  12-real links stay
 // compressed (rows 0, 1) and row 2 is rebuilt where it is needed.
 template <int FMT, int GAUGE, int ALGO>
@@ -82,75 +167,106 @@ __device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t,
       IO::load_raw(a.links, a.g.vh, p, mu, i, uf[mu]);
       IO::load_raw(a.links, a.g.vh, q, mu, nb[mu], ub[mu]);
     }
-    // K(x) = (k_0 + k_1) + (k_2 + k_3), k_mu the direction terms (k_0 = 0 for
-    // Coulomb gauge): the order of the four-threads-per-site layout
-    float W[18], k2[18];
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      float ka[18], kb[18];
-#pragma unroll
-      for (int d = 0; d < 2; d++) {
-        const int mu = 2 * h + d;
-        float *k = d ? kb : ka;
-        if (mu < MU0) {
-          mat_zero(k);
-        } else if (IO::kCompressed) {
-          float ff[18], fb[18];
-#pragma unroll
-          for (int e = 0; e < 18; e++) {
-            ff[e] = uf[mu][e];
-            fb[e] = ub[mu][e];
-          }
-          rebuild_row2(ff);
-          rebuild_row2(fb);
-          k_term(k, ff, fb);
-        } else {
-          k_term(k, uf[mu], ub[mu]);
-        }
-      }
-      float *dst = h ? k2 : W;
-#pragma unroll
-      for (int e = 0; e < 18; e++) dst[e] = ka[e] + kb[e];
-    }
-#pragma unroll
-    for (int e = 0; e < 18; e++) W[e] = W[e] + k2[e];
-    violation_of_K(W, acc[0], acc[1]);
-    uint4 draws = make_uint4(0, 0, 0, 0);
-    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
-    float gm[18];
-    local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
-#pragma unroll
-    for (int mu = MU0; mu < 4; mu++) {
-      float r[18];
-      if (IO::kCompressed) rebuild_row2(uf[mu]);  // g U needs row 2 of U
-      mat_mul(gm, uf[mu], r);
-      if (a.reunit) reunitarise(r);
-      IO::store(a.links, a.g.vh, p, mu, i, r);
-      mat_mul_dag(ub[mu], gm, r);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
-      if (a.reunit) reunitarise(r);
-      IO::store(a.links, a.g.vh, q, mu, nb[mu], r);
-    }
-    if (GAUGE == GAUGE_COULOMB && a.transform_temporal) {
-      const int nb0 = cb_shift(a.g, c, 0, -1);
-      float u[18], r[18];
-      IO::load(a.links, a.g.vh, p, 0, i, u);
-      mat_mul(gm, u, r);
-      if (a.reunit) reunitarise(r);
-      IO::store(a.links, a.g.vh, p, 0, i, r);
-      IO::load(a.links, a.g.vh, q, 0, nb0, u);
-      mat_mul_dag(u, gm, r);
-      if (a.reunit) reunitarise(r);
-      IO::store(a.links, a.g.vh, q, 0, nb0, r);
-    }
-    if (a.G) {
-      float gx[18], r[18];
-      GIO::load(a.G, a.g.vh, p, i, gx);
-      mat_mul(gm, gx, r);
-      if (a.reunit) reunitarise(r);
-      GIO::store(a.G, a.g.vh, p, i, r);
-    }
+    site_update_f32<FMT, GAUGE, ALGO>(a, p, c, i, nb, uf, ub, nullptr, acc);
   }
   fused_store<float, 1>(a, p, t, bx, acc);
+}
+
+// 16-byte asynchronous copy global -> shared (cp.async, L1 bypassed) and its
+// group bookkeeping
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// chunks of one site staged by the pipelined layout: 8 links x 3 (FP32-12) + G x 3
+constexpr int LGT_PIPE_CHUNKS = 27;
+
+// FP32-12, pipelined: persistent blocks walk the (slice, tile) list; while a
+// thread updates its current site, the links and G of its next site are on the
+// way into shared memory (cp.async), so each thread keeps a site's loads in
+// flight through its compute phase.  A thread reads back only the chunks it
+// staged itself (layout [buffer][chunk][thread]: conflict-free 16-byte reads),
+// so no block barrier is needed; cp.async.wait_group orders each thread's own
+// copies.  The site update is the one-thread body's, so results are the same.
+template <int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, int tiles_x) {
+  extern __shared__ float4 lgt_stage[];  // [2][LGT_PIPE_CHUNKS][blockDim.x]
+  typedef LinkIO<FMT_F32_12> IO;
+  constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+  const int T = (int)blockDim.x, tid = (int)threadIdx.x, q = p ^ 1;
+  const int total = tiles_x * a.g.nt;
+  const float4 *L = reinterpret_cast<const float4 *>(a.links);
+  const float4 *Gs = reinterpret_cast<const float4 *>(a.G);
+  auto issue = [&](int tile, int buf) {
+    if (tile < total) {
+      const int t = tile / tiles_x, j = (tile - t * tiles_x) * T + tid;
+      if (!(a.active && !a.active[t]) && j < a.g.vs_half) {
+        const Coords c = coords_in_slice(a.g, p, t, j);
+        const int i = t * a.g.vs_half + j;
+        float4 *st = lgt_stage + (size_t)buf * LGT_PIPE_CHUNKS * T + tid;
+#pragma unroll
+        for (int mu = MU0; mu < 4; mu++) {
+          const int nb = cb_shift(a.g, c, mu, -1);
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            cp_async16(st + (mu * 6 + k) * T, L + (size_t)((p * 4 + mu) * 3 + k) * a.g.vh + i);
+            cp_async16(st + (mu * 6 + 3 + k) * T, L + (size_t)((q * 4 + mu) * 3 + k) * a.g.vh + nb);
+          }
+        }
+        if (Gs) {
+#pragma unroll
+          for (int k = 0; k < 3; k++) cp_async16(st + (24 + k) * T, Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+        }
+      }
+    }
+    cp_async_commit();  // possibly empty: every iteration commits exactly one group
+  };
+  int tile = (int)blockIdx.x;
+  issue(tile, 0);
+  for (int it = 0; tile < total; it++, tile += (int)gridDim.x) {
+    issue(tile + (int)gridDim.x, (it + 1) & 1);
+    cp_async_wait<1>();  // this thread's copies of the current tile have landed
+    const int t = tile / tiles_x, bx = tile - t * tiles_x;
+    if (a.active && !a.active[t]) continue;  // the whole tile belongs to one slice
+    const int j = bx * T + tid;
+    float acc[2] = {0.0f, 0.0f};
+    if (j < a.g.vs_half) {
+      const Coords c = coords_in_slice(a.g, p, t, j);
+      const int i = t * a.g.vs_half + j;
+      const float4 *st = lgt_stage + (size_t)(it & 1) * LGT_PIPE_CHUNKS * T + tid;
+      float uf[4][18], ub[4][18], gx[18];
+      int nb[4];
+#pragma unroll
+      for (int mu = MU0; mu < 4; mu++) {
+        nb[mu] = cb_shift(a.g, c, mu, -1);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const float4 f = st[(mu * 6 + k) * T], b = st[(mu * 6 + 3 + k) * T];
+          uf[mu][4 * k] = f.x, uf[mu][4 * k + 1] = f.y, uf[mu][4 * k + 2] = f.z, uf[mu][4 * k + 3] = f.w;
+          ub[mu][4 * k] = b.x, ub[mu][4 * k + 1] = b.y, ub[mu][4 * k + 2] = b.z, ub[mu][4 * k + 3] = b.w;
+        }
+#pragma unroll
+        for (int e = 12; e < 18; e++) uf[mu][e] = ub[mu][e] = 0.0f;
+      }
+      if (Gs) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const float4 v = st[(24 + k) * T];
+          gx[4 * k] = v.x, gx[4 * k + 1] = v.y, gx[4 * k + 2] = v.z, gx[4 * k + 3] = v.w;
+        }
+        rebuild_row2(gx);
+      }
+      site_update_f32<FMT_F32_12, GAUGE, ALGO>(a, p, c, i, nb, uf, ub, Gs ? gx : nullptr, acc);
+    }
+    fused_store<float, 1>(a, p, t, bx, acc);
+  }
+  cp_async_wait<0>();  // nothing of this thread's in flight at exit
 }
 
 

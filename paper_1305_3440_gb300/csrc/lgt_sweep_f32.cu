@@ -1,20 +1,27 @@
 // lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
 // storage), one instantiation per gauge, algorithm and launch configuration
-// (one or four threads per site).
+// (one or four threads per site; pipelined through shared memory).
 #include "lgt_sweep.cuh"
 
 namespace lgt {
 
 template <int FMT, int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs a, int p) {
-  if constexpr (lgt_cfg_quad(CFG)) sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
-  else sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  if constexpr (lgt_cfg_quad(CFG)) {
+    sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
+  } else if constexpr (lgt_cfg_pipe(CFG)) {
+    if constexpr (FMT == FMT_F32_12)
+      sweep_body_f32_pipe<GAUGE, ALGO>(a, p, (a.g.vs_half + (int)blockDim.x - 1) / (int)blockDim.x);
+  } else {
+    sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  }
 }
 
 template <int CFG>
 static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
 #define LGT_PICK(F, G, A) \
   if (fmt == F && gauge == G && algo == A) return k_sweep_f32<F, G, A, CFG>;
+  if (!lgt_cfg_supported(fmt, CFG)) return nullptr;
   LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_OR)
   LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_SR)
   LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_OR)
@@ -36,6 +43,7 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 4: return pick_cfg<4>(fmt, gauge, algo);
     case 5: return pick_cfg<5>(fmt, gauge, algo);
     case 6: return pick_cfg<6>(fmt, gauge, algo);
+    case 7: return pick_cfg<7>(fmt, gauge, algo);
   }
   return nullptr;
 }

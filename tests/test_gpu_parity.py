@@ -549,21 +549,22 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
 @pytest.mark.parametrize("gauge", list(GAUGES))
 @pytest.mark.parametrize("algo", list(ALGOS))
 def test_launch_configurations_are_bit_identical(lgt, bulk, gauge, algo):
-    """Every launch configuration (one or four threads per site, every block size)
-    forms K(x) in the same order and groups the fused estimate by the same 8 sites,
+    """Every launch configuration (one or four threads per site, every block size,
+    pipelined through shared memory) forms K(x) in the same order and groups the fused estimate by the same 8 sites,
     so sweeps (with reunitarisation) and whole ladder runs agree bit for bit; the
     ragged lattice leaves a partial block in every configuration."""
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
+    ncfg = 8
     ref = None
-    for k in range(7):
+    for k in range(ncfg):
         out = gpu_run(lgt, U, 3, working=True, launch_config=k + 1, **kw)
         if ref is None:
             ref = out
         assert np.array_equal(out, ref), f"launch configuration {k} differs after 3 sweeps"
     ref = None
-    for k in range(7):
+    for k in range(ncfg):
         p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, theta_tol=1e-12, max_sweeps=3000, **kw)
         ctx = lgt.lgt_create(p, U)
         try:
@@ -572,7 +573,8 @@ def test_launch_configurations_are_bit_identical(lgt, bulk, gauge, algo):
             cfgs = lgt.lgt_get_stats(ctx).launch_config
         finally:
             lgt.lgt_destroy(ctx)
-        assert st == lgt.LGT_OK and cfgs[0] == k
+        supported = k != 7 or bulk == "fp32_12"  # the pipelined layout stages 12-real links only
+        assert st == lgt.LGT_OK and cfgs[0] == (k if supported else 0)
         got = (res.F, res.theta, res.sweeps_bulk, res.sweeps_fp64)
         if ref is None:
             ref, ref_links = got, links

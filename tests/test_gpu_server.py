@@ -110,7 +110,13 @@ def test_server_graph_replay_changes_nothing(lgt):
         assert np.array_equal(l1, l2)
     # tick counts depend on when the submissions arrive, not on the graphs
     assert cd["graph_launches"] == 0 and cd["graph_captures"] == 0 and cd["ticks"] > 0
-    assert 0 < cg["graph_captures"] <= 16 and cg["graph_launches"] > cg["ticks"] // 2, cg
+    assert 0 < cg["graph_captures"] <= 16 and cg["graph_launches"] > 0, cg
+    # one job alone: its launch shape changes only at the start, at promotion and
+    # at certification, so all but a few ticks are replays
+    one = {}
+    (st, res, _), = run_server(lgt, [JOBS[0]], counters=one)
+    assert st == lgt.LGT_OK
+    assert one["graph_launches"] >= one["ticks"] - 12, one
 
 
 def test_server_matches_single_context_and_oracle(lgt):
