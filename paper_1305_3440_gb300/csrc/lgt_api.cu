@@ -649,6 +649,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   const int64_t bulk0 = c->sweeps_bulk, fp640 = c->sweeps_fp64;
   Meas m;
   lgt_status st;
+  bool promoted = false;
   if (c->phase == 0) {
     // bulk FP32 phase: until the working field's theta drops below theta_switch
     // or stops improving (the FP32 rounding floor)
@@ -673,11 +674,22 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     }
     st = promote(c);
     if (st != LGT_OK) return st;
+    promoted = true;
   }
-  // FP64 phase to theta < tol
+  // FP64-accurate phase to theta < tol
   const double tol = c->prm.theta_tol;
-  st = measure(c, 0, coulomb ? tol : -1.0, &m);
-  if (st != LGT_OK) return st;
+  bool certified = false;  // m is an exact measurement with the plaquette
+  if (promoted) {
+    // the promoted field carries the rounding of the FP32 G (theta ~ 1e-8, far
+    // above any tolerance): polish first, every slice taking part until the
+    // first estimate
+    LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)c->g.nt, c->stream));
+    c->active_slices = c->g.nt;
+    m.theta = HUGE_VAL;
+  } else {
+    st = measure(c, 0, coulomb ? tol : -1.0, &m);
+    if (st != LGT_OK) return st;
+  }
   while (m.theta >= tol && remaining > 0) {
     const int n = (int)(remaining < k ? remaining : k);
     st = run_sweeps(c, n, coulomb ? 1 : 0);
@@ -685,17 +697,21 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     remaining -= n;
     st = estimate(c, coulomb ? tol : -1.0, &m);
     if (st != LGT_OK) return st;
+    certified = false;
     if (m.theta < tol) {  // the estimate says converged: certify with the exact measurement
-      st = measure(c, 0, coulomb ? tol : -1.0, &m);
+      st = measure(c, 1, coulomb ? tol : -1.0, &m);
       if (st != LGT_OK) return st;
+      certified = true;
     }
   }
   // all slices active again for later calls
   LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)c->g.nt, c->stream));
   c->active_slices = c->g.nt;
-  Meas fin;
-  st = measure(c, 1, -1.0, &fin);
-  if (st != LGT_OK) return st;
+  Meas fin = m;  // the certifying measurement covers every slice and the plaquette
+  if (!certified) {
+    st = measure(c, 1, -1.0, &fin);
+    if (st != LGT_OK) return st;
+  }
   const bool conv = m.theta < tol;
   if (res) {
     res->F = fin.F;

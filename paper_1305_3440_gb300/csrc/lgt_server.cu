@@ -8,13 +8,16 @@
 //      format x gauge x algorithm) covers the sites of all live jobs of that
 //      variant;
 //   3. one batched reduction of the sweeps' fused estimates gives each job's
-//      F and theta; jobs that start, were just promoted, or whose estimate
-//      says converged get a batched exact measurement instead (one
-//      device->host copy for all jobs);
+//      F and theta; jobs that start, or whose estimate says converged, get a
+//      batched exact measurement instead (with the plaquette when it
+//      certifies; one device->host copy for all jobs);
 //   4. per job, the same ladder decisions as lgt_fix (Sec. 4 driver): bulk FP32
 //      until theta < theta_switch (or the FP32 floor), promotion, polishing to
-//      theta < theta_tol, or max_sweeps; finished jobs are measured once more,
-//      copied out and their memory released, which admits the next ones.
+//      theta < theta_tol, or max_sweeps; finished jobs are copied out (measured
+//      once more unless a certifying measurement holds the result) and their
+//      memory released, which admits the next ones.
+// The tick's launch sequence is captured into a CUDA graph and replayed while
+// its shape repeats (see tick()).
 // A job's sequence of kernels and decisions depends only on its own
 // parameters, so its result is bit-identical alone and in any mix.
 #include <cuda_runtime.h>
@@ -76,6 +79,7 @@ struct Job {
   double best = 0.0;
   int stall = 0;
   bool measure_only = true;  // next tick measures without sweeping
+  bool certify = false;      // that measurement certifies convergence (with the plaquette)
   int nthis = 0;             // sweeps in the current tick
   int nbx = 0;
 
@@ -421,7 +425,7 @@ cudaError_t tick(lgt_server *s) {
     for (; k < morder.size() && morder[k]->work_fmt() == seg.fmt; k++) {
       Job *j = morder[k];
       BatchMeas r;
-      fill_meas_args(&r.a, j->g, j->work_links(), j->ws, 0, coulomb_target(j));
+      fill_meas_args(&r.a, j->g, j->work_links(), j->ws, j->certify ? 1 : 0, coulomb_target(j));
       r.block_begin = seg.blocks;
       r.nbx = j->nbx;
       mrows.push_back(r);
@@ -482,8 +486,10 @@ cudaError_t tick(lgt_server *s) {
 cudaError_t collect(lgt_server *s, Job *j) {
   cudaError_t e = anchor_materialise(s, j);
   if (e != cudaSuccess) return e;
-  e = launch_measure(j->work_fmt(), j->g, j->work_links(), j->ws, 1, -1.0, kServerBlock, s->stream);
-  if (e != cudaSuccess) return e;
+  if (!j->certify) {  // a certifying measurement already holds F, theta and the plaquette
+    e = launch_measure(j->work_fmt(), j->g, j->work_links(), j->ws, 1, -1.0, kServerBlock, s->stream);
+    if (e != cudaSuccess) return e;
+  }
   void *stage = nullptr;
   if ((e = dev_alloc(s, &stage, aos_bytes_of(j->g))) != cudaSuccess) return e;
   if (j->phase >= 1) e = launch_egress(j->work_fmt(), j->g, j->u64, (double *)stage, s->stream);
@@ -514,7 +520,10 @@ cudaError_t promote_job(lgt_server *s, Job *j) {
     j->phase = 3;
     j->anchored = j->d_dirty = false;
   }
-  j->measure_only = true;
+  // as lgt_fix: no measurement of the promoted field (its theta is far above any
+  // tolerance); every slice takes part until the first estimate
+  if (e == cudaSuccess) e = cudaMemsetAsync(j->ws.active, 1, (size_t)j->g.nt, s->stream);
+  j->measure_only = false;
   return e;
 }
 
@@ -593,6 +602,8 @@ void worker_main(lgt_server *s) {
           j->sweep_index += (uint64_t)j->nthis;
         }
         j->measure_only = false;
+        const bool certified = exact && j->certify;
+        j->certify = false;
         if (j->phase == 0) {
           if (exact) {
             j->best = theta;
@@ -608,10 +619,12 @@ void worker_main(lgt_server *s) {
           }
         } else if (theta < j->prm.theta_tol) {
           if (exact) {
+            j->certify = certified;  // collect() reuses the certifying measurement
             finished.push_back(j);
             fstatus.push_back(LGT_OK);
           } else {
             j->measure_only = true;  // certify next tick
+            j->certify = true;
           }
         } else if (j->remaining <= 0) {
           finished.push_back(j);
