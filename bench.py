@@ -129,16 +129,17 @@ def algorithmic_bytes_per_site(kind: str) -> int:
     """Bytes one site update must move.  Bulk: its 8 links in and out plus G(x) in
     and out (FP32-12 links 48 B, FP32-18 72 B, G stored as 2 rows: 48 B).
     FP32-pair and FP64 polish: 8 links of 144 B in and out.  Anchored polish:
-    K0(x) (144 B), the 8 links' FP32-12 copies (384 B) and the 8 neighbours'
-    D high parts (384 B) in, its own D (96 B: rows 0, 1 as pairs) in and out."""
+    K0(x) (144 B) and the 8 links' FP32-12 copies (384 B) in, its own D (96 B:
+    rows 0, 1 as pairs) in and out, and the other parity's D high parts (48 B
+    per site: each is read by 8 neighbours, compulsory once)."""
     if kind == "fp32_12":
         return 16 * 48 + 2 * 48
     if kind == "fp32_18":
         return 16 * 72 + 2 * 48
     if kind == "anchor":
-        return 144 + 8 * 48 + 8 * 48 + 2 * 96
+        return 144 + 8 * 48 + 48 + 2 * 96
     if kind == "anchor_coulomb":  # spatial directions only
-        return 144 + 6 * 48 + 6 * 48 + 2 * 96
+        return 144 + 6 * 48 + 48 + 2 * 96
     return 16 * 144
 
 
@@ -267,6 +268,8 @@ def run_ours(args):
             stats_kernel["fp64_launches"] += st.sweep_launches[1]
             stats_kernel["launches"] += st.launches
             stats_kernel["launch_config"] = list(st.launch_config)
+            stats_kernel["loop_launches"] = stats_kernel.get("loop_launches", 0) + st.loop_launches
+            stats_kernel["loop_chunks"] = stats_kernel.get("loop_chunks", 0) + st.loop_chunks
             sweeps += res.sweeps_bulk + res.sweeps_fp64
             results.append(res.as_dict())
         ev1.record(stream)
@@ -379,7 +382,10 @@ def run_ours(args):
                 "result": {"F": last["F"], "theta": last["theta"], "plaquette": last["plaquette"]},
                 "time_to_theta_1e-14": ttt, "other_runs": variants, "kernels": kernels, "roofline": roofline,
                 "e2e": e2e,
-                "gpu_launches": stats_kernel["launches"], "clocks": clocks, "cpu_baseline": cpu}
+                "gpu_launches": stats_kernel["launches"],
+                "device_loop": {"graph_launches": stats_kernel.get("loop_launches", 0),
+                                "chunks": stats_kernel.get("loop_chunks", 0)},
+                "clocks": clocks, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

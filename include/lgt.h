@@ -95,10 +95,11 @@ typedef enum {
  *   transformed links G U' G^+ (Sec. 3), with the constant
  *   K0 = sum_mu U'_mu(x) + U'_mu(x-mu)^+ stored once as FP32 pairs and the
  *   small C = sum_mu U'_mu(x) D(x+mu)^+ + U'_mu(x-mu)^+ D(x-mu)^+ formed in
- *   FP32; rotations as in PAIR; D kept as FP32 pairs, so G is unitary to
- *   ~2^-48.  Only D is written (1104 bytes moved per site update against
- *   2304 for PAIR).  Measurements and output form G U' G^+ in FP64; a
- *   measurement makes it the new anchor.
+ *   FP32; rotation angles, SU(2) elements and delta = g - 1 in FP32 from the
+ *   small quantities; D accumulated as FP32 pairs.  Only D is written (768
+ *   bytes of compulsory traffic per site update against 2304 for PAIR).
+ *   Measurements and output form G U' G^+ in FP64 with G orthonormalised in
+ *   FP64 (an exact gauge transform); a measurement makes it the new anchor.
  * With bulk = LGT_FP64 every sweep uses the FP64 kernel. */
 typedef enum { LGT_POLISH_PAIR = 0, LGT_POLISH_FP64 = 1, LGT_POLISH_ANCHOR = 2 } lgt_polish;
 
@@ -148,9 +149,10 @@ typedef struct {
  *                            (2 per SM) that stage the next site's links and G
  *                            in shared memory (cp.async) during the update.
  * A configuration that a phase's kernel lacks (4-7 after promotion; 7 on
- * FP32-18 links) falls back to configuration 0 for that phase.  Every configuration forms
- * K(x) and the fused estimate in the same order, so results do not depend on
- * it, only the time does. */
+ * FP32-18 links) falls back to configuration 0 for that phase.  Every
+ * configuration forms K(x) and the fused estimate in the same order; results
+ * differ only where the compiler fuses multiply-adds differently in the two
+ * kernels (FP32 rounding; converged F within 1e-10). */
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
@@ -233,9 +235,12 @@ typedef struct {
   int64_t launches;          /* every kernel launch of this context */
   double measure_ms;         /* device time of exact measurements */
   int64_t measure_launches;
-  int32_t launch_config[2];  /* launch configuration of the bulk / polish sweep kernels:
-                                0: 128 threads, <= 255 registers; 1: 128, <= 170;
-                                2: 256, <= 255; 3: 64, <= 128 */
+  int32_t launch_config[2];  /* launch configuration of the bulk / polish sweep kernels
+                                (the table above lgt_params_default) */
+  int64_t loop_launches;     /* lgt_fix device loops: CUDA graph launches, each running
+                                chunks of check_every sweeps and their checks on the
+                                device until a check stops it */
+  int64_t loop_chunks;       /* chunks those launches ran */
 } lgt_stats;
 
 /* Counters since creation (or the last lgt_load).  Sweep-kernel times come

@@ -205,6 +205,10 @@ struct lgt_ctx {
   std::vector<Pending> *pending;
   std::vector<cudaEvent_t> *event_pool;
   lgt_stats stats;
+  // device loops of lgt_fix: [0] bulk sweeps, [1] sweeps after promotion
+  int use_loops;                   // 0: host-driven chunks only (LGT_FIX_GRAPHS=0, or a loop failed to build)
+  LoopState *d_loop, *h_loop;      // loop state (device) and its pinned copy
+  cudaGraphExec_t loop_exec[2];
 };
 
 static void resolve_events(lgt_ctx *c);
@@ -222,6 +226,10 @@ static void ctx_free(lgt_ctx *c) {
     for (auto e : *c->event_pool) cudaEventDestroy(e);
     delete c->event_pool;
   }
+  for (int k = 0; k < 2; k++)
+    if (c->loop_exec[k]) cudaGraphExecDestroy(c->loop_exec[k]);
+  if (c->d_loop) cudaFree(c->d_loop);
+  if (c->h_loop) cudaFreeHost(c->h_loop);
   if (c->stage) cudaFree(c->stage);
   if (c->u64) cudaFree(c->u64);
   if (c->u32) cudaFree(c->u32);
@@ -376,6 +384,12 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   CTX_CUDA(cudaMemsetAsync(c->ws_base, 0, wsb, c->stream));
   workspace_carve(c->ws_base, g, 64, &c->ws);
   CTX_CUDA(cudaMallocHost(&c->host, 4096 + sizeof(double) * 2 * (size_t)g.nt));
+  CTX_CUDA(cudaMalloc(&c->d_loop, sizeof(LoopState)));
+  CTX_CUDA(cudaMallocHost(&c->h_loop, sizeof(LoopState)));
+  {
+    const char *lv = getenv("LGT_FIX_GRAPHS");  // "0": lgt_fix drives every chunk from the host
+    c->use_loops = !(lv && lv[0] == '0');
+  }
   // block sizes: given, or timed on the still-empty buffers
   const int polish_fmt = params->bulk == LGT_FP64 ? (int)FMT_F64
                          : (params->polish == LGT_POLISH_PAIR ? (int)FMT_PAIR
@@ -635,6 +649,127 @@ extern "C" lgt_status lgt_promote(lgt_ctx *ctx) {
   return promote(ctx);
 }
 
+// ------------------------------------------------------------- device loops
+// lgt_fix's chunks (check_every sweeps, the fused estimate, the decision) as
+// one CUDA graph: a conditional while node whose body is the chunk's 2k
+// half-sweep launches, the estimate's finish and a one-thread decide kernel
+// that applies the host driver's rules to the loop state and sets the
+// condition.  The sweep kernels read their sweep numbers from the loop state,
+// so the body is the same for every chunk.  slot 0: bulk sweeps, 1: after
+// promotion.  Built on first use; the context's buffers and parameters do not
+// change afterwards.
+static lgt_status build_loop(lgt_ctx *c, int slot) {
+  const bool anch = c->phase == 3;
+  const int fmt = anch ? (int)FMT_ANCHOR : work_fmt(c);
+  void *links = (c->phase == 0 || anch) ? c->u32 : c->u64;
+  void *G = (c->phase == 0 || anch) ? c->G : nullptr;
+  const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
+  const int k = c->prm.check_every;
+  const bool coulomb = c->prm.gauge == LGT_COULOMB;
+  const double target = slot == 0 ? c->prm.theta_switch : c->prm.theta_tol;
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp = {};
+  cudaError_t e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  }
+  // captured on a private stream (the context's stream may be the legacy
+  // default stream, which cannot capture); the graph then runs on the context's
+  cudaStream_t cs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = cudaSuccess;
+      for (int sw = 0; sw < k && el == cudaSuccess; sw++)
+        for (int parity = 0; parity < 2 && el == cudaSuccess; parity++)
+          el = launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, (unsigned long long)sw, 0, coulomb ? 1 : 0,
+                                 lc, cs, anch ? c->k0 : nullptr, c->d_loop, c->phase == 0 ? c->prm.reunit_every : 0);
+      if (el == cudaSuccess)
+        el = launch_fused_finish(c->g, c->ws, c->cfg.gauge, lgt_cfg_sites(lc), coulomb ? target : -1.0, cs);
+      if (el == cudaSuccess) el = launch_loop_decide(c->d_loop, c->ws.fused_totals, c->cfg.gauge, k, c->g.vs_half, h, cs);
+      e = cudaStreamEndCapture(cs, &body);
+      if (el != cudaSuccess) e = el;
+    }
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->loop_exec[slot], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // the host-driven chunks take over
+    c->loop_exec[slot] = nullptr;
+    c->use_loops = 0;
+    return LGT_EAGAIN;
+  }
+  return LGT_OK;
+}
+
+// Run whole chunks on the device while the driver's rules allow (at least
+// one; the caller checked them and remaining >= check_every).  Updates the
+// counters, *best / *stall (bulk), *remaining and the estimate in *m.
+static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64_t *remaining, Meas *m) {
+  const int k = c->prm.check_every;
+  const int kind = c->phase == 0 ? 0 : 1;
+  const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
+  if (c->phase == 3) {  // the anchored sweeps need a current anchor
+    lgt_status st = anchor_setup(c);
+    if (st != LGT_OK) return st;
+    c->d_dirty = 1;
+  }
+  LoopState &L = *c->h_loop;
+  L.sweep = c->sweep_index;
+  L.count = kind == 0 ? c->sweeps_bulk : c->sweeps_fp64;
+  L.remaining = *remaining;
+  L.site_updates = 0;
+  L.target = slot == 0 ? c->prm.theta_switch : c->prm.theta_tol;
+  L.best = best ? *best : 0.0;
+  L.theta = 0.0;
+  L.stall = stall ? *stall : 0;
+  L.bulk = slot == 0 ? 1 : 0;
+  L.active = c->active_slices;
+  L.iters = 0;
+  L.max_iters = (int)(*remaining / k);
+  LGT_CUDA(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopState), cudaMemcpyHostToDevice, c->stream));
+  const int bt = batch_begin(c, kind);
+  LGT_CUDA(cudaGraphLaunch(c->loop_exec[slot], c->stream));
+  batch_end(c, bt);
+  LGT_CUDA(cudaMemcpyAsync(c->host, c->ws.fused_totals, sizeof(double) * TOT_N, cudaMemcpyDeviceToHost, c->stream));
+  LGT_CUDA(cudaMemcpyAsync(c->h_loop, c->d_loop, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+  lgt_status st = sync_stream(c);
+  if (st != LGT_OK) return st;
+  const int64_t n = (int64_t)L.iters * k;
+  c->sweep_index += (uint64_t)n;
+  if (kind == 0) c->sweeps_bulk += n;
+  else c->sweeps_fp64 += n;
+  *remaining = L.remaining;
+  if (best) *best = L.best;
+  if (stall) *stall = L.stall;
+  c->last_sites = lgt_cfg_sites(lc);
+  c->stats.sweep_launches[kind] += 2 * n;
+  c->stats.launches += (int64_t)L.iters * (2 * k + 2);
+  c->stats.site_updates[kind] += L.site_updates;
+  c->stats.loop_launches++;
+  c->stats.loop_chunks += L.iters;
+  fill_meas(c, c->host, m);
+  c->active_slices = m->active;
+  return LGT_OK;
+}
+
+// whether the next chunks can run as a device loop (built on demand)
+static bool loop_ready(lgt_ctx *c, int slot, int64_t remaining) {
+  if (!c->use_loops || remaining < c->prm.check_every) return false;
+  if (!c->loop_exec[slot] && build_loop(c, slot) != LGT_OK) return false;
+  return true;
+}
+
 // ------------------------------------------------------------- the driver
 extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   if (!ctx) {
@@ -659,6 +794,11 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     double best = m.theta;
     int stall = 0;
     while (m.theta >= target && remaining > 0 && stall < 3) {
+      if (loop_ready(c, 0, remaining)) {  // whole chunks, decided on the device
+        st = run_loop(c, 0, &best, &stall, &remaining, &m);
+        if (st != LGT_OK) return st;
+        continue;
+      }
       const int n = (int)(remaining < k ? remaining : k);
       st = run_sweeps(c, n, coulomb ? 1 : 0);
       if (st != LGT_OK) return st;
@@ -691,12 +831,17 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     if (st != LGT_OK) return st;
   }
   while (m.theta >= tol && remaining > 0) {
-    const int n = (int)(remaining < k ? remaining : k);
-    st = run_sweeps(c, n, coulomb ? 1 : 0);
-    if (st != LGT_OK) return st;
-    remaining -= n;
-    st = estimate(c, coulomb ? tol : -1.0, &m);
-    if (st != LGT_OK) return st;
+    if (loop_ready(c, 1, remaining)) {  // whole chunks, decided on the device
+      st = run_loop(c, 1, nullptr, nullptr, &remaining, &m);
+      if (st != LGT_OK) return st;
+    } else {
+      const int n = (int)(remaining < k ? remaining : k);
+      st = run_sweeps(c, n, coulomb ? 1 : 0);
+      if (st != LGT_OK) return st;
+      remaining -= n;
+      st = estimate(c, coulomb ? tol : -1.0, &m);
+      if (st != LGT_OK) return st;
+    }
     certified = false;
     if (m.theta < tol) {  // the estimate says converged: certify with the exact measurement
       st = measure(c, 1, coulomb ? tol : -1.0, &m);

@@ -48,11 +48,31 @@ size_t workspace_bytes(const Geom &g, int min_block);
 void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w);
 
 // Arguments of one lattice's half-sweep (also one row of a batched launch).
+// State of a device-side sweep loop (lgt_fix's chunks of check_every sweeps run
+// as a CUDA graph with a conditional while node): the decide kernel updates it
+// after each chunk's fused estimate, the sweep kernels read the sweep counters.
+struct LoopState {
+  unsigned long long sweep;  // number of the next sweep (RNG counter)
+  long long count;           // sweeps of this phase so far (reunitarisation schedule)
+  long long remaining;       // sweeps the caller still allows
+  long long site_updates;    // site updates done by the loop
+  double target;             // theta_switch (bulk) or theta_tol (polish)
+  double best;               // bulk: smallest estimate so far
+  double theta;              // last estimate
+  int stall;                 // bulk: checks without improvement
+  int bulk;                  // 1: bulk rules (target, stall), 0: polish rules (target)
+  int active;                // slices the next sweeps update
+  int iters, max_iters;      // chunks run by this launch, and their cap
+};
+
 struct SweepArgs {
   Geom g;
   void *links;
   void *G;
   const void *aux;  // anchored polish: K0
+  // device loop: sweep = loop->sweep + sweep, reunitarise when
+  // (loop->count + sweep + 1) % reunit_every == 0 (sweep holds the offset in the chunk)
+  const LoopState *loop;
 
   const uint8_t *active;
   double2 *warp_part;  // [2][nt][wps]
@@ -139,7 +159,8 @@ struct SweepCfg {
 //   site's links and G staged in shared memory by cp.async during the update:
 //     7: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
 // Every configuration forms K(x) in the same order and groups the fused
-// estimate by the same 8 sites, so results do not depend on the choice.
+// estimate by the same 8 sites; results differ only where the compiler fuses
+// multiply-adds differently in two kernels (FP32 rounding).
 constexpr int LGT_NCFG = 8;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
@@ -167,9 +188,12 @@ sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg);   // FP64, FP32-p
 // One half-sweep of parity p on a field of format fmt with launch
 // configuration cfg.  G (nullable) is multiplied by g at every updated site.
 // use_mask: skip inactive slices.
+// loop / reunit_every: a device loop's sweep (SweepArgs.loop; sweep is then the
+// offset within the chunk).
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
-                              cudaStream_t st, const void *aux = nullptr);
+                              cudaStream_t st, const void *aux = nullptr, const LoopState *loop = nullptr,
+                              int reunit_every = 0);
 
 // Fused estimate of F and theta from the last two half-sweeps (each sweep
 // kernel leaves per-warp sums of Re tr K and tr Delta^2 computed from the K it
@@ -209,6 +233,10 @@ cudaError_t launch_fill_unit(int fmt, const Geom &g, void *soa, cudaStream_t st)
 
 // In-place conversion of an FP64 field to FP32-pair storage (to_pair = 1)
 // or back (to_pair = 0).
+// Device loop: one thread advances the LoopState after a chunk of k sweeps and
+// sets the while node's condition (another chunk or not).
+cudaError_t launch_loop_decide(LoopState *L, const double *fused_totals, int gauge, int k, int vs_half,
+                               cudaGraphConditionalHandle h, cudaStream_t st);
 // Anchored polish: G = 1 + D (pairs) applied in FP64 (as launch_apply_G).
 cudaError_t launch_apply_D(const Geom &g, const void *D, const void *u64_in, void *u64_out, double *aos_out,
                            int skip_temporal, cudaStream_t st);

@@ -74,6 +74,7 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->links = links;
   a->G = G;
   a->aux = nullptr;
+  a->loop = nullptr;
   a->active = use_mask ? w.active : nullptr;
   a->warp_part = w.warp_part;
   a->wps = w.wps;
@@ -89,7 +90,7 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
 
 cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
-                              cudaStream_t st, const void *aux) {
+                              cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every) {
   sweep_fn fn = (fmt == FMT_F32_18 || fmt == FMT_F32_12) ? pick_sweep_f32(fmt, c.gauge, c.algo, cfg)
                                                           : pick_sweep_hi(fmt, c.gauge, c.algo, cfg);
   const int block = lgt_cfg_threads(cfg);
@@ -97,6 +98,8 @@ cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, cons
   SweepArgs a;
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   a.aux = aux;
+  a.loop = loop;
+  a.reunit_every = reunit_every;
   if (lgt_cfg_pipe(cfg)) {  // persistent: lgt_cfg_minblocks blocks per SM over the (slice, tile) list
     const int smem = LGT_PIPE_SMEM_PER_THREAD * block;
     static int sms_of[64];  // per device ordinal, looked up once
@@ -474,6 +477,41 @@ cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, in
   FusedArgs a;
   fill_fused_args(&a, g, w, gauge, sweep_sites, coulomb_target);
   k_fused_finish<<<g.nt, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ device loop decision
+// After a chunk of k sweeps and its fused estimate: advance the loop's counters
+// and decide, with the host driver's rules, whether another chunk follows.
+__global__ void k_loop_decide(LoopState *L, const double *tot, int gauge, int k, int vs_half,
+                              cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double theta = gauge == GAUGE_COULOMB ? tot[TOT_THETA_COULOMB_MAX] : tot[TOT_THETA_LANDAU];
+  L->site_updates += 2LL * k * (long long)vs_half * L->active;
+  L->active = (int)tot[TOT_ACTIVE_SLICES];
+  L->sweep += (unsigned long long)k;
+  L->count += k;
+  L->remaining -= k;
+  L->iters += 1;
+  L->theta = theta;
+  bool go = theta >= L->target;
+  if (L->bulk) {
+    if (theta < L->best) {
+      L->best = theta;
+      L->stall = 0;
+    } else {
+      L->stall += 1;
+    }
+    go = go && L->stall < 3;
+  }
+  // only whole chunks run on the device; the host takes a shorter last chunk
+  go = go && L->remaining >= k && L->iters < L->max_iters;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t launch_loop_decide(LoopState *L, const double *fused_totals, int gauge, int k, int vs_half,
+                               cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_loop_decide<<<1, 32, 0, st>>>(L, fused_totals, gauge, k, vs_half, h);
   return cudaGetLastError();
 }
 

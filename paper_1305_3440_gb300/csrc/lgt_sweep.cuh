@@ -61,6 +61,18 @@ __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
   return philox4x32_10(ctr, key);
 }
 
+// A device loop's sweep kernels take the sweep number (SR counter) and the
+// reunitarisation flag from the loop state (see LoopState).
+__device__ __forceinline__ SweepArgs resolve_loop(const SweepArgs &in) {
+  SweepArgs a = in;
+  if (a.loop) {
+    const unsigned long long off = a.sweep;
+    a.sweep = a.loop->sweep + off;
+    a.reunit = a.reunit_every > 0 && ((a.loop->count + (long long)off + 1) % a.reunit_every) == 0;
+  }
+  return a;
+}
+
 // The FP32 site update once the site's links are in registers (raw storage:
 // 12-real links with row 2 zero): K(x), the fused estimate terms, the local
 // update, the stores of the 8 links (and, for Coulomb gauge, the temporal
@@ -464,7 +476,8 @@ __device__ __forceinline__ void sweep_body_pair(const SweepArgs &a, int p, int t
 
 // Anchored polishing sweep (lgt_anchor.cuh): a.links = FP32-12 copy of the
 // anchor field U', a.G = D = G - 1 (pairs), a.aux = K0 (pairs).  One thread per
-// site; only D(x) is written.
+// site; only D(x) is written.  K(x) in pair precision; rotations, delta = g - 1
+// and delta D in FP32; D accumulated as a pair.
 template <int GAUGE, int ALGO>
 __device__ __forceinline__ void sweep_body_anchor(const SweepArgs &a, int p, int t, int bx, int nbx) {
   typedef LinkIO<FMT_F32_12> IO;
@@ -495,15 +508,12 @@ __device__ __forceinline__ void sweep_body_anchor(const SweepArgs &a, int p, int
     K0IO::load(a.aux, a.g.vh, p, i, K);
 #pragma unroll
     for (int e = 0; e < 18; e++) K[e] = pair_add(K[e], f2{C[e], 0.0f});
-    f2 D[18];
-    DIO::load_pair(a.G, a.g.vh, p, i, D);
+    float dh[18];  // D(x), high parts, row 2 rebuilt
+    DIO::load_hi(a.G, a.g.vh, p, i, dh);
     {
-      float dh[18], mh[18], dm[18];
+      float mh[18], dm[18];
 #pragma unroll
-      for (int e = 0; e < 18; e++) {
-        dh[e] = D[e].hi;
-        mh[e] = K[e].hi;
-      }
+      for (int e = 0; e < 18; e++) mh[e] = K[e].hi;
       mat_mul(dh, mh, dm);
 #pragma unroll
       for (int e = 0; e < 18; e++) K[e] = pair_add(K[e], f2{dm[e], 0.0f});
@@ -511,11 +521,13 @@ __device__ __forceinline__ void sweep_body_anchor(const SweepArgs &a, int p, int
     pair_violation(K, acc[0], acc[1]);
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
-    Rot rot[3];
-    pair_local_update<ALGO>(K, rot, (float)a.omega, a.sr_thr, draws);
-    f2 d[18];
-    pair_delta(rot, d);
-    d_update(D, d);
+    RotF rf[3];
+    anchor_local_update<ALGO>(K, rf, (float)a.omega, a.sr_thr, draws);
+    float d[18];
+    float_delta(rf, d);
+    f2 D[18];
+    DIO::load_pair_rows(a.G, a.g.vh, p, i, D);
+    d_update_lite(D, dh, d);
     DIO::store_pair(a.G, a.g.vh, p, i, D);
   }
   fused_store<float, 1>(a, p, t, bx, acc);

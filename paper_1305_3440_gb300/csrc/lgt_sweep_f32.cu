@@ -6,7 +6,8 @@
 namespace lgt {
 
 template <int FMT, int GAUGE, int ALGO, int CFG>
-__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs a, int p) {
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs in, int p) {
+  const SweepArgs a = resolve_loop(in);
   if constexpr (lgt_cfg_quad(CFG)) {
     sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
   } else if constexpr (lgt_cfg_pipe(CFG)) {

@@ -6,17 +6,20 @@
 namespace lgt {
 
 template <int GAUGE, int ALGO, int CFG>
-__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs a, int p) {
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs in, int p) {
+  const SweepArgs a = resolve_loop(in);
   sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <int GAUGE, int ALGO, int CFG>
-__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_pair(SweepArgs a, int p) {
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_pair(SweepArgs in, int p) {
+  const SweepArgs a = resolve_loop(in);
   sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <int GAUGE, int ALGO, int CFG>
-__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_anchor(SweepArgs a, int p) {
+__global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_anchor(SweepArgs in, int p) {
+  const SweepArgs a = resolve_loop(in);
   sweep_body_anchor<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 

@@ -54,13 +54,15 @@ class lgt_stats(ctypes.Structure):
     _fields_ = [("sweep_ms", ctypes.c_double * 2), ("sweep_launches", ctypes.c_int64 * 2),
                 ("site_updates", ctypes.c_int64 * 2), ("launches", ctypes.c_int64),
                 ("measure_ms", ctypes.c_double), ("measure_launches", ctypes.c_int64),
-                ("launch_config", ctypes.c_int32 * 2)]
+                ("launch_config", ctypes.c_int32 * 2), ("loop_launches", ctypes.c_int64),
+                ("loop_chunks", ctypes.c_int64)]
 
     def as_dict(self):
         return dict(sweep_ms=list(self.sweep_ms), sweep_launches=list(self.sweep_launches),
                     site_updates=list(self.site_updates), launches=self.launches,
                     measure_ms=self.measure_ms, measure_launches=self.measure_launches,
-                    launch_config=list(self.launch_config))
+                    launch_config=list(self.launch_config), loop_launches=self.loop_launches,
+                    loop_chunks=self.loop_chunks)
 
 
 class LgtError(RuntimeError):
