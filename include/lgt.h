@@ -122,7 +122,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..8: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..10: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
 } lgt_params;
@@ -147,8 +147,11 @@ typedef struct {
  *   one thread per site, pipelined (FP32-12 bulk sweeps only):
  *                         7: 128 threads, <= 255 registers, persistent blocks
  *                            (2 per SM) that stage the next site's links and G
- *                            in shared memory (cp.async) during the update.
- * A configuration that a phase's kernel lacks (4-7 after promotion; 7 on
+ *                            in shared memory (cp.async) during the update;
+ *   one thread per site, lean (FP32 bulk sweeps only): K(x) streamed, links
+ *   loaded again for the write-back:
+ *                         8: 128 threads, <= 128 registers; 9: 128, <= 96.
+ * A configuration that a phase's kernel lacks (4-9 after promotion; 7 on
  * FP32-18 links) falls back to configuration 0 for that phase.  Every
  * configuration forms K(x) and the fused estimate in the same order; results
  * differ only where the compiler fuses multiply-adds differently in the two

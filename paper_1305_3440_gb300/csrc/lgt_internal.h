@@ -158,21 +158,25 @@ struct SweepCfg {
 //   one thread per site, pipelined (FP32-12 only): persistent blocks, the next
 //   site's links and G staged in shared memory by cp.async during the update:
 //     7: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
+//   one thread per site, lean (FP32 formats): K(x) streamed, links loaded again
+//   for the write-back:
+//     8: 128 threads, <= 128 registers     9: 128 threads, <= 96 registers
 // Every configuration forms K(x) in the same order and groups the fused
 // estimate by the same 8 sites; results differ only where the compiler fuses
 // multiply-adds differently in two kernels (FP32 rounding).
-constexpr int LGT_NCFG = 8;
+constexpr int LGT_NCFG = 10;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
-  return c == 1 ? 3 : (c == 3 ? 8 : (c == 4 ? 4 : (c == 5 ? 2 : (c == 6 ? 6 : (c == 7 ? 2 : 1)))));
+  return c == 1 ? 3 : (c == 3 ? 8 : (c == 4 ? 4 : (c == 5 ? 2 : (c == 6 ? 6 : (c == 7 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : 1)))))));
 }
 __host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4 && c <= 6; }
 __host__ __device__ constexpr bool lgt_cfg_pipe(int c) { return c == 7; }
+__host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9; }
 // sites covered by one block (per tile for the pipelined configuration)
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
 // whether a storage format has kernels for a configuration
 __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
-  return c >= 0 && c < LGT_NCFG && (!lgt_cfg_quad(c) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
+  return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
          (!lgt_cfg_pipe(c) || fmt == FMT_F32_12);
 }
 // dynamic shared memory of the pipelined configuration: 2 buffers x 27 chunks x 16 B per thread

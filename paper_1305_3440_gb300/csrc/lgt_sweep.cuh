@@ -184,6 +184,75 @@ __device__ __forceinline__ void sweep_body_f32(const SweepArgs &a, int p, int t,
   fused_store<float, 1>(a, p, t, bx, acc);
 }
 
+// FP32 link formats, lean: K(x) streamed (each link loaded, widened to 3 rows,
+// added and dropped), the links loaded again for the write-back (L2 still
+// holds them), so a thread keeps about a third of the registers of the
+// all-in-registers body and more warps fit on an SM.
+template <int FMT, int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_f32_lean(const SweepArgs &a, int p, int t, int bx) {
+  typedef LinkIO<FMT> IO;
+  if (a.active && !a.active[t]) return;
+  const int j = bx * blockDim.x + threadIdx.x;
+  float acc[2] = {0.0f, 0.0f};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    // K(x) = (k_0 + k_1) + (k_2 + k_3), as the other layouts
+    float W[18], k2[18];
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+      float ka[18], kb[18];
+#pragma unroll
+      for (int d = 0; d < 2; d++) {
+        const int mu = 2 * h + d;
+        float *k = d ? kb : ka;
+        if (mu < MU0) {
+          mat_zero(k);
+        } else {
+          float uf[18], ub[18];
+          IO::load(a.links, a.g.vh, p, mu, i, uf);
+          IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), ub);
+          k_term(k, uf, ub);
+        }
+      }
+      float *dst = h ? k2 : W;
+#pragma unroll
+      for (int e = 0; e < 18; e++) dst[e] = ka[e] + kb[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 18; e++) W[e] = W[e] + k2[e];
+    violation_of_K(W, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    float gm[18];
+    local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+    const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
+#pragma unroll 1
+    for (int mu = mu_lo; mu < 4; mu++) {
+      const int nb = cb_shift(a.g, c, mu, -1);
+      float u[18], r[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      mat_mul(gm, u, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, p, mu, i, r);
+      IO::load_raw(a.links, a.g.vh, q, mu, nb, u);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
+      mat_mul_dag(u, gm, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, q, mu, nb, r);
+    }
+    if (a.G) {
+      float gx[18], r[18];
+      GIO::load(a.G, a.g.vh, p, i, gx);
+      mat_mul(gm, gx, r);
+      if (a.reunit) reunitarise(r);
+      GIO::store(a.G, a.g.vh, p, i, r);
+    }
+  }
+  fused_store<float, 1>(a, p, t, bx, acc);
+}
+
 // 16-byte asynchronous copy global -> shared (cp.async, L1 bypassed) and its
 // group bookkeeping
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {

@@ -13,6 +13,8 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
   } else if constexpr (lgt_cfg_pipe(CFG)) {
     if constexpr (FMT == FMT_F32_12)
       sweep_body_f32_pipe<GAUGE, ALGO>(a, p, (a.g.vs_half + (int)blockDim.x - 1) / (int)blockDim.x);
+  } else if constexpr (lgt_cfg_lean(CFG)) {
+    sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
   } else {
     sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
   }
@@ -45,6 +47,8 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 5: return pick_cfg<5>(fmt, gauge, algo);
     case 6: return pick_cfg<6>(fmt, gauge, algo);
     case 7: return pick_cfg<7>(fmt, gauge, algo);
+    case 8: return pick_cfg<8>(fmt, gauge, algo);
+    case 9: return pick_cfg<9>(fmt, gauge, algo);
   }
   return nullptr;
 }

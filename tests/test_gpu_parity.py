@@ -550,7 +550,7 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
 @pytest.mark.parametrize("algo", list(ALGOS))
 def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     """Every launch configuration (one or four threads per site, every block size,
-    pipelined through shared memory) forms K(x) in the same order and groups the
+    pipelined through shared memory, lean) forms K(x) in the same order and groups the
     fused estimate by the same 8 sites; what remains is where the compiler fuses
     multiply-adds in each kernel (FP32 rounding, which a nearly degenerate SU(2)
     projection can amplify along a trajectory).  So the test compares what the
@@ -560,7 +560,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
-    ncfg = 8
+    ncfg = 10
     ref = None
     for k in range(ncfg):
         p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, **kw)
