@@ -187,6 +187,7 @@ struct lgt_ctx {
   void *k0;       // anchored polish: K0 (pairs)
   int anchored;   // anchored polish: K0, the FP32-12 copy in u32 and D refer to the field in u64
   int d_dirty;    // anchored polish: D != 0 (sweeps since the field in u64 was last formed)
+  int64_t anchor_sweeps;  // anchored polish: sweeps since the last anchor set-up
   void *ws_base;  // workspace allocation
   Workspace ws;
   double *host;   // pinned readback buffer
@@ -480,6 +481,14 @@ static lgt_status anchor_setup(lgt_ctx *c) {
   LGT_CUDA(launch_anchor_setup(c->g, c->u64, c->u32, c->k0, c->G, c->cfg.gauge, c->stream));
   c->stats.launches++;
   c->anchored = 1;
+  c->anchor_sweeps = 0;
+  return LGT_OK;
+}
+
+// anchored polish: after LGT_REANCHOR_SWEEPS sweeps on one anchor, form the
+// field (the next sweep sets up a new anchor with D = 0)
+static lgt_status anchor_refresh(lgt_ctx *c) {
+  if (c->phase == 3 && c->anchored && c->anchor_sweeps >= LGT_REANCHOR_SWEEPS) return anchor_materialise(c);
   return LGT_OK;
 }
 
@@ -511,6 +520,7 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
     }
   }
   batch_end(c, bt);
+  if (anch) c->anchor_sweeps += n_half / 2;
   c->stats.sweep_launches[kind] += n_half;
   c->stats.launches += n_half;
   const int64_t slices = use_mask ? c->active_slices : c->g.nt;
@@ -737,6 +747,11 @@ static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64
   L.active = c->active_slices;
   L.iters = 0;
   L.max_iters = (int)(*remaining / k);
+  if (c->phase == 3) {  // end the launch where the anchor is due for renewal
+    const int64_t left = LGT_REANCHOR_SWEEPS - c->anchor_sweeps;
+    const int64_t cap = left > 0 ? (left + k - 1) / k : 1;
+    if (cap < L.max_iters) L.max_iters = (int)cap;
+  }
   LGT_CUDA(cudaMemcpyAsync(c->d_loop, c->h_loop, sizeof(LoopState), cudaMemcpyHostToDevice, c->stream));
   const int bt = batch_begin(c, kind);
   LGT_CUDA(cudaGraphLaunch(c->loop_exec[slot], c->stream));
@@ -747,6 +762,7 @@ static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64
   if (st != LGT_OK) return st;
   const int64_t n = (int64_t)L.iters * k;
   c->sweep_index += (uint64_t)n;
+  if (c->phase == 3) c->anchor_sweeps += n;
   if (kind == 0) c->sweeps_bulk += n;
   else c->sweeps_fp64 += n;
   *remaining = L.remaining;
@@ -793,7 +809,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     if (st != LGT_OK) return st;
     double best = m.theta;
     int stall = 0;
-    while (m.theta >= target && remaining > 0 && stall < 3) {
+    while (m.theta >= target && remaining > 0 && stall < LGT_STALL_CHECKS) {
       if (loop_ready(c, 0, remaining)) {  // whole chunks, decided on the device
         st = run_loop(c, 0, &best, &stall, &remaining, &m);
         if (st != LGT_OK) return st;
@@ -809,7 +825,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
         best = m.theta;
         stall = 0;
       } else {
-        stall++;
+        stall = m.theta < LGT_STALL_CEILING ? stall + 1 : 0;
       }
     }
     st = promote(c);
@@ -831,6 +847,8 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     if (st != LGT_OK) return st;
   }
   while (m.theta >= tol && remaining > 0) {
+    st = anchor_refresh(c);
+    if (st != LGT_OK) return st;
     if (loop_ready(c, 1, remaining)) {  // whole chunks, decided on the device
       st = run_loop(c, 1, nullptr, nullptr, &remaining, &m);
       if (st != LGT_OK) return st;

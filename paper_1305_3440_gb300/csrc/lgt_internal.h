@@ -48,6 +48,20 @@ size_t workspace_bytes(const Geom &g, int min_block);
 void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w);
 
 // Arguments of one lattice's half-sweep (also one row of a batched launch).
+// Ladder rules shared by lgt_fix, its device loop and the server.
+// The bulk phase also ends when the estimate stops improving for
+// LGT_STALL_CHECKS checks in a row -- the FP32 rounding floor -- but only
+// counts such checks below LGT_STALL_CEILING: far above any FP32 floor the
+// overrelaxed iteration's estimate may wander for a few checks without a
+// floor being near (seen on Coulomb lattices, where theta is a max over
+// slices), and promoting there would leave the polish a large transformation.
+constexpr int LGT_STALL_CHECKS = 3;
+constexpr double LGT_STALL_CEILING = 1e-8;
+// The anchored polish forms its field and re-anchors after this many sweeps
+// without a measurement: the FP32 correction C ~ |D| 2^-24 must stay small
+// against the violations being removed, so D is not left to grow.
+constexpr int LGT_REANCHOR_SWEEPS = 500;
+
 // State of a device-side sweep loop (lgt_fix's chunks of check_every sweeps run
 // as a CUDA graph with a conditional while node): the decide kernel updates it
 // after each chunk's fused estimate, the sweep kernels read the sweep counters.

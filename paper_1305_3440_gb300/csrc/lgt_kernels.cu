@@ -500,9 +500,9 @@ __global__ void k_loop_decide(LoopState *L, const double *tot, int gauge, int k,
       L->best = theta;
       L->stall = 0;
     } else {
-      L->stall += 1;
+      L->stall = theta < LGT_STALL_CEILING ? L->stall + 1 : 0;
     }
-    go = go && L->stall < 3;
+    go = go && L->stall < LGT_STALL_CHECKS;
   }
   // only whole chunks run on the device; the host takes a shorter last chunk
   go = go && L->remaining >= k && L->iters < L->max_iters;

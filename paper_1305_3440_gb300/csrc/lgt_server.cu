@@ -73,6 +73,7 @@ struct Job {
   Workspace ws;
   int phase = 0, bulk_fmt = FMT_F64;  // phase as lgt_get_progress (3: anchored polish)
   bool anchored = false, d_dirty = false;
+  int64_t anchor_sweeps = 0;  // anchored polish: sweeps since the last anchor set-up
   SweepCfg cfg;
   int64_t sweeps_bulk = 0, sweeps_fp64 = 0, remaining = 0;
   uint64_t sweep_index = 0;
@@ -229,6 +230,7 @@ cudaError_t anchor_materialise(lgt_server *s, Job *j) {
 cudaError_t anchor_setup(lgt_server *s, Job *j) {
   if (j->phase != 3 || j->anchored) return cudaSuccess;
   j->anchored = true;
+  j->anchor_sweeps = 0;
   return launch_anchor_setup(j->g, j->u64, j->u32, j->k0, j->G, j->cfg.gauge, s->stream);
 }
 
@@ -360,7 +362,12 @@ cudaError_t tick(lgt_server *s) {
   // sweeps need a current anchor (rare: at promotion and certification; issued
   // before, and outside, the tick's captured sequence)
   for (Job *j : live) {
-    cudaError_t e = j->measure_only ? anchor_materialise(s, j) : anchor_setup(s, j);
+    cudaError_t e = cudaSuccess;
+    // as lgt_fix: a measurement forms the field; so does an anchor that has
+    // served LGT_REANCHOR_SWEEPS sweeps (the next sweeps set up a new one)
+    if (j->measure_only || (j->phase == 3 && j->anchored && j->anchor_sweeps >= LGT_REANCHOR_SWEEPS))
+      e = anchor_materialise(s, j);
+    if (e == cudaSuccess && !j->measure_only) e = anchor_setup(s, j);
     if (e != cudaSuccess) return e;
     if (!j->measure_only && j->phase == 3) j->d_dirty = true;
   }
@@ -598,6 +605,7 @@ void worker_main(lgt_server *s) {
         if (!exact) {
           if (j->phase == 0) j->sweeps_bulk += j->nthis;
           else j->sweeps_fp64 += j->nthis;
+          if (j->phase == 3) j->anchor_sweeps += j->nthis;
           j->remaining -= j->nthis;
           j->sweep_index += (uint64_t)j->nthis;
         }
@@ -612,9 +620,9 @@ void worker_main(lgt_server *s) {
             j->best = theta;
             j->stall = 0;
           } else {
-            j->stall++;
+            j->stall = theta < LGT_STALL_CEILING ? j->stall + 1 : 0;
           }
-          if (theta < j->prm.theta_switch || j->remaining <= 0 || j->stall >= 3) {
+          if (theta < j->prm.theta_switch || j->remaining <= 0 || j->stall >= LGT_STALL_CHECKS) {
             if ((e = promote_job(s, j)) != cudaSuccess) break;
           }
         } else if (theta < j->prm.theta_tol) {

@@ -629,3 +629,46 @@ def test_device_loop_is_bit_identical(lgt, bulk, gauge, algo):
     assert t0["loop_launches"] == 0 and t1["loop_launches"] > 0 and t1["loop_chunks"] >= t1["loop_launches"]
     if s1 == lgt.LGT_OK:
         assert r1["theta"] < 1e-13
+
+
+def test_coulomb_bulk_runs_to_the_fp32_floor(lgt):
+    """Coulomb 32^3 x 64 (eps 0.5176, seed 1003; a job of the served stream): the
+    estimate (a max over 64 slices) can stall for a few checks far above any FP32
+    floor; the bulk phase must not stop there (that left the polish a large
+    transformation and a floor above 1e-14)."""
+    dims = (64, 32, 32, 32)
+    U = synth.field(dims, 0.5175765603053992, 1003)
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_COULOMB, bulk=lgt.LGT_FP32_12, theta_tol=1e-14,
+                               max_sweeps=20000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and res.theta < 1e-14, res.as_dict()
+    assert res.sweeps_bulk > 1000, res.as_dict()
+
+
+def test_anchored_polish_from_an_early_promotion(lgt):
+    """Promoted far from convergence (theta ~ 1e-3), the anchored polish carries a
+    large transformation; renewing the anchor every 500 sweeps keeps its FP32
+    correction small, so it still reaches 1e-14 and the result is a gauge
+    transform of the input."""
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 0.5, 17)
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, theta_tol=1e-14, max_sweeps=20000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        lgt.lgt_sweep(ctx, 20)
+        lgt.lgt_promote(ctx)
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and res.sweeps_fp64 > 500, res.as_dict()
+    m = O.measure(V)
+    assert m["theta"] < 1e-14
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+    ref = U.copy()
+    r = O.fix(ref, omega=1.7, tol=1e-14, max_sweeps=20000)
+    assert abs(r["F"] - res.F) < 1e-10
