@@ -47,7 +47,7 @@ struct Coords {
 };
 
 // site j (0 <= j < vs_half) of parity p in timeslice t
-__device__ __forceinline__ Coords coords_in_slice(const Geom &g, int p, int t, int j) {
+__host__ __device__ __forceinline__ Coords coords_in_slice(const Geom &g, int p, int t, int j) {
   Coords c;
   const int row = j / g.half1;
   c.x2 = row % g.n2;
@@ -58,12 +58,12 @@ __device__ __forceinline__ Coords coords_in_slice(const Geom &g, int p, int t, i
 }
 
 // within-parity index of a site
-__device__ __forceinline__ int cb_index(const Geom &g, int x1, int x2, int x3, int t) {
+__host__ __device__ __forceinline__ int cb_index(const Geom &g, int x1, int x2, int x3, int t) {
   return ((t * g.n3 + x3) * g.n2 + x2) * g.half1 + (x1 >> 1);
 }
 
 // within-parity index of x + dir * mu-hat (dir = +-1)
-__device__ __forceinline__ int cb_shift(const Geom &g, const Coords &c, int mu, int dir) {
+__host__ __device__ __forceinline__ int cb_shift(const Geom &g, const Coords &c, int mu, int dir) {
   int x1 = c.x1, x2 = c.x2, x3 = c.x3, t = c.t;
   if (mu == 0) {
     t += dir;

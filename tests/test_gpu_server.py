@@ -197,3 +197,50 @@ def test_server_errors_and_cancel(lgt):
         assert res[j_long][0] == lgt.LGT_ECANCELLED
     finally:
         lgt.lgt_server_destroy(srv)
+
+
+def test_server_from_several_threads(lgt):
+    """Submit, poll and cancel from four host threads at once (the server is
+    thread-safe; ctypes releases the GIL around each call): every job ends
+    converged or, the one cancelled, LGT_ECANCELLED, and the server is empty."""
+    import threading
+    srv = lgt.lgt_server_create(8 << 30, 0)
+    fields = {k: synth.field((4, 4, 4, 8), 0.4, 300 + k) for k in range(12)}
+    results, errors = {}, []
+
+    def worker(w):
+        try:
+            mine = []
+            for k in range(3 * w, 3 * w + 3):
+                p = lgt.lgt_params_default(dims=(4, 4, 4, 8), bulk=lgt.LGT_FP32_12, theta_tol=1e-13, max_sweeps=5000)
+                mine.append((k, lgt.lgt_submit(srv, p, fields[k])))
+            if w == 1:
+                lgt.lgt_cancel(srv, mine[0][1])
+            t0 = time.time()
+            pending = dict(mine)
+            while pending and time.time() - t0 < 120:
+                for k, jid in list(pending.items()):
+                    st, res = lgt.lgt_poll(srv, jid)
+                    if st != lgt.LGT_EAGAIN:
+                        results[k] = (st, res.theta)
+                        del pending[k]
+                time.sleep(0.002)
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+    try:
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(180)
+        done, live, used = lgt.lgt_server_stats(srv)
+    finally:
+        lgt.lgt_server_destroy(srv)
+    assert not errors, errors
+    assert len(results) == 12 and done == 12 and live == 0 and used == 0
+    for k, (st, theta) in results.items():
+        if k == 3:
+            assert st in (lgt.LGT_ECANCELLED, lgt.LGT_OK)
+        else:
+            assert st == lgt.LGT_OK and theta < 1e-13, (k, st, theta)
