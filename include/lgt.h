@@ -125,6 +125,10 @@ typedef struct {
   int32_t launch_config;      /* 0: as block_size says; k = 1..10: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
+  int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
+  int32_t reserved;           /* must be 0 */
+  double sa_beta0, sa_beta1;  /* inverse temperature of the first and the last annealing sweep,
+                                 0 < sa_beta0 <= sa_beta1 (geometric in between) */
 } lgt_params;
 
 typedef struct {
@@ -137,6 +141,15 @@ typedef struct {
   int32_t status;       /* lgt_status of the job */
   int32_t reserved;
 } lgt_result;
+
+/* Simulated annealing (Sec. 1 names it as a preconditioner that lowers the
+ * chance of ending in a poor Gribov copy; its details are in a reference this
+ * text lacks).  Read as sa_sweeps sweeps before the relaxation, each subgroup
+ * element drawn from exp(beta Re tr[r M]) with respect to Haar measure (an
+ * SU(2) heat bath, Kennedy-Pendleton draws from Philox streams keyed by seed),
+ * beta rising geometrically from sa_beta0 to sa_beta1.  They run in the bulk
+ * precision (launch configuration 0) and count as bulk sweeps; lgt_fix runs
+ * them once per loaded field.  Not served (lgt_submit: LGT_EINVAL). */
 
 /* Launch configurations of the sweep kernels (lgt_params.launch_config - 1):
  *   one thread per site:  0: 128 threads, <= 255 registers; 1: 128, <= 170;
@@ -159,7 +172,8 @@ typedef struct {
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
- * transform_temporal 1, block_size 0, launch_config 0, polish LGT_POLISH_ANCHOR, omega_polish 1.3
+ * transform_temporal 1, block_size 0, launch_config 0, polish LGT_POLISH_ANCHOR, omega_polish 1.3,
+ * sa_sweeps 0, sa_beta0 1, sa_beta1 100
  * (after promotion the residual is short-wavelength noise, which a smaller
  * omega removes fastest).  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);

@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 LANDAU, COULOMB = 0, 1
-OR, SR = 0, 1
+OR, SR, SA = 0, 1, 2
 
 _dp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -72,6 +72,14 @@ def _load():
                                   ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   _dp, _dp]
             L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_sa_sweeps.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+            L.orc_kp_draws.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _dp]
+            L.orc_su2_heatbath.argtypes = [_dp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_int, _dp]
+            L.orc_su2_heatbath.restype = None
+            L.orc_sa_beta.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+            L.orc_sa_beta.restype = ctypes.c_double
             L.orc_set_threads.restype = None
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -205,3 +213,36 @@ def fix(links, gauge=LANDAU, algo=OR, omega=1.7, p=0.0, seed=0, tol=1e-14, max_s
                                 check_every, transform_temporal, ctypes.byref(sw), ctypes.addressof(F),
                                 ctypes.addressof(th)), "orc_fix")
     return dict(converged=(rc == 0), sweeps=sw.value, F=F.value, theta=th.value)
+
+
+def sa_sweeps(links, n, beta0, beta1, gauge=LANDAU, seed=0, sweep0=0, transform_temporal=1):
+    """n simulated-annealing (SU(2) heat-bath) sweeps in place, beta rising
+    geometrically from beta0 to beta1 (see the C source for the reading)."""
+    L = _load()
+    d = _dims_of(links)
+    _check(L.orc_sa_sweeps(d, links.ctypes.data, gauge, float(beta0), float(beta1), int(n), seed, sweep0,
+                           transform_temporal), "orc_sa_sweeps")
+    return links
+
+
+def kp_draws(alpha, n, seed=0):
+    """(draws, failures): n Kennedy-Pendleton draws of x with density
+    ~ sqrt(1 - x^2) exp(alpha x) on [-1, 1] (NaN where every attempt failed)."""
+    L = _load()
+    out = np.empty(int(n), np.float64)
+    fails = L.orc_kp_draws(float(alpha), int(n), seed, out.ctypes.data)
+    return out, fails
+
+
+def su2_heatbath(q, beta, seed=0, sweep=0, site=0, subgroup=0):
+    """The heat-bath SU(2) element (quaternion) for a block projection q."""
+    L = _load()
+    qq = np.ascontiguousarray(q, np.float64)
+    r = np.empty(4, np.float64)
+    L.orc_su2_heatbath(qq.ctypes.data, float(beta), seed, sweep, site, subgroup, r.ctypes.data)
+    return r
+
+
+def sa_beta(beta0, beta1, n, i):
+    """beta of annealing sweep i of n (geometric from beta0 to beta1)."""
+    return _load().orc_sa_beta(float(beta0), float(beta1), int(n), int(i))

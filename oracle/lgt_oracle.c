@@ -61,7 +61,7 @@
 #define NC 3
 
 enum { ORC_LANDAU = 0, ORC_COULOMB = 1 };
-enum { ORC_OR = 0, ORC_SR = 1 };
+enum { ORC_OR = 0, ORC_SR = 1, ORC_SA = 2 };
 
 /* ------------------------------------------------------------------ complex */
 typedef struct { double re, im; } cplx;
@@ -313,10 +313,102 @@ static su3 su2_embed(const double r[4], int i, int j) {
 
 static const int SUBGROUP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 
+/* ------------------------------------ simulated annealing: SU(2) heat bath */
+/* Simulated annealing (named by the paper as a preconditioner, Sec. 1; its
+ * details are in a reference this text lacks) is read as sweeps whose SU(2)
+ * subgroup elements are drawn from exp(beta Re tr[r M]) with respect to Haar
+ * measure, beta rising over the sweeps.  With the block projection q,
+ * Re tr[r M] = 2 |q| (r . p) for the maximum p = (q0, -q)/|q| (4-vector dot
+ * product), so r = a p (matrix product) with a0 = x drawn from the density
+ * proportional to sqrt(1 - x^2) exp(alpha x), alpha = 2 beta |q|, and the
+ * vector part of a uniform on the sphere of radius sqrt(1 - x^2).  x is drawn
+ * by the method of Kennedy and Pendleton (1985), at most SA_MAX_ATTEMPTS
+ * tries; if all are rejected the subgroup is left unchanged. */
+#define SA_TAG 0x53414842u /* "SAHB": heat-bath stream */
+#define SA_MAX_ATTEMPTS 64u
+#define SA_DIRECTION 0xFFFFFFu
+
+/* uniform in (0, 1) from a 32-bit word */
+static double unit_open(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* the four uniforms of (site, subgroup, attempt) in one sweep */
+static void sa_uniforms(uint64_t seed, uint64_t sweep, int64_t site, int s, uint32_t attempt, double u[4]) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const uint32_t ctr[4] = {(uint32_t)site, ((uint32_t)s << 24) | attempt, (uint32_t)sweep, SA_TAG};
+  uint32_t w[4];
+  philox4x32_10(ctr, key, w);
+  for (int k = 0; k < 4; k++) u[k] = unit_open(w[k]);
+}
+
+/* Kennedy-Pendleton draw of x in [-1, 1], density ~ sqrt(1 - x^2) exp(alpha x):
+ * delta = -(ln u0 + cos^2(2 pi u1) ln u2) / alpha has density ~ sqrt(delta)
+ * exp(-alpha delta); accepting with probability sqrt(1 - delta / 2) supplies
+ * the rest of sqrt(1 - x^2) = sqrt(2 delta) sqrt(1 - delta / 2), x = 1 - delta.
+ * Returns 0 on success, 1 when every attempt was rejected. */
+static int kp_draw(double alpha, uint64_t seed, uint64_t sweep, int64_t site, int s, double *x) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (uint32_t k = 0; k < SA_MAX_ATTEMPTS; k++) {
+    double u[4];
+    sa_uniforms(seed, sweep, site, s, k, u);
+    const double c = cos(two_pi * u[1]);
+    const double delta = -(log(u[0]) + c * c * log(u[2])) / alpha;
+    if (u[3] * u[3] <= 1.0 - 0.5 * delta) {
+      *x = 1.0 - delta;
+      return 0;
+    }
+  }
+  return 1;
+}
+
+/* quaternion of the matrix product A B (matrices in the su2_embed convention) */
+static void su2_mul(const double a[4], const double b[4], double r[4]) {
+  const cplx a00 = c_make(a[0], a[3]), a01 = c_make(a[2], a[1]), a10 = c_make(-a[2], a[1]), a11 = c_make(a[0], -a[3]);
+  const cplx b00 = c_make(b[0], b[3]), b01 = c_make(b[2], b[1]), b10 = c_make(-b[2], b[1]);
+  const cplx c00 = c_add(c_mul(a00, b00), c_mul(a01, b10));
+  const cplx c01 = c_add(c_mul(a00, b01), c_mul(a01, c_make(b[0], -b[3])));
+  (void)a10;
+  (void)a11;
+  r[0] = c00.re;
+  r[3] = c00.im;
+  r[2] = c01.re;
+  r[1] = c01.im;
+}
+
+/* heat-bath element for the block projection q at inverse temperature beta */
+static void su2_heatbath(const double q[4], double beta, uint64_t seed, uint64_t sweep, int64_t site, int s,
+                         double r[4]) {
+  const double norm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double x;
+  if (!(norm > 0.0) || !(beta > 0.0) || kp_draw(2.0 * beta * norm, seed, sweep, site, s, &x)) {
+    r[0] = 1.0; /* no update of this subgroup */
+    r[1] = r[2] = r[3] = 0.0;
+    return;
+  }
+  double p[4], u[4];
+  su2_maximum(q, p);
+  sa_uniforms(seed, sweep, site, s, SA_DIRECTION, u);
+  const double two_pi = 6.283185307179586476925286766559;
+  const double cth = 2.0 * u[0] - 1.0, sth = sqrt(1.0 - cth * cth), phi = two_pi * u[1];
+  const double rad = sqrt(x * x < 1.0 ? 1.0 - x * x : 0.0);
+  const double a[4] = {x, rad * sth * cos(phi), rad * sth * sin(phi), rad * cth};
+  su2_mul(a, p, r);
+}
+
+/* the simulated-annealing schedule: beta rises geometrically from beta0 (sweep
+ * 0) to beta1 (sweep n - 1) */
+static double sa_beta(double beta0, double beta1, int n, int i) {
+  if (n <= 1) return beta1;
+  return beta0 * pow(beta1 / beta0, (double)i / (double)(n - 1));
+}
+
 typedef struct {
-  int algo;          /* ORC_OR or ORC_SR */
+  int algo;          /* ORC_OR, ORC_SR or ORC_SA */
   double omega;      /* overrelaxation parameter */
   uint64_t sr_thr;   /* stochastic relaxation: accept iff draw < sr_thr */
+  double beta;       /* simulated annealing: inverse temperature */
+  uint64_t seed;     /* simulated annealing: stream of the site, sweep below */
+  uint64_t sweep;
+  int64_t site;
 } update_rule;
 
 /* Section 3: maximise f = Re tr[g K] by iterating over the three SU(2)
@@ -331,11 +423,15 @@ static su3 local_gauge_update(const su3 *K, const update_rule *rule, const uint3
     const int i = SUBGROUP[s][0], j = SUBGROUP[s][1];
     double q[4], r[4];
     su2_project(W.e[i][i], W.e[i][j], W.e[j][i], W.e[j][j], q);
-    su2_maximum(q, r);
-    if (rule->algo == ORC_OR) {
-      su2_overrelax(r, rule->omega);
-    } else if ((uint64_t)draws[s] < rule->sr_thr) {
-      su2_square(r);
+    if (rule->algo == ORC_SA) {
+      su2_heatbath(q, rule->beta, rule->seed, rule->sweep, rule->site, s, r);
+    } else {
+      su2_maximum(q, r);
+      if (rule->algo == ORC_OR) {
+        su2_overrelax(r, rule->omega);
+      } else if ((uint64_t)draws[s] < rule->sr_thr) {
+        su2_square(r);
+      }
     }
     su3 R = su2_embed(r, i, j);
     if (trace_W) trace_W[s] = W;
@@ -376,7 +472,11 @@ static void update_site(const lattice *l, double *links, int64_t site, const swe
   su3 K = gather_K(l, links, site, cfg->gauge);
   uint32_t u[3] = {0, 0, 0};
   if (cfg->rule.algo == ORC_SR) sr_draws(cfg->seed, sweep, site, u);
-  su3 g = local_gauge_update(&K, &cfg->rule, u, NULL, NULL);
+  update_rule rule = cfg->rule;
+  rule.seed = cfg->seed;
+  rule.sweep = sweep;
+  rule.site = site;
+  su3 g = local_gauge_update(&K, &rule, u, NULL, NULL);
   apply_gauge_update(l, links, site, &g, cfg->gauge, cfg->transform_temporal);
 }
 
@@ -557,6 +657,10 @@ static sweep_cfg make_cfg(int gauge, int algo, double omega, double p, uint64_t 
   c.rule.algo = algo;
   c.rule.omega = omega;
   c.rule.sr_thr = sr_threshold(p);
+  c.rule.beta = 0.0;
+  c.rule.seed = seed;
+  c.rule.sweep = 0;
+  c.rule.site = 0;
   c.seed = seed;
   c.transform_temporal = transform_temporal;
   return c;
@@ -644,6 +748,10 @@ void orc_local_update(const double *K, int algo, double omega, double p, const u
   rule.algo = algo;
   rule.omega = omega;
   rule.sr_thr = sr_threshold(p);
+  rule.beta = 0.0;
+  rule.seed = 0;
+  rule.sweep = 0;
+  rule.site = 0;
   uint32_t u[3] = {0, 0, 0};
   if (draws) { u[0] = draws[0]; u[1] = draws[1]; u[2] = draws[2]; }
   su3 g = local_gauge_update(&k, &rule, u, W, R);
@@ -679,6 +787,46 @@ void orc_sr_draws(uint64_t seed, uint64_t sweep, int64_t site, uint32_t *out) { 
  * first).  Coulomb: per-timeslice convergence, converged slices are no longer
  * updated; converged when every theta_t < tol.
  * Returns 0 converged, 1 not converged within max_sweeps, <0 on error. */
+/* Simulated annealing: n heat-bath sweeps (even then odd), sweep numbers
+ * sweep0 .. sweep0+n-1, beta from the geometric schedule sa_beta. */
+int orc_sa_sweeps(const int32_t dims[4], double *links, int gauge, double beta0, double beta1, int n, uint64_t seed,
+                  uint64_t sweep0, int transform_temporal) {
+  if (check_dims(dims) || n < 0 || !(beta0 > 0.0) || !(beta1 > 0.0)) return -1;
+  const lattice l = make_lattice(dims);
+  for (int i = 0; i < n; i++) {
+    sweep_cfg cfg = make_cfg(gauge, ORC_SA, 1.0, 0.0, seed, transform_temporal);
+    cfg.rule.beta = sa_beta(beta0, beta1, n, i);
+    half_sweep(&l, links, 0, &cfg, sweep0 + (uint64_t)i, NULL, NULL);
+    half_sweep(&l, links, 1, &cfg, sweep0 + (uint64_t)i, NULL, NULL);
+  }
+  return 0;
+}
+
+/* n Kennedy-Pendleton draws at alpha (stream: site = draw index, subgroup 0,
+ * sweep 0); returns how many failed (all attempts rejected; out = NaN). */
+int orc_kp_draws(double alpha, int64_t n, uint64_t seed, double *out) {
+  int fails = 0;
+  for (int64_t k = 0; k < n; k++) {
+    double x;
+    if (kp_draw(alpha, seed, 0, k, 0, &x)) {
+      out[k] = NAN;
+      fails++;
+    } else {
+      out[k] = x;
+    }
+  }
+  return fails;
+}
+
+/* The heat-bath SU(2) element for one block projection q (as the sweep
+ * would draw it for site, subgroup s, sweep). */
+void orc_su2_heatbath(const double *q, double beta, uint64_t seed, uint64_t sweep, int64_t site, int s,
+                      double *r_out) {
+  su2_heatbath(q, beta, seed, sweep, site, s, r_out);
+}
+
+double orc_sa_beta(double beta0, double beta1, int n, int i) { return sa_beta(beta0, beta1, n, i); }
+
 int orc_fix(const int32_t dims[4], double *links, int gauge, int algo, double omega, double p, uint64_t seed,
             double tol, int max_sweeps, int check_every, int transform_temporal, int *sweeps_out, double *F_out,
             double *theta_out) {

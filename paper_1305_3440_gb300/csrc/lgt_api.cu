@@ -80,6 +80,10 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->block_size = 0;
   p->polish = LGT_POLISH_ANCHOR;
   p->launch_config = 0;
+  p->sa_sweeps = 0;
+  p->reserved = 0;
+  p->sa_beta0 = 1.0;
+  p->sa_beta1 = 100.0;
   p->omega_polish = 1.3;
   return LGT_OK;
 }
@@ -139,6 +143,15 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("block_size must be 0, 64, 128 or 256");
     return LGT_EINVAL;
   }
+  if (p->sa_sweeps < 0 || (p->sa_sweeps > 0 && !(p->sa_beta0 > 0.0 && p->sa_beta0 <= p->sa_beta1 &&
+                                                  p->sa_beta1 < 1e300))) {
+    lgt_set_error("sa_sweeps >= 0 and 0 < sa_beta0 <= sa_beta1 (finite) required");
+    return LGT_EINVAL;
+  }
+  if (p->reserved != 0) {
+    lgt_set_error("reserved must be 0");
+    return LGT_EINVAL;
+  }
   if (p->launch_config < 0 || p->launch_config > LGT_NCFG) {
     lgt_set_error("launch_config must be in [0, %d]", LGT_NCFG);
     return LGT_EINVAL;
@@ -188,6 +201,7 @@ struct lgt_ctx {
   int anchored;   // anchored polish: K0, the FP32-12 copy in u32 and D refer to the field in u64
   int d_dirty;    // anchored polish: D != 0 (sweeps since the field in u64 was last formed)
   int64_t anchor_sweeps;  // anchored polish: sweeps since the last anchor set-up
+  int sa_pending;         // the loaded field has not had its annealing sweeps yet
   void *ws_base;  // workspace allocation
   Workspace ws;
   double *host;   // pinned readback buffer
@@ -322,6 +336,7 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
   }
   c->phase = c->prm.bulk == LGT_FP64 ? 1 : 0;
   c->anchored = c->d_dirty = 0;
+  c->sa_pending = c->prm.sa_sweeps > 0;
   c->active_slices = g.nt;
   c->cfg.omega = c->prm.omega;  // omega_polish takes over at promotion
   c->sweeps_bulk = c->sweeps_fp64 = 0;
@@ -786,6 +801,43 @@ static bool loop_ready(lgt_ctx *c, int slot, int64_t remaining) {
   return true;
 }
 
+// ------------------------------------------------------ simulated annealing
+// beta of annealing sweep i of n: geometric from beta0 to beta1
+static double sa_beta(double beta0, double beta1, int n, int i) {
+  if (n <= 1) return beta1;
+  return beta0 * pow(beta1 / beta0, (double)i / (double)(n - 1));
+}
+
+// The loaded field's annealing sweeps (heat bath, launch configuration 0),
+// counted as sweeps of the current phase.
+static lgt_status run_annealing(lgt_ctx *c, int64_t *remaining) {
+  const int n = (int)(c->prm.sa_sweeps < *remaining ? c->prm.sa_sweeps : *remaining);
+  const int fmt = work_fmt(c);
+  void *links = c->phase == 0 ? c->u32 : c->u64;
+  void *G = c->phase == 0 ? c->G : nullptr;
+  const int kind = c->phase == 0 ? 0 : 1;
+  SweepCfg sc = c->cfg;
+  sc.algo = ALGO_SA;
+  const int bt = batch_begin(c, kind);
+  for (int i = 0; i < n; i++) {
+    sc.beta = sa_beta(c->prm.sa_beta0, c->prm.sa_beta1, c->prm.sa_sweeps, i);
+    const int reunit = c->phase == 0 && c->prm.reunit_every > 0 && ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
+    for (int parity = 0; parity < 2; parity++)
+      LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, sc, parity, c->sweep_index, reunit, 0, 0, c->stream));
+    c->sweep_index++;
+    if (kind == 0) c->sweeps_bulk++;
+    else c->sweeps_fp64++;
+  }
+  batch_end(c, bt);
+  c->last_sites = lgt_cfg_sites(0);
+  c->stats.sweep_launches[kind] += 2 * n;
+  c->stats.launches += 2 * n;
+  c->stats.site_updates[kind] += 2LL * n * c->g.vs_half * c->g.nt;
+  *remaining -= n;
+  c->sa_pending = 0;
+  return sync_stream(c);
+}
+
 // ------------------------------------------------------------- the driver
 extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   if (!ctx) {
@@ -801,6 +853,10 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   Meas m;
   lgt_status st;
   bool promoted = false;
+  if (c->sa_pending && (c->phase == 0 || c->phase == 1)) {
+    st = run_annealing(c, &remaining);
+    if (st != LGT_OK) return st;
+  }
   if (c->phase == 0) {
     // bulk FP32 phase: until the working field's theta drops below theta_switch
     // or stops improving (the FP32 rounding floor)

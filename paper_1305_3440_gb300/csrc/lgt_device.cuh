@@ -29,7 +29,7 @@ enum { FMT_PAIR = 3 };
 // fixed anchor field (FP32-12 copy + K0 pairs) with D = G - 1 as pairs.
 enum { FMT_ANCHOR = 4 };
 enum { GAUGE_LANDAU = 0, GAUGE_COULOMB = 1 };
-enum { ALGO_OR = 0, ALGO_SR = 1 };
+enum { ALGO_OR = 0, ALGO_SR = 1, ALGO_SA = 2 };  // SA: simulated-annealing heat bath
 
 #define LGT_RE(a, b) (2 * (3 * (a) + (b)))
 #define LGT_IM(a, b) (2 * (3 * (a) + (b)) + 1)
@@ -347,6 +347,76 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
 
 #define LGT_SR_TAG 0x53524C58u  // stream tag of the stochastic-relaxation draws
 
+// ------------------------------------------- simulated annealing (heat bath)
+// Simulated annealing (named by the paper as a preconditioner, Sec. 1) is
+// read as sweeps whose subgroup elements r are drawn from exp(beta Re tr[r M])
+// times Haar measure, beta rising over the sweeps.  With p the maximum
+// (closed form above) and q the block projection, Re tr[r M] = 2 |q| (r . p),
+// so r = a p (matrix product), a0 = x drawn from sqrt(1 - x^2) exp(alpha x)
+// on [-1, 1] with alpha = 2 beta |q| (Kennedy and Pendleton 1985: at most
+// LGT_SA_ATTEMPTS tries, else the subgroup is left unchanged), the vector
+// part of a uniform on the sphere of radius sqrt(1 - x^2).  Draws: Philox,
+// key = seed, counter = (site, subgroup << 24 | attempt, sweep, tag).
+#define LGT_SA_TAG 0x53414842u  // stream tag of the heat-bath draws
+#define LGT_SA_ATTEMPTS 64u
+#define LGT_SA_DIRECTION 0xFFFFFFu
+
+struct SaDraw {
+  double beta;
+  uint2 key;
+  uint32_t site, sweep;
+};
+
+template <typename R>
+__device__ __forceinline__ R unit_open(uint32_t w) {
+  return (R(w) + R(0.5)) * R(1.0 / 4294967296.0);
+}
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+__device__ __forceinline__ float cos_t(float x) { return cosf(x); }
+__device__ __forceinline__ double cos_t(double x) { return cos(x); }
+__device__ __forceinline__ float sin_t(float x) { return sinf(x); }
+__device__ __forceinline__ double sin_t(double x) { return sin(x); }
+
+// Heat-bath element for a block projection given at twice the unit scale
+// (qq = 2 q, as local_update forms it): alpha = 2 beta |q| = beta |qq|.
+// r stays the identity on a degenerate block or when every attempt fails.
+template <typename R>
+__device__ __forceinline__ void su2_heatbath(R qq0, R qq1, R qq2, R qq3, const SaDraw &sd, int s, R &r0, R &r1,
+                                             R &r2, R &r3) {
+  r0 = R(1), r1 = R(0), r2 = R(0), r3 = R(0);
+  const R n2 = qq0 * qq0 + qq1 * qq1 + qq2 * qq2 + qq3 * qq3;
+  if (!(n2 > R(0)) || !(sd.beta > 0.0)) return;
+  const R norm = sqrt(n2);
+  const R alpha = R(sd.beta) * norm;
+  const R two_pi = R(6.283185307179586476925286766559);
+  R x = R(1);
+  bool ok = false;
+  for (uint32_t k = 0; k < LGT_SA_ATTEMPTS && !ok; k++) {
+    const uint4 w = philox4x32_10(make_uint4(sd.site, ((uint32_t)s << 24) | k, sd.sweep, LGT_SA_TAG), sd.key);
+    const R c = cos_t(two_pi * unit_open<R>(w.y));
+    const R delta = -(log_t(unit_open<R>(w.x)) + c * c * log_t(unit_open<R>(w.z))) / alpha;
+    const R u3 = unit_open<R>(w.w);
+    if (u3 * u3 <= R(1) - R(0.5) * delta) {
+      x = R(1) - delta;
+      ok = true;
+    }
+  }
+  if (!ok) return;
+  const R inv = R(1) / norm;
+  const R p0 = qq0 * inv, p1 = -qq1 * inv, p2 = -qq2 * inv, p3 = -qq3 * inv;
+  const uint4 w = philox4x32_10(make_uint4(sd.site, ((uint32_t)s << 24) | LGT_SA_DIRECTION, sd.sweep, LGT_SA_TAG), sd.key);
+  const R cth = R(2) * unit_open<R>(w.x) - R(1);
+  const R sth = sqrt(R(1) - cth * cth), phi = two_pi * unit_open<R>(w.y);
+  const R rad = x * x < R(1) ? sqrt(R(1) - x * x) : R(0);
+  const R a0 = x, a1 = rad * sth * cos_t(phi), a2 = rad * sth * sin_t(phi), a3 = rad * cth;
+  // r = a p for the matrices [[r0 + i r3, r2 + i r1], [-r2 + i r1, r0 - i r3]]
+  r0 = a0 * p0 - a1 * p1 - a2 * p2 - a3 * p3;
+  r1 = a0 * p1 + a1 * p0 + a3 * p2 - a2 * p3;
+  r2 = a0 * p2 + a2 * p0 + a1 * p3 - a3 * p1;
+  r3 = a0 * p3 + a3 * p0 + a2 * p1 - a1 * p2;
+}
+
 // --------------------------------------------------- Sec. 3: local update
 // Maximise Re tr[g K] over SU(3) by one pass over the SU(2) subgroups
 // (0,1), (0,2), (1,2) (Cabibbo-Marinari).  W starts as K; for each subgroup
@@ -355,7 +425,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
 // overrelaxed to first order (Sec. 3.1) or squared with probability p
 // (Sec. 3.2), and W <- R W, g <- R g.  On return g holds the update.
 template <typename R, int ALGO>
-__device__ __forceinline__ void local_update(R W[18], R g[18], R omega, uint64_t sr_thr, uint4 draws) {
+__device__ __forceinline__ void local_update(R W[18], R g[18], R omega, uint64_t sr_thr, uint4 draws,
+                                             const SaDraw *sa = nullptr) {
 #pragma unroll
   for (int s = 0; s < 3; s++) {
     const int i = (s == 2) ? 1 : 0;
@@ -367,14 +438,18 @@ __device__ __forceinline__ void local_update(R W[18], R g[18], R omega, uint64_t
     const R q3 = W[LGT_IM(i, i)] - W[LGT_IM(j, j)];
     const R n2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
     R r0 = R(1), r1 = R(0), r2 = R(0), r3 = R(0);
-    if (n2 > R(0)) {
+    if (ALGO == ALGO_SA) {
+      su2_heatbath<R>(q0, q1, q2, q3, *sa, s, r0, r1, r2, r3);
+    } else if (n2 > R(0)) {
       const R inv = rsqrt_t(n2);
       r0 = q0 * inv;
       r1 = -q1 * inv;
       r2 = -q2 * inv;
       r3 = -q3 * inv;
     }
-    if (ALGO == ALGO_OR) {
+    if (ALGO == ALGO_SA) {
+      // drawn above
+    } else if (ALGO == ALGO_OR) {
       r0 = (R(1) - omega) + omega * r0;
       r1 *= omega;
       r2 *= omega;

@@ -95,6 +95,7 @@ struct SweepArgs {
   unsigned long long sr_thr;
   unsigned long long seed;
   unsigned long long sweep;
+  double beta;  // ALGO_SA
   int transform_temporal;
   int reunit;
   // batched launches only: reunitarise when (count_base + s + 1) % reunit_every == 0
@@ -156,6 +157,7 @@ struct SweepCfg {
   unsigned long long sr_thr;
   unsigned long long seed;
   int transform_temporal;
+  double beta = 0.0;         // ALGO_SA: inverse temperature of the sweep
 };
 
 // Single-lattice half-sweep kernels, one per (format, gauge, algorithm,

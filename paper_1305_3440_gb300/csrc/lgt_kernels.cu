@@ -82,6 +82,7 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->sr_thr = c.sr_thr;
   a->seed = c.seed;
   a->sweep = sweep;
+  a->beta = c.beta;
   a->transform_temporal = c.transform_temporal;
   a->reunit = reunit;
   a->reunit_every = 0;

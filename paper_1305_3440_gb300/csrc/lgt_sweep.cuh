@@ -50,6 +50,19 @@ __device__ __forceinline__ void k_term(R k[18], const R uf[18], const R ub[18]) 
   acc_add_dag(k, ub);
 }
 
+// the heat-bath stream of one site update (simulated annealing)
+__device__ __forceinline__ SaDraw sa_draw_of(const SweepArgs &a, const Coords &c) {
+  SaDraw d;
+  d.beta = a.beta;
+  d.key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+  d.site = (uint32_t)((unsigned long long)c.x1 +
+                      (unsigned long long)a.g.n1 *
+                          ((unsigned long long)c.x2 +
+                           (unsigned long long)a.g.n2 * ((unsigned long long)c.x3 + (unsigned long long)a.g.n3 * c.t)));
+  d.sweep = (uint32_t)a.sweep;
+  return d;
+}
+
 __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
   const unsigned long long lex =
       (unsigned long long)c.x1 +
@@ -120,7 +133,9 @@ __device__ __forceinline__ void site_update_f32(const SweepArgs &a, int p, const
   uint4 draws = make_uint4(0, 0, 0, 0);
   if (ALGO == ALGO_SR) draws = sr_draws(a, c);
   float gm[18];
-  local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+  SaDraw sd;
+  if (ALGO == ALGO_SA) sd = sa_draw_of(a, c);
+  local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws, &sd);
 #pragma unroll
   for (int mu = MU0; mu < 4; mu++) {
     float r[18];
@@ -464,7 +479,9 @@ __device__ __forceinline__ void sweep_body_f64(const SweepArgs &a, int p, int t,
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
     double gm[18];
-    local_update<double, ALGO>(W, gm, a.omega, a.sr_thr, draws);
+    SaDraw sd;
+    if (ALGO == ALGO_SA) sd = sa_draw_of(a, c);
+    local_update<double, ALGO>(W, gm, a.omega, a.sr_thr, draws, &sd);
     const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
     for (int mu = mu_lo; mu < 4; mu++) {
       const int nbm = mu < MU0 ? cb_shift(a.g, c, 0, -1) : nb[mu];

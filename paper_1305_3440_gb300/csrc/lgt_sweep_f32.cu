@@ -33,6 +33,12 @@ static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
   LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_SR)
   LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_OR)
   LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_SR)
+  if constexpr (CFG == 0) {  // the annealing sweeps run in configuration 0 only
+    LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_SA)
+    LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_SA)
+    LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_SA)
+    LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_SA)
+  }
 #undef LGT_PICK
   return nullptr;
 }

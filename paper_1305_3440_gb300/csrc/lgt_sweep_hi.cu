@@ -26,9 +26,15 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
 template <int CFG>
 static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
   if (fmt == FMT_F64) {
+    if constexpr (CFG == 0) {  // the annealing sweeps run in configuration 0 only
+      if (algo == ALGO_SA)
+        return gauge == GAUGE_LANDAU ? k_sweep_f64<GAUGE_LANDAU, ALGO_SA, CFG> : k_sweep_f64<GAUGE_COULOMB, ALGO_SA, CFG>;
+    }
+    if (algo == ALGO_SA) return nullptr;
     if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_f64<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_f64<GAUGE_LANDAU, ALGO_OR, CFG>;
     return algo == ALGO_SR ? k_sweep_f64<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_f64<GAUGE_COULOMB, ALGO_OR, CFG>;
   }
+  if (algo == ALGO_SA) return nullptr;
   if (fmt == FMT_PAIR) {
     if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_pair<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_pair<GAUGE_LANDAU, ALGO_OR, CFG>;
     return algo == ALGO_SR ? k_sweep_pair<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_pair<GAUGE_COULOMB, ALGO_OR, CFG>;

@@ -38,7 +38,9 @@ class lgt_params(ctypes.Structure):
                 ("theta_tol", ctypes.c_double), ("theta_switch", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reunit_every", ctypes.c_int32), ("block_size", ctypes.c_int32),
-                ("polish", ctypes.c_int32), ("launch_config", ctypes.c_int32), ("omega_polish", ctypes.c_double)]
+                ("polish", ctypes.c_int32), ("launch_config", ctypes.c_int32), ("omega_polish", ctypes.c_double),
+                ("sa_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sa_beta0", ctypes.c_double),
+                ("sa_beta1", ctypes.c_double)]
 
 
 class lgt_result(ctypes.Structure):

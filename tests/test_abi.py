@@ -67,7 +67,8 @@ def test_defaults(lgt):
 @pytest.mark.parametrize("field,value", [("dims", (8, 8, 8, 7)), ("dims", (0, 8, 8, 8)),
                                          ("omega", 2.0), ("omega", 0.9), ("check_every", 0),
                                          ("block_size", 96), ("theta_tol", 0.0), ("bulk", 7),
-                                         ("launch_config", 11), ("launch_config", -1)])
+                                         ("launch_config", 11), ("launch_config", -1), ("sa_sweeps", -1),
+                                         ("reserved", 1)])
 def test_bad_params_rejected_before_any_device_work(lgt, field, value):
     import numpy as np
     kw = {"dims": (4, 4, 4, 4), field: value}
@@ -77,6 +78,14 @@ def test_bad_params_rejected_before_any_device_work(lgt, field, value):
         lgt.lgt_create(p, links)
     assert e.value.status == lgt.LGT_EINVAL
     assert lgt.lgt_last_error()
+
+
+@pytest.mark.parametrize("b0,b1", [(0.0, 1.0), (2.0, 1.0), (1.0, float("inf"))])
+def test_annealing_schedule_rejected(lgt, b0, b1):
+    import numpy as np
+    p = lgt.lgt_params_default(dims=(4, 4, 4, 4), sa_sweeps=3, sa_beta0=b0, sa_beta1=b1)
+    with pytest.raises(lgt.LgtError):
+        lgt.lgt_create(p, np.zeros((4, 4, 4, 4, 4, 3, 3), np.complex128))
 
 
 def test_sr_probability_range(lgt):

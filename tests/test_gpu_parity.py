@@ -673,3 +673,69 @@ def test_anchored_polish_from_an_early_promotion(lgt):
     m = O.measure(V)
     assert m["theta"] < 1e-14
     assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+
+
+# ------------------------------------------------ simulated annealing
+@pytest.mark.parametrize("gauge", list(GAUGES))
+def test_annealing_sweeps_match_the_oracle(lgt, gauge):
+    """The heat-bath sweeps draw from the same Philox streams as the oracle; in
+    FP64 the Kennedy-Pendleton accept/reject decisions agree (they differ only if
+    a comparison falls within rounding of its threshold), so three annealing
+    sweeps agree with the oracle to FP64 rounding.  In FP32 storage and
+    arithmetic a few decisions may flip; nearly every entry still agrees to
+    FP32 accuracy and the result is a gauge transform of the input."""
+    U = synth.field(DIMS_RAGGED, 0.5, 51)
+    g = GAUGES[gauge]
+    ref = U.copy()
+    O.sa_sweeps(ref, 3, 2.0, 20.0, gauge=g, seed=13)
+    for bulk, tol in [(lgt.LGT_FP64, 1e-11), (lgt.LGT_FP32_12, 1e-5)]:
+        p = lgt.lgt_params_default(dims=U.shape[:4], gauge=g, bulk=bulk, seed=13, sa_sweeps=3, sa_beta0=2.0,
+                                   sa_beta1=20.0, max_sweeps=3, reunit_every=0)
+        ctx = lgt.lgt_create(p, U)
+        try:
+            st, res = lgt.lgt_fix(ctx)  # the 3 annealing sweeps use up max_sweeps
+            V = lgt.lgt_get_links(ctx, U.shape[:4]) if bulk == lgt.LGT_FP64 else lgt.lgt_get_working_links(ctx, U.shape[:4])
+            Vg = lgt.lgt_get_links(ctx, U.shape[:4])
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st == lgt.LGT_ENOTCONV and res.sweeps_bulk + res.sweeps_fp64 == 3
+        err = np.abs(V - ref)
+        if bulk == lgt.LGT_FP64:
+            assert err.max() < tol, err.max()
+        else:
+            assert np.mean(err < tol) > 0.995, np.mean(err < tol)
+        assert np.abs(plaquettes(Vg) - plaquettes(U)).max() < 1e-12
+
+
+def test_annealing_then_relaxation(lgt):
+    """lgt_fix with annealing first: the FP64 path follows the oracle's annealing
+    and relaxation to the same converged F; the mixed ladder converges too."""
+    dims = (4, 6, 4, 8)
+    U = synth.field(dims, 0.6, 52)
+    kw = dict(dims=dims, seed=21, sa_sweeps=40, sa_beta0=1.0, sa_beta1=100.0, theta_tol=1e-14, max_sweeps=5000)
+    ref = U.copy()
+    O.sa_sweeps(ref, 40, 1.0, 100.0, seed=21)
+    r = O.fix(ref, omega=1.7, tol=1e-14, max_sweeps=5000)
+    out = {}
+    for bulk in (lgt.LGT_FP64, lgt.LGT_FP32_12):
+        ctx = lgt.lgt_create(lgt.lgt_params_default(bulk=bulk, **kw), U)
+        try:
+            st, res = lgt.lgt_fix(ctx)
+            V = lgt.lgt_get_links(ctx, dims)
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st == lgt.LGT_OK and O.measure(V)["theta"] < 1e-14
+        assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+        out[bulk] = res.F
+    assert abs(out[lgt.LGT_FP64] - r["F"]) < 1e-10
+
+
+def test_annealing_is_not_served(lgt):
+    srv = lgt.lgt_server_create(1 << 30, 0)
+    try:
+        p = lgt.lgt_params_default(dims=(4, 4, 4, 4), sa_sweeps=5)
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_submit(srv, p, synth.field((4, 4, 4, 4), 0.3, 1))
+        assert e.value.status == lgt.LGT_EINVAL
+    finally:
+        lgt.lgt_server_destroy(srv)

@@ -510,3 +510,87 @@ def test_haar_moments():
     assert abs(np.mean(np.abs(tr) ** 2) - 1) < 0.03
     e, d = unitarity_error(h)
     assert e < 1e-14 and d < 1e-14
+
+
+# ------------------------------------------- simulated annealing (heat bath)
+@pytest.mark.parametrize("alpha", [0.8, 4.0, 16.0, 64.0])
+def test_kp_draws_follow_the_heat_bath_density(alpha):
+    """x with density ~ sqrt(1 - x^2) exp(alpha x) on [-1, 1] has the closed-form
+    moments E[x] = I2(alpha)/I1(alpha) and E[x^2] = 1 - 3 I2/(alpha I1) (modified
+    Bessel functions; derivatives of the normalisation pi I1(alpha)/alpha)."""
+    from scipy.special import iv
+    n = 200000
+    x, fails = O.kp_draws(alpha, n, seed=11)
+    assert fails <= 2e-3 * n
+    x = x[np.isfinite(x)]
+    assert np.all(np.abs(x) <= 1.0)
+    m1 = iv(2, alpha) / iv(1, alpha)
+    m2 = 1.0 - 3.0 * iv(2, alpha) / (alpha * iv(1, alpha))
+    var = m2 - m1 * m1
+    assert abs(x.mean() - m1) < 5 * np.sqrt(var / x.size)
+    # fourth central moment bound for the second-moment check
+    assert abs((x * x).mean() - m2) < 5 * np.sqrt(np.var(x * x) / x.size)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 10.0])
+def test_heat_bath_element_is_distributed_around_the_maximum(alpha):
+    """The drawn SU(2) element r is unit, its overlap x = r . p with the maximum p
+    follows the heat-bath moments, and its part orthogonal to p points uniformly
+    (zero mean, isotropic covariance in the 3-space orthogonal to p)."""
+    from scipy.special import iv
+    rng = np.random.default_rng(5)
+    q = rng.normal(size=4)
+    beta = alpha / (2.0 * np.linalg.norm(q))
+    p = np.array([q[0], -q[1], -q[2], -q[3]]) / np.linalg.norm(q)
+    n = 40000
+    r = np.array([O.su2_heatbath(q, beta, seed=9, sweep=3, site=k, subgroup=1) for k in range(n)])
+    assert np.abs(np.linalg.norm(r, axis=1) - 1).max() < 1e-14
+    x = r @ p
+    m1 = iv(2, alpha) / iv(1, alpha)
+    assert abs(x.mean() - m1) < 5 * x.std() / np.sqrt(n)
+    basis = np.linalg.qr(np.column_stack([p, rng.normal(size=(4, 3))]))[0][:, 1:]  # orthonormal, p-orthogonal
+    v = r @ basis
+    v = v / np.linalg.norm(v, axis=1, keepdims=True)
+    assert np.abs(v.mean(axis=0)).max() < 5 / np.sqrt(3 * n)
+    cov = v.T @ v / n
+    assert np.abs(cov - np.eye(3) / 3).max() < 0.02
+
+
+def test_heat_bath_at_large_beta_is_the_maximum():
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        q = rng.normal(size=4)
+        p = np.array([q[0], -q[1], -q[2], -q[3]]) / np.linalg.norm(q)
+        r = O.su2_heatbath(q, 1e8, seed=1, sweep=0, site=int(rng.integers(1 << 30)), subgroup=2)
+        assert np.abs(r - p).max() < 1e-3
+
+
+def test_annealing_schedule_is_geometric():
+    b = [O.sa_beta(0.5, 50.0, 5, i) for i in range(5)]
+    assert b[0] == pytest.approx(0.5) and b[-1] == pytest.approx(50.0)
+    assert np.allclose(np.diff(np.log(b)), np.log(100.0) / 4)
+    assert O.sa_beta(0.5, 50.0, 1, 0) == 50.0
+
+
+@pytest.mark.parametrize("gauge", [O.LANDAU, O.COULOMB])
+def test_annealing_sweeps_are_gauge_transformations(gauge):
+    """Heat-bath updates are gauge transformations like the relaxation's: every
+    plaquette is kept, links stay unitary; at high beta the functional rises."""
+    dims = (4, 4, 6, 4)
+    U = synth.field(dims, 0.5, 41)
+    V = U.copy()
+    O.sa_sweeps(V, 5, 1.0, 10.0, gauge=gauge, seed=3)
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+    e, d = unitarity_error(V)
+    assert e < 1e-13 and d < 1e-13
+    W = V.copy()
+    O.sa_sweeps(W, 10, 1e3, 1e4, gauge=gauge, seed=4, sweep0=5)
+    assert O.measure(W, gauge)["F"] > O.measure(V, gauge)["F"]
+
+
+def test_annealing_then_relaxation_converges():
+    dims = (4, 4, 4, 4)
+    U = synth.field(dims, 0.5, 42)
+    O.sa_sweeps(U, 30, 1.0, 100.0, seed=7)
+    r = O.fix(U, omega=1.7, tol=1e-14, max_sweeps=3000)
+    assert r["converged"] and O.measure(U)["theta"] < 1e-14
