@@ -393,7 +393,10 @@ def run_ours(args):
                 # an omega schedule, not the workload's: omega = 1.7 only down to theta = 1e-4,
                 # then 1.1 (the sweeps after the switch need far fewer sweeps at omega 1.1)
                 ("omega_schedule_1.7_to_1.1", DIMS, dev_in,
-                 dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, theta_switch=1e-4, omega_polish=1.1))]
+                 dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, theta_switch=1e-4, omega_polish=1.1)),
+                # simulated annealing first (200 heat-bath sweeps, beta 1 -> 100), then the ladder
+                ("annealing_200", DIMS, dev_in,
+                 dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, sa_sweeps=200, sa_beta0=1.0, sa_beta1=100.0))]
         small = torch.from_numpy(synth.field((8, 8, 8, 8), 0.3, 1)).to(f"cuda:{local}")
         runs += [("8x4_fp64", (8, 8, 8, 8), small, dict(bulk=lgt.LGT_FP64, omega=OMEGA, max_sweeps=1000)),
                  ("8x4_mixed", (8, 8, 8, 8), small, dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, max_sweeps=1000))]
