@@ -24,8 +24,9 @@
 //     G U' G^+ in FP64 with G orthonormalised in FP64, an exact gauge transform
 //     of the input whatever G's rounding.
 // Per site update the sweep reads K0 (144 B), 8 FP32 links (384 B), the high
-// parts of 8 neighbours' D (384 B) and its own D (96 B), and writes its own D
-// (96 B): 1104 B, no link is written.
+// parts of 8 neighbours' D (384 B, each neighbour's read by 8 sites, so 48 B
+// of compulsory traffic) and its own D (96 B), and writes its own D (96 B):
+// 768 B of compulsory traffic; no link is written.
 #pragma once
 
 #include "lgt_device.cuh"
@@ -275,35 +276,6 @@ __device__ __forceinline__ void d_update_lite(f2 D[12], const float dh[18], cons
       D[LGT_RE(i, j)] = pair_add(pair_add(D[LGT_RE(i, j)], f2{d[LGT_RE(i, j)], 0.0f}), f2{re, 0.0f});
       D[LGT_IM(i, j)] = pair_add(pair_add(D[LGT_IM(i, j)], f2{d[LGT_IM(i, j)], 0.0f}), f2{im, 0.0f});
     }
-}
-
-// D <- D + delta + delta D on rows 0 and 1 (G <- g G), pair arithmetic
-__device__ __forceinline__ void d_update(f2 D[18], const f2 d[18]) {
-  f2 r[12];
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-      f2 c[6], x[6];
-#pragma unroll
-      for (int k = 0; k < 3; k++) {  // re: d_re D_re - d_im D_im
-        c[2 * k] = d[LGT_RE(i, k)];
-        x[2 * k] = D[LGT_RE(k, j)];
-        c[2 * k + 1] = pair_neg(d[LGT_IM(i, k)]);
-        x[2 * k + 1] = D[LGT_IM(k, j)];
-      }
-      r[LGT_RE(i, j)] = pair_axpy6(pair_add(D[LGT_RE(i, j)], d[LGT_RE(i, j)]), c, x);
-#pragma unroll
-      for (int k = 0; k < 3; k++) {  // im: d_re D_im + d_im D_re
-        c[2 * k] = d[LGT_RE(i, k)];
-        x[2 * k] = D[LGT_IM(k, j)];
-        c[2 * k + 1] = d[LGT_IM(i, k)];
-        x[2 * k + 1] = D[LGT_RE(k, j)];
-      }
-      r[LGT_IM(i, j)] = pair_axpy6(pair_add(D[LGT_IM(i, j)], d[LGT_IM(i, j)]), c, x);
-    }
-#pragma unroll
-  for (int e = 0; e < 12; e++) D[e] = r[e];
 }
 
 }  // namespace lgt
