@@ -48,7 +48,28 @@ __global__ void __launch_bounds__(256) k_measure_batch(const BatchMeas *jobs, in
   measure_body<FMT>(J.a, t, p, rem - p * J.nbx, J.nbx);
 }
 
+// FP32 bulk sweeps of the batch: the lean one-thread layout (K streamed, links
+// reloaded for the write-back; <= 128 registers, 4 blocks of 128 threads per
+// SM), as launch configuration 8 of the single-lattice kernels.
+template <int FMT, int GAUGE, int ALGO>
+__global__ void __launch_bounds__(128, 4) k_sweep_batch_lean(const BatchSweep *jobs, int n, int p, int s) {
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, blockIdx.x);
+  const BatchSweep &J = jobs[k];
+  SweepArgs a = J.a;
+  a.sweep += (unsigned long long)s;
+  a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
+  const int local = blockIdx.x - J.block_begin;
+  const int t = local / J.nbx;
+  sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, t, local - t * J.nbx);
+}
+
 typedef void (*batch_fn)(const BatchSweep *, int, int, int);
+
+template <int FMT>
+static batch_fn pick_batch_lean(int gauge, int algo) {
+  if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_batch_lean<FMT, GAUGE_LANDAU, ALGO_SR> : k_sweep_batch_lean<FMT, GAUGE_LANDAU, ALGO_OR>;
+  return algo == ALGO_SR ? k_sweep_batch_lean<FMT, GAUGE_COULOMB, ALGO_SR> : k_sweep_batch_lean<FMT, GAUGE_COULOMB, ALGO_OR>;
+}
 
 template <int FMT>
 static batch_fn pick_batch_fmt(int gauge, int algo) {
@@ -61,8 +82,8 @@ cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSwe
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
   batch_fn fn = nullptr;
   if (fmt == FMT_F64) fn = pick_batch_fmt<FMT_F64>(gauge, algo);
-  else if (fmt == FMT_F32_18) fn = pick_batch_fmt<FMT_F32_18>(gauge, algo);
-  else if (fmt == FMT_F32_12) fn = pick_batch_fmt<FMT_F32_12>(gauge, algo);
+  else if (fmt == FMT_F32_18) fn = block == 128 ? pick_batch_lean<FMT_F32_18>(gauge, algo) : pick_batch_fmt<FMT_F32_18>(gauge, algo);
+  else if (fmt == FMT_F32_12) fn = block == 128 ? pick_batch_lean<FMT_F32_12>(gauge, algo) : pick_batch_fmt<FMT_F32_12>(gauge, algo);
   else if (fmt == FMT_PAIR) fn = pick_batch_fmt<FMT_PAIR>(gauge, algo);
   else if (fmt == FMT_ANCHOR) fn = pick_batch_fmt<FMT_ANCHOR>(gauge, algo);
   if (!fn) return cudaErrorInvalidValue;
