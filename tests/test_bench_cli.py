@@ -41,3 +41,24 @@ def test_gpu_arm_refuses_without_a_device(built):
         pytest.skip("a GPU is present")
     r = _run(["--steps", "1", "--warmup", "0"], timeout=120)
     assert r.returncode != 0 and "CUDA GPU" in (r.stdout + r.stderr)
+
+
+def test_traffic_record_is_tied_to_the_kernel_sources(tmp_path, monkeypatch):
+    """bench.py uses an ncu traffic record only while the kernel sources hash to
+    the value stored with it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.kernel_source_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.md").write_text(
+        f"    traffic-record: kernel=k_sweep_f32 config=7 bytes_per_launch=123 sources={h}\n"
+        "    traffic-record: kernel=k_sweep_f32 config=8 bytes_per_launch=456 sources=0000000000000000\n")
+    for rel in bench.KERNEL_SOURCES:
+        dst = tmp_path / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("k_sweep_f32", 7) == 123
+    assert bench.recorded_traffic("k_sweep_f32", 8) is None  # recorded for other sources
+    assert bench.recorded_traffic("k_sweep_anchor", 0) is None
