@@ -148,8 +148,10 @@ typedef struct {
  * element drawn from exp(beta Re tr[r M]) with respect to Haar measure (an
  * SU(2) heat bath, Kennedy-Pendleton draws from Philox streams keyed by seed),
  * beta rising geometrically from sa_beta0 to sa_beta1.  They run in the bulk
- * precision (launch configuration 0) and count as bulk sweeps; lgt_fix runs
- * them once per loaded field.  Not served (lgt_submit: LGT_EINVAL). */
+ * precision (launch configuration 0) and count as bulk sweeps; in FP32 every
+ * annealing sweep reunitarises the links and G it writes, whatever
+ * reunit_every says.  lgt_fix runs them once per loaded field.  Not served
+ * (lgt_submit: LGT_EINVAL). */
 
 /* Launch configurations of the sweep kernels (lgt_params.launch_config - 1):
  *   one thread per site:  0: 128 threads, <= 255 registers; 1: 128, <= 170;

@@ -821,7 +821,12 @@ static lgt_status run_annealing(lgt_ctx *c, int64_t *remaining) {
   const int bt = batch_begin(c, kind);
   for (int i = 0; i < n; i++) {
     sc.beta = sa_beta(c->prm.sa_beta0, c->prm.sa_beta1, c->prm.sa_sweeps, i);
-    const int reunit = c->phase == 0 && c->prm.reunit_every > 0 && ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
+    // Heat-bath rotations are far from the identity.  The FP32 storage keeps G
+    // (and 12-real links) as two rows and rebuilds the third as a cross product,
+    // so under such rotations the rows' norm error grows by about 4/3 per update
+    // and overflows within some 50 sweeps: in FP32 every annealing sweep
+    // reunitarises what it writes.
+    const int reunit = c->phase == 0;
     for (int parity = 0; parity < 2; parity++)
       LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, sc, parity, c->sweep_index, reunit, 0, 0, c->stream));
     c->sweep_index++;

@@ -730,6 +730,41 @@ def test_annealing_then_relaxation(lgt):
     assert abs(out[lgt.LGT_FP64] - r["F"]) < 1e-10
 
 
+@pytest.mark.parametrize("bulk", ["fp32_12", "fp32_18"])
+def test_long_fp32_annealing_stays_unitary(lgt, bulk):
+    """Hundreds of heat-bath sweeps at low beta rotate every site far from the
+    identity.  G (and 12-real links) keep two rows in FP32 and rebuild the third,
+    which under such rotations amplifies the rows' norm error by about 4/3 per
+    update; without reprojection it overflows within some 50 sweeps.  After 300
+    FP32 annealing sweeps the working links and the transformed FP64 field are
+    finite and unitary, the plaquettes are those of the input, and the ladder
+    then converges."""
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 1.0, 302)
+    kw = dict(dims=dims, bulk=getattr(lgt, "LGT_" + bulk.upper()), seed=3, sa_sweeps=300, sa_beta0=0.5,
+              sa_beta1=50.0, reunit_every=0)
+    ctx = lgt.lgt_create(lgt.lgt_params_default(max_sweeps=300, **kw), U)
+    try:
+        st, res = lgt.lgt_fix(ctx)  # the annealing sweeps use up max_sweeps
+        W = lgt.lgt_get_working_links(ctx, dims)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_ENOTCONV and res.sweeps_bulk == 300
+    for X in (W, V):
+        assert np.isfinite(X.view(np.float64)).all()
+    assert max(unitarity_error(W)) < 1e-5 and max(unitarity_error(V)) < 1e-12
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+    ctx = lgt.lgt_create(lgt.lgt_params_default(max_sweeps=40000, theta_tol=1e-14, **kw), U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and O.measure(V)["theta"] < 1e-14
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+
+
 def test_annealing_is_not_served(lgt):
     srv = lgt.lgt_server_create(1 << 30, 0)
     try:
