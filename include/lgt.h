@@ -122,7 +122,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..10: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..11: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
   int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
@@ -165,9 +165,16 @@ typedef struct {
  *                            in shared memory (cp.async) during the update;
  *   one thread per site, lean (FP32 bulk sweeps only): K(x) streamed, links
  *   loaded again for the write-back:
- *                         8: 128 threads, <= 128 registers; 9: 128, <= 96.
- * A configuration that a phase's kernel lacks (4-9 after promotion; 7 on
- * FP32-18 links) falls back to configuration 0 for that phase.  Every
+ *                         8: 128 threads, <= 128 registers; 9: 128, <= 96;
+ *   one thread per site, streaming (FP32-12 bulk sweeps only):
+ *                        10: as 7, but one launch runs up to 64 half-sweeps:
+ *                            blocks take (half-sweep, slice, 8 tiles) items
+ *                            in order from a counter and start an item once
+ *                            the previous half-sweep has finished its slice
+ *                            and both neighbours (bounded waits: a wait over
+ *                            2 s fails the call with LGT_ECUDA).
+ * A configuration that a phase's kernel lacks (4-10 after promotion; 7 and 10
+ * on FP32-18 links) falls back to configuration 0 for that phase.  Every
  * configuration forms K(x) and the fused estimate in the same order; results
  * differ only where the compiler fuses multiply-adds differently in the two
  * kernels (FP32 rounding; converged F within 1e-10). */
@@ -249,7 +256,8 @@ LGT_API lgt_status lgt_load(lgt_ctx *ctx, const double *links, int links_on_devi
 
 typedef struct {
   double sweep_ms[2];        /* device time of the sweep kernels: [0] bulk FP32, [1] FP64 */
-  int64_t sweep_launches[2]; /* half-sweep kernel launches in each precision */
+  int64_t sweep_launches[2]; /* half-sweeps run by the sweep kernels in each precision
+                                (one per launch, except the streaming configuration's) */
   int64_t site_updates[2];   /* site updates done in each precision (converged Coulomb slices excluded) */
   int64_t launches;          /* every kernel launch of this context */
   double measure_ms;         /* device time of exact measurements */

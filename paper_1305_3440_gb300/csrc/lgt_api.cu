@@ -224,6 +224,8 @@ struct lgt_ctx {
   int use_loops;                   // 0: host-driven chunks only (LGT_FIX_GRAPHS=0, or a loop failed to build)
   LoopState *d_loop, *h_loop;      // loop state (device) and its pinned copy
   cudaGraphExec_t loop_exec[2];
+  int loop_sweep_launches[2];      // sweep kernel launches in one chunk of each loop
+  int *h_err;                      // pinned copy of the workspace's error word
 };
 
 static void resolve_events(lgt_ctx *c);
@@ -245,6 +247,7 @@ static void ctx_free(lgt_ctx *c) {
     if (c->loop_exec[k]) cudaGraphExecDestroy(c->loop_exec[k]);
   if (c->d_loop) cudaFree(c->d_loop);
   if (c->h_loop) cudaFreeHost(c->h_loop);
+  if (c->h_err) cudaFreeHost(c->h_err);
   if (c->stage) cudaFree(c->stage);
   if (c->u64) cudaFree(c->u64);
   if (c->u32) cudaFree(c->u32);
@@ -293,9 +296,19 @@ static void resolve_events(lgt_ctx *c) {
   c->pending->clear();
 }
 
+// A streaming sweep launch that gave up waiting for a neighbouring slice (it
+// never should: see the streaming body) leaves bit LGT_ERR_STREAM_WAIT in the
+// error word and the field half-updated; every synchronisation reports it
+// until the next lgt_load.
 static lgt_status sync_stream(lgt_ctx *c) {
+  const bool streaming = lgt_cfg_stream(c->cfg_bulk) && c->h_err;
+  if (streaming) LGT_CUDA(cudaMemcpyAsync(c->h_err, c->ws.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LGT_CUDA(cudaStreamSynchronize(c->stream));
   resolve_events(c);
+  if (streaming && (*c->h_err & LGT_ERR_STREAM_WAIT)) {
+    lgt_set_error("a streaming sweep launch timed out waiting for a neighbouring slice; the field is invalid");
+    return LGT_ECUDA;
+  }
   return LGT_OK;
 }
 
@@ -402,6 +415,8 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   CTX_CUDA(cudaMallocHost(&c->host, 4096 + sizeof(double) * 2 * (size_t)g.nt));
   CTX_CUDA(cudaMalloc(&c->d_loop, sizeof(LoopState)));
   CTX_CUDA(cudaMallocHost(&c->h_loop, sizeof(LoopState)));
+  CTX_CUDA(cudaMallocHost(&c->h_err, sizeof(int)));
+  *c->h_err = 0;
   {
     const char *lv = getenv("LGT_FIX_GRAPHS");  // "0": lgt_fix drives every chunk from the host
     c->use_loops = !(lv && lv[0] == '0');
@@ -520,24 +535,20 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
     c->d_dirty = 1;
   }
   const int bt = batch_begin(c, kind);
-  for (int h = 0; h < n_half; h++) {
-    const int parity = (first_parity + h) & 1;
-    int reunit = 0;
-    if (c->phase == 0 && c->prm.reunit_every > 0) reunit = ((c->sweeps_bulk + 1) % c->prm.reunit_every) == 0;
-    const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
-    LGT_CUDA(launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, c->sweep_index, reunit, use_mask, lc,
-                               c->stream, anch ? c->k0 : nullptr));
-    c->last_sites = lgt_cfg_sites(lc);
-    if (parity == 1) {
-      c->sweep_index++;
-      if (c->phase == 0) c->sweeps_bulk++;
-      else c->sweeps_fp64++;
-    }
-  }
+  const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
+  const int reunit_every = c->phase == 0 ? c->prm.reunit_every : 0;
+  int launches = 0;
+  LGT_CUDA(launch_half_sweeps(fmt, c->g, links, G, c->ws, c->cfg, first_parity, n_half, c->sweep_index, c->sweeps_bulk,
+                              reunit_every, use_mask, lc, c->stream, anch ? c->k0 : nullptr, nullptr, &launches));
+  c->last_sites = lgt_cfg_sites(lc);
+  const int64_t done = (first_parity + n_half) / 2;  // sweeps whose odd half ran
+  c->sweep_index += (uint64_t)done;
+  if (c->phase == 0) c->sweeps_bulk += done;
+  else c->sweeps_fp64 += done;
   batch_end(c, bt);
   if (anch) c->anchor_sweeps += n_half / 2;
   c->stats.sweep_launches[kind] += n_half;
-  c->stats.launches += n_half;
+  c->stats.launches += launches;
   const int64_t slices = use_mask ? c->active_slices : c->g.nt;
   c->stats.site_updates[kind] += (int64_t)n_half * (int64_t)c->g.vs_half * slices;
   return LGT_OK;
@@ -713,11 +724,9 @@ static lgt_status build_loop(lgt_ctx *c, int slot) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t el = cudaSuccess;
-      for (int sw = 0; sw < k && el == cudaSuccess; sw++)
-        for (int parity = 0; parity < 2 && el == cudaSuccess; parity++)
-          el = launch_half_sweep(fmt, c->g, links, G, c->ws, c->cfg, parity, (unsigned long long)sw, 0, coulomb ? 1 : 0,
-                                 lc, cs, anch ? c->k0 : nullptr, c->d_loop, c->phase == 0 ? c->prm.reunit_every : 0);
+      cudaError_t el = launch_half_sweeps(fmt, c->g, links, G, c->ws, c->cfg, 0, 2 * k, 0, 0,
+                                          c->phase == 0 ? c->prm.reunit_every : 0, coulomb ? 1 : 0, lc, cs,
+                                          anch ? c->k0 : nullptr, c->d_loop, &c->loop_sweep_launches[slot]);
       if (el == cudaSuccess)
         el = launch_fused_finish(c->g, c->ws, c->cfg.gauge, lgt_cfg_sites(lc), coulomb ? target : -1.0, cs);
       if (el == cudaSuccess) el = launch_loop_decide(c->d_loop, c->ws.fused_totals, c->cfg.gauge, k, c->g.vs_half, h, cs);
@@ -785,7 +794,7 @@ static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64
   if (stall) *stall = L.stall;
   c->last_sites = lgt_cfg_sites(lc);
   c->stats.sweep_launches[kind] += 2 * n;
-  c->stats.launches += (int64_t)L.iters * (2 * k + 2);
+  c->stats.launches += (int64_t)L.iters * (c->loop_sweep_launches[slot] + 2);
   c->stats.site_updates[kind] += L.site_updates;
   c->stats.loop_launches++;
   c->stats.loop_chunks += L.iters;

@@ -90,16 +90,15 @@ int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, voi
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   // each configuration: 2 warm-up half-sweeps, then the best of 3 timings of 8
+  // (as the driver issues them: 8 launches, or one streaming launch)
   float best_ms = 1e30f;
   int best = 0;
   for (int k = 0; k < LGT_NCFG && e == cudaSuccess; k++) {
     if (!lgt_cfg_supported(fmt, k)) continue;
-    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++)
-      e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st, aux);
+    e = launch_half_sweeps(fmt, g, links, G, ws, cfg, 0, 2, 0, 0, 0, 0, k, st, aux);
     for (int trial = 0; trial < 3 && e == cudaSuccess; trial++) {
       e = cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 8 && e == cudaSuccess; rep++)
-        e = launch_half_sweep(fmt, g, links, G, ws, cfg, rep & 1, 0, 0, 0, k, st, aux);
+      if (e == cudaSuccess) e = launch_half_sweeps(fmt, g, links, G, ws, cfg, 0, 8, 0, 0, 0, 0, k, st, aux);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;

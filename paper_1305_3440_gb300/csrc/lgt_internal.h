@@ -41,7 +41,8 @@ struct Workspace {
   double *slice_theta;      // [nt]
   double *totals;           // [TOT_N]
   uint8_t *active;          // [nt]
-  int *err;                 // [1]
+  int *err;                 // [1] bit 0: ingest check failed, bit 1: a streaming sweep's wait timed out
+  unsigned *stream_ctr;     // [2 + nt] streaming sweeps: ticket, abort flag, tiles done per slice
 };
 
 size_t workspace_bytes(const Geom &g, int min_block);
@@ -101,6 +102,11 @@ struct SweepArgs {
   // batched launches only: reunitarise when (count_base + s + 1) % reunit_every == 0
   int reunit_every;
   long long count_base;
+  // streaming launches (one kernel for n_half half-sweeps): their counters and error word
+  unsigned *stream;
+  int *err;
+  int n_half;
+  int stream_tiles;  // tiles (of blockDim.x sites) per scheduled item
 };
 
 // Arguments of one lattice's exact measurement.
@@ -177,26 +183,44 @@ struct SweepCfg {
 //   one thread per site, lean (FP32 formats): K(x) streamed, links loaded again
 //   for the write-back:
 //     8: 128 threads, <= 128 registers     9: 128 threads, <= 96 registers
+//   one thread per site, streaming (FP32-12 only): one persistent launch runs
+//   several half-sweeps; its blocks take (half-sweep, slice, tile) items in
+//   order from a ticket counter and start an item as soon as the previous
+//   half-sweep has finished the item's slice and its two neighbours, so the
+//   pipeline does not drain between half-sweeps; staging as configuration 7:
+//    10: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
 // Every configuration forms K(x) in the same order and groups the fused
 // estimate by the same 8 sites; results differ only where the compiler fuses
 // multiply-adds differently in two kernels (FP32 rounding).
-constexpr int LGT_NCFG = 10;
+constexpr int LGT_NCFG = 11;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
-  return c == 1 ? 3 : (c == 3 ? 8 : (c == 4 ? 4 : (c == 5 ? 2 : (c == 6 ? 6 : (c == 7 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : 1)))))));
+  return c == 1 ? 3
+                : (c == 3 ? 8
+                          : (c == 4 ? 4
+                                    : (c == 5 ? 2
+                                              : (c == 6 ? 6 : (c == 7 || c == 10 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : 1)))))));
 }
 __host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4 && c <= 6; }
 __host__ __device__ constexpr bool lgt_cfg_pipe(int c) { return c == 7; }
 __host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9; }
+__host__ __device__ constexpr bool lgt_cfg_stream(int c) { return c == 10; }
 // sites covered by one block (per tile for the pipelined configuration)
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
 // whether a storage format has kernels for a configuration
 __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
   return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
-         (!lgt_cfg_pipe(c) || fmt == FMT_F32_12);
+         (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c)) || fmt == FMT_F32_12);
 }
-// dynamic shared memory of the pipelined configuration: 2 buffers x 27 chunks x 16 B per thread
+// dynamic shared memory of the pipelined and streaming configurations: 2 buffers x 27 chunks x 16 B per thread
 constexpr int LGT_PIPE_SMEM_PER_THREAD = 2 * 27 * 16;
+// streaming configuration: half-sweeps per launch at most, the bound on one
+// wait for a neighbouring slice (after it the launch gives up, sets bit 1 of
+// the error word and ends), and the error bit
+constexpr int LGT_STREAM_MAX_HALF = 64;
+constexpr int LGT_STREAM_TILES = 8;  // tiles (of 128 sites) per scheduled item (LGT_STREAM_TILES in the environment)
+constexpr unsigned long long LGT_STREAM_WAIT_NS = 2000000000ull;
+constexpr int LGT_ERR_STREAM_WAIT = 2;
 // configuration for a requested block size (lgt_params.block_size)
 inline int lgt_cfg_of_block(int block) { return block == 256 ? 2 : (block == 64 ? 3 : 0); }
 // fused-estimate slots: one per 8 consecutive sites of a slice
@@ -214,6 +238,18 @@ cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, cons
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
                               cudaStream_t st, const void *aux = nullptr, const LoopState *loop = nullptr,
                               int reunit_every = 0);
+
+// n_half consecutive half-sweeps, the first of parity p0: half-sweep h has
+// parity (p0 + h) & 1 and belongs to sweep s = (p0 + h) / 2 of the run, whose
+// number is sweep0 + s (with a device loop: loop->sweep + sweep0 + s) and which
+// reunitarises when reunit_every > 0 and (count_base + s + 1) % reunit_every
+// == 0 (with a device loop: loop->count + sweep0 + s + 1).  The streaming
+// configuration runs them in launches of up to LGT_STREAM_MAX_HALF half-sweeps,
+// the others one launch each.  *launches (nullable) receives the kernel launches.
+cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                               int p0, int n_half, unsigned long long sweep0, long long count_base, int reunit_every,
+                               int use_mask, int cfg, cudaStream_t st, const void *aux = nullptr,
+                               const LoopState *loop = nullptr, int *launches = nullptr);
 
 // Fused estimate of F and theta from the last two half-sweeps (each sweep
 // kernel leaves per-warp sums of Re tr K and tr Delta^2 computed from the K it

@@ -5,6 +5,7 @@
 // variants, compiled in parallel), their bodies in lgt_sweep.cuh.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "lgt_device.cuh"
 #include "lgt_internal.h"
@@ -32,6 +33,7 @@ size_t workspace_bytes(const Geom &g, int min_block) {
   b += sizeof(double) * TOT_N;                             // totals
   b += sizeof(unsigned) * ((size_t)g.nt + 1);              // counters
   b += (size_t)g.nt + sizeof(int);                         // active, err
+  b += sizeof(unsigned) * ((size_t)g.nt + 2);              // stream_ctr
   return b + 16 * 20;                                      // alignment slack
 }
 
@@ -65,6 +67,8 @@ void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
   p = align16(p + sizeof(unsigned));
   w->err = (int *)p;
   p = align16(p + sizeof(int));
+  w->stream_ctr = (unsigned *)p;
+  p = align16(p + sizeof(unsigned) * ((size_t)g.nt + 2));
   w->active = (uint8_t *)p;
 }
 
@@ -87,40 +91,157 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->reunit = reunit;
   a->reunit_every = 0;
   a->count_base = 0;
+  a->stream = w.stream_ctr;
+  a->err = w.err;
+  a->n_half = 1;
+  static const int tiles = [] {
+    const char *v = getenv("LGT_STREAM_TILES");
+    const int n = v ? atoi(v) : 0;
+    return n >= 1 && n <= 64 ? n : LGT_STREAM_TILES;
+  }();
+  a->stream_tiles = tiles;
 }
 
-cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
-                              int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
-                              cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every) {
-  sweep_fn fn = (fmt == FMT_F32_18 || fmt == FMT_F32_12) ? pick_sweep_f32(fmt, c.gauge, c.algo, cfg)
-                                                          : pick_sweep_hi(fmt, c.gauge, c.algo, cfg);
+// SMs of the current device, looked up once per device ordinal
+static int device_sms() {
+  static int sms_of[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int &sms = sms_of[dev & 63];
+  if (!sms) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Within a run of half-sweeps every launch after the first, whose predecessor in
+// the stream is then a sweep kernel, carries programmatic stream serialisation
+// (configurations with blocks per site tile; not the persistent ones)
+// (the kernels begin with griddepcontrol.wait): the next half-sweep's blocks are
+// scheduled while the previous one drains.  LGT_SWEEP_PDL=0 in the
+// environment: plain launches only.
+static bool use_pdl() {
+  static const bool on = [] {
+    const char *v = getenv("LGT_SWEEP_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+static cudaError_t launch_fn(sweep_fn fn, dim3 grid, int block, int smem, cudaStream_t st, const SweepArgs &a,
+                             int parity, bool pdl) {
+  if (!pdl || !use_pdl()) {
+    fn<<<grid, block, smem, st>>>(a, parity);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = dim3(block);
+  lc.dynamicSmemBytes = (size_t)smem;
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, fn, a, parity);
+}
+
+// one launch of a sweep kernel (n_half > 1: streaming configuration only)
+static cudaError_t launch_sweep_kernel(sweep_fn fn, int cfg, const Geom &g, SweepArgs &a, int parity, cudaStream_t st,
+                                       bool pdl = false) {
   const int block = lgt_cfg_threads(cfg);
+  if (lgt_cfg_pipe(cfg) || lgt_cfg_stream(cfg)) {
+    // persistent: lgt_cfg_minblocks blocks per SM over the (half-sweep, slice, tile) list
+    const int smem = LGT_PIPE_SMEM_PER_THREAD * block;
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)ceil_div(g.vs_half, block) * g.nt * a.n_half;
+    const long long cap = (long long)device_sms() * lgt_cfg_minblocks(cfg);
+    const int blocks = (int)(tiles < cap ? tiles : cap);
+    if (lgt_cfg_stream(cfg)) {  // counters start at zero in every launch
+      e = cudaMemsetAsync(a.stream, 0, sizeof(unsigned) * ((size_t)g.nt + 2), st);
+      if (e != cudaSuccess) return e;
+    }
+    // (persistent blocks fill the SMs' shared memory, so the successor's blocks
+    // could only be placed as they exit: measured a little slower, left plain)
+    return launch_fn(fn, dim3(blocks), block, smem, st, a, parity & 1, false);
+  }
+  return launch_fn(fn, dim3(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), g.nt), block, 0, st, a, parity & 1, pdl);
+}
+
+static sweep_fn pick_sweep(int fmt, const SweepCfg &c, int cfg) {
+  return (fmt == FMT_F32_18 || fmt == FMT_F32_12) ? pick_sweep_f32(fmt, c.gauge, c.algo, cfg)
+                                                  : pick_sweep_hi(fmt, c.gauge, c.algo, cfg);
+}
+
+static cudaError_t half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                              int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
+                              cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every, bool pdl) {
+  sweep_fn fn = pick_sweep(fmt, c, cfg);
   if (!fn || !lgt_cfg_supported(fmt, cfg)) return cudaErrorInvalidValue;
   SweepArgs a;
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   a.aux = aux;
   a.loop = loop;
   a.reunit_every = reunit_every;
-  if (lgt_cfg_pipe(cfg)) {  // persistent: lgt_cfg_minblocks blocks per SM over the (slice, tile) list
-    const int smem = LGT_PIPE_SMEM_PER_THREAD * block;
-    static int sms_of[64];  // per device ordinal, looked up once
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int &sms = sms_of[dev & 63];
-    if (!sms) {
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (sms <= 0) sms = 1;
+  if (lgt_cfg_stream(cfg) && loop) a.count_base = 0;  // the loop's count is added on the device
+  return launch_sweep_kernel(fn, cfg, g, a, parity, st, pdl);
+}
+
+cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                              int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
+                              cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every) {
+  return half_sweep(fmt, g, links, G, w, c, parity, sweep, reunit, use_mask, cfg, st, aux, loop, reunit_every, false);
+}
+
+cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
+                               int p0, int n_half, unsigned long long sweep0, long long count_base, int reunit_every,
+                               int use_mask, int cfg, cudaStream_t st, const void *aux, const LoopState *loop,
+                               int *launches) {
+  if (launches) *launches = 0;
+  if (n_half <= 0) return cudaSuccess;
+  if (!lgt_cfg_stream(cfg)) {
+    for (int h = 0; h < n_half; h++) {
+      const int s = (p0 + h) >> 1;
+      cudaError_t e;
+      if (loop) {  // sweep number and schedule from the loop state (sweep0 + s: offset in the chunk)
+        e = half_sweep(fmt, g, links, G, w, c, p0 + h, sweep0 + s, 0, use_mask, cfg, st, aux, loop, reunit_every,
+                       h > 0);
+      } else {
+        const int reunit = reunit_every > 0 && ((count_base + s + 1) % reunit_every) == 0;
+        e = half_sweep(fmt, g, links, G, w, c, p0 + h, sweep0 + s, reunit, use_mask, cfg, st, aux, nullptr, 0, h > 0);
+      }
+      if (e != cudaSuccess) return e;
+      if (launches) ++*launches;
     }
-    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    const long long tiles = (long long)ceil_div(g.vs_half, block) * g.nt;
-    const int blocks = (int)(tiles < (long long)sms * lgt_cfg_minblocks(cfg) ? tiles : (long long)sms * lgt_cfg_minblocks(cfg));
-    fn<<<blocks, block, smem, st>>>(a, parity & 1);
-    return cudaGetLastError();
+    return cudaSuccess;
   }
-  dim3 grid(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), g.nt);
-  fn<<<grid, block, 0, st>>>(a, parity & 1);
-  return cudaGetLastError();
+  sweep_fn fn = pick_sweep(fmt, c, cfg);
+  if (!fn || !lgt_cfg_supported(fmt, cfg)) return cudaErrorInvalidValue;
+  // launches of at most LGT_STREAM_MAX_HALF half-sweeps (and 2^30 tiles: the
+  // ticket and slice counters are 32-bit)
+  const long long tiles_half = (long long)ceil_div(g.vs_half, lgt_cfg_threads(cfg)) * g.nt;
+  long long per_launch = (1ll << 30) / (tiles_half > 0 ? tiles_half : 1);
+  if (per_launch > LGT_STREAM_MAX_HALF) per_launch = LGT_STREAM_MAX_HALF;
+  if (per_launch < 1) per_launch = 1;
+  for (int h0 = 0; h0 < n_half; h0 += (int)per_launch) {
+    const int n = (int)((n_half - h0) < per_launch ? (n_half - h0) : per_launch);
+    const int p = (p0 + h0) & 1;
+    const long long s0 = (p0 + h0 - p) / 2;  // sweeps of the run before this launch's first
+    SweepArgs a;
+    fill_sweep_args(&a, g, links, G, w, c, sweep0 + (unsigned long long)s0, 0, use_mask);
+    a.aux = aux;
+    a.loop = loop;
+    a.reunit_every = reunit_every;
+    a.count_base = loop ? 0 : count_base + s0;
+    a.n_half = n;
+    cudaError_t e = launch_sweep_kernel(fn, cfg, g, a, p, st);
+    if (e != cudaSuccess) return e;
+    if (launches) ++*launches;
+  }
+  return cudaSuccess;
 }
 
 template <int FMT>

@@ -74,6 +74,16 @@ __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
   return philox4x32_10(ctr, key);
 }
 
+// Programmatic dependent launch: a sweep kernel may be scheduled while the
+// kernel before it in the stream drains.  Its first act is griddepcontrol.wait,
+// which returns once that kernel has completed and its writes are visible, so
+// nothing of the field, the loop state or the estimate slots is touched before;
+// then it lets its own successor be scheduled.  Both are no-ops in a plain launch.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // A device loop's sweep kernels take the sweep number (SR counter) and the
 // reunitarisation flag from the loop state (see LoopState).
 __device__ __forceinline__ SweepArgs resolve_loop(const SweepArgs &in) {
@@ -365,6 +375,234 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
   cp_async_wait<0>();  // nothing of this thread's in flight at exit
 }
 
+
+// ---------------------------------------------------------------- streaming
+// Several half-sweeps in one persistent launch.  Item n of the launch is
+// (half-sweep h, position k, group bx of up to stream_tiles tiles) with
+// n = (h * nt + k) * items_x + bx;
+// half-sweep h visits slice t = (h + k) mod nt at position k.  A site of
+// slice t touches links stored in slices t and t - 1 only (the temporal
+// backward link), so half-sweep h may update slice t once half-sweep h - 1 has
+// finished slices t - 1, t and t + 1; with the slice order shifted by one per
+// half-sweep, those are the first three positions of half-sweep h - 1 after
+// k, long finished when item (h, k) comes up, and the pipeline streams across
+// half-sweep boundaries.  done[t] counts the finished items of slice t over the
+// launch: it reaches h * items_x only when every item of slice t in half-sweeps
+// before h has finished, because each such item waited for the ones before it.
+// Blocks take items from a ticket counter, in order, and wait only for items
+// of smaller tickets, which running blocks hold; a block waits only while it
+// holds no unfinished item of its own, so the launch cannot deadlock, however
+// many of its blocks are resident.  Every wait is bounded in time: after
+// LGT_STREAM_WAIT_NS the block raises the abort flag and bit 1 of the error
+// word, and every block ends.
+__device__ __forceinline__ unsigned long long lgt_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned lgt_ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Publication: after a block barrier, one thread's release-add makes the whole
+// block's earlier writes visible to a thread whose acquire-load reads the sum
+// (release is cumulative over what the barrier ordered before it); that thread
+// passes them on to its block through the next barrier.
+__device__ __forceinline__ void lgt_red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct StreamItem {
+  int h, t, bx;
+};
+__device__ __forceinline__ StreamItem stream_item(unsigned n, int items_x, int nt) {
+  StreamItem it;
+  const unsigned per_half = (unsigned)items_x * (unsigned)nt;
+  it.h = (int)(n / per_half);
+  const unsigned r = n - (unsigned)it.h * per_half;
+  const int k = (int)(r / (unsigned)items_x);
+  it.bx = (int)(r - (unsigned)k * (unsigned)items_x);
+  it.t = (it.h % nt + k) % nt;
+  return it;
+}
+// whether half-sweep it.h - 1 has finished slices t - 1, t, t + 1 (one look)
+__device__ __forceinline__ bool stream_ready(const unsigned *done, const StreamItem &it, int items_x, int nt) {
+  if (it.h == 0) return true;
+  const unsigned need = (unsigned)it.h * (unsigned)items_x;
+  const int tm = it.t == 0 ? nt - 1 : it.t - 1, tp = it.t == nt - 1 ? 0 : it.t + 1;
+  const unsigned a = lgt_ld_acquire(done + tm), b = lgt_ld_acquire(done + it.t), c = lgt_ld_acquire(done + tp);
+  return a >= need && b >= need && c >= need;
+}
+// bounded wait for stream_ready (thread 0 of a block); false: the launch gives up
+__device__ __forceinline__ bool stream_wait(unsigned *ctr, int *err, const StreamItem &it, int items_x, int nt) {
+  const unsigned long long t0 = lgt_clock_ns();
+  for (unsigned k = 0; k < (1u << 26); k++) {
+    if (stream_ready(ctr + 2, it, items_x, nt)) return true;
+    if (lgt_ld_acquire(ctr + 1)) return false;  // another block gave up
+    if (lgt_clock_ns() - t0 > LGT_STREAM_WAIT_NS) break;
+    __nanosleep(128);
+  }
+  atomicExch(ctr + 1, 1u);
+  atomicOr(err, LGT_ERR_STREAM_WAIT);
+  return false;
+}
+
+template <int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p0, int tiles_x) {
+  extern __shared__ float4 lgt_stage[];  // [2][LGT_PIPE_CHUNKS][blockDim.x]
+  __shared__ unsigned s_next;            // the next item's ticket
+  __shared__ int s_ready, s_go;          // its slices were ready when looked at; the current item may start
+  typedef LinkIO<FMT_F32_12> IO;
+  constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+  const int T = (int)blockDim.x, tid = (int)threadIdx.x, nt = in.g.nt;
+  const int per_item = in.stream_tiles;                    // tiles per item
+  const int items_x = (tiles_x + per_item - 1) / per_item;  // items per slice
+  const unsigned total = (unsigned)items_x * (unsigned)nt * (unsigned)in.n_half;
+  unsigned *ctr = in.stream;
+  const float4 *L = reinterpret_cast<const float4 *>(in.links);
+  const float4 *Gs = reinterpret_cast<const float4 *>(in.G);
+  // sweep numbers and the reunitarisation schedule of the launch's sweeps
+  // (with a device loop, in.sweep is the launch's offset in the chunk)
+  unsigned long long sweep0 = in.sweep;
+  long long count0 = in.count_base;
+  if (in.loop) {
+    sweep0 = in.loop->sweep + in.sweep;
+    count0 = in.loop->count + (long long)in.sweep;
+  }
+  // stage tile `tile` of slice it.t in half-sweep it.h
+  auto issue = [&](const StreamItem &it, int tile, int buf) {
+    const int p = (p0 + it.h) & 1, q = p ^ 1;
+    const int j = tile * T + tid;
+    if (!(in.active && !in.active[it.t]) && j < in.g.vs_half) {
+      const Coords c = coords_in_slice(in.g, p, it.t, j);
+      const int i = it.t * in.g.vs_half + j;
+      float4 *st = lgt_stage + (size_t)buf * LGT_PIPE_CHUNKS * T + tid;
+#pragma unroll
+      for (int mu = MU0; mu < 4; mu++) {
+        const int nb = cb_shift(in.g, c, mu, -1);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          cp_async16(st + (mu * 6 + k) * T, L + (size_t)((p * 4 + mu) * 3 + k) * in.g.vh + i);
+          cp_async16(st + (mu * 6 + 3 + k) * T, L + (size_t)((q * 4 + mu) * 3 + k) * in.g.vh + nb);
+        }
+      }
+      if (Gs) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) cp_async16(st + (24 + k) * T, Gs + (size_t)(p * 3 + k) * in.g.vh + i);
+      }
+    }
+  };
+  // thread 0 looks (without waiting: the item may depend on this block's
+  // current one) whether ticket n's slices are ready, and shares n
+  auto share = [&](unsigned n) {
+    if (tid == 0) {
+      int ready = 0;
+      if (n < total && !lgt_ld_acquire(ctr + 1)) {
+        ready = stream_ready(ctr + 2, stream_item(n, items_x, nt), items_x, nt) ? 1 : 0;
+      }
+      s_next = n;
+      s_ready = ready;
+    }
+    __syncthreads();
+  };
+  share(tid == 0 ? atomicAdd(ctr, 1u) : 0u);
+  unsigned cur = s_next;
+  int staged = s_ready, buf = 0;  // staged: the current tile's loads are issued
+  if (cur < total && staged) {
+    const StreamItem it = stream_item(cur, items_x, nt);
+    issue(it, it.bx * per_item, 0);
+  }
+  cp_async_commit();
+  bool abort = false;
+  while (cur < total && !abort) {
+    const StreamItem it = stream_item(cur, items_x, nt);  // it.bx: the item's index in its slice
+    const int first = it.bx * per_item;
+    const int ntl = tiles_x - first < per_item ? tiles_x - first : per_item;
+    const int p = (p0 + it.h) & 1;
+    const int sw = (p0 + it.h) >> 1;  // sweep of the launch
+    SweepArgs a = in;
+    a.sweep = sweep0 + (unsigned long long)sw;
+    a.reunit = in.reunit_every > 0 ? (int)(((count0 + sw + 1) % in.reunit_every) == 0) : in.reunit;
+    const bool on = !(in.active && !in.active[it.t]);
+    unsigned ticket = 0;
+    if (tid == 0) ticket = atomicAdd(ctr, 1u);  // the next item's ticket, used at the last tile
+    unsigned nxt = 0;
+    int nxt_ready = 0;
+    // one copy of the site update: unrolled, the body would outgrow the instruction cache
+#pragma unroll 1
+    for (int u = 0; u < ntl; u++) {
+      if (!staged) {  // first tile of an item that was not ready: wait, then load it
+        if (tid == 0) s_go = stream_wait(ctr, in.err, it, items_x, nt) ? 1 : 0;
+        __syncthreads();
+        if (!s_go) {  // uniform: every thread read the same flag
+          abort = true;
+          break;
+        }
+        issue(it, first + u, buf);
+        cp_async_commit();
+      }
+      // stage the tile after this one (the item's slices are ready now): the
+      // item's next tile, or the next item's first if its slices are ready
+      if (u + 1 < ntl) {
+        issue(it, first + u + 1, buf ^ 1);
+      } else {
+        share(ticket);
+        nxt = s_next;
+        nxt_ready = s_ready;
+        if (nxt < total && nxt_ready) {
+          const StreamItem in2 = stream_item(nxt, items_x, nt);
+          issue(in2, in2.bx * per_item, buf ^ 1);
+        }
+      }
+      cp_async_commit();   // possibly empty: every tile commits exactly one group here
+      cp_async_wait<1>();  // all but that group: this thread's copies of the current tile have landed
+      if (on) {  // the whole tile belongs to one slice
+        const int tile = first + u;
+        const int j = tile * T + tid;
+        float acc[2] = {0.0f, 0.0f};
+        if (j < in.g.vs_half) {
+          const Coords c = coords_in_slice(in.g, p, it.t, j);
+          const int i = it.t * in.g.vs_half + j;
+          const float4 *st = lgt_stage + (size_t)buf * LGT_PIPE_CHUNKS * T + tid;
+          float uf[4][18], ub[4][18], gx[18];
+          int nb[4];
+#pragma unroll
+          for (int mu = MU0; mu < 4; mu++) {
+            nb[mu] = cb_shift(in.g, c, mu, -1);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+              const float4 f = st[(mu * 6 + k) * T], b = st[(mu * 6 + 3 + k) * T];
+              uf[mu][4 * k] = f.x, uf[mu][4 * k + 1] = f.y, uf[mu][4 * k + 2] = f.z, uf[mu][4 * k + 3] = f.w;
+              ub[mu][4 * k] = b.x, ub[mu][4 * k + 1] = b.y, ub[mu][4 * k + 2] = b.z, ub[mu][4 * k + 3] = b.w;
+            }
+#pragma unroll
+            for (int e = 12; e < 18; e++) uf[mu][e] = ub[mu][e] = 0.0f;
+          }
+          if (Gs) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+              const float4 v = st[(24 + k) * T];
+              gx[4 * k] = v.x, gx[4 * k + 1] = v.y, gx[4 * k + 2] = v.z, gx[4 * k + 3] = v.w;
+            }
+            rebuild_row2(gx);
+          }
+          site_update_f32<FMT_F32_12, GAUGE, ALGO>(a, p, c, i, nb, uf, ub, Gs ? gx : nullptr, acc);
+        }
+        fused_store<float, 1>(a, p, it.t, tile, acc);
+      }
+      buf ^= 1;
+      staged = 1;  // the item's next tile was issued above
+    }
+    if (abort) break;
+    // the item is finished once every thread's stores are: publish it
+    __syncthreads();
+    if (tid == 0) lgt_red_release_add(ctr + 2 + it.t, 1u);
+    cur = nxt;
+    staged = nxt_ready;
+  }
+  cp_async_wait<0>();  // nothing of this thread's in flight at exit
+}
 
 // FP32 link formats, four threads per site: thread m of the site's quad owns
 // direction m (for Coulomb gauge thread 0 owns the temporal links, which the

@@ -1,12 +1,19 @@
 // lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
 // storage), one instantiation per gauge, algorithm and launch configuration
-// (one or four threads per site; pipelined through shared memory).
+// (one or four threads per site; pipelined through shared memory; streaming
+// several half-sweeps per launch).
 #include "lgt_sweep.cuh"
 
 namespace lgt {
 
 template <int FMT, int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f32(SweepArgs in, int p) {
+  pdl_enter();
+  if constexpr (lgt_cfg_stream(CFG)) {  // sweep numbers per item, from the loop state or the arguments
+    if constexpr (FMT == FMT_F32_12)
+      sweep_body_f32_stream<GAUGE, ALGO>(in, p, (in.g.vs_half + (int)blockDim.x - 1) / (int)blockDim.x);
+    return;
+  }
   const SweepArgs a = resolve_loop(in);
   if constexpr (lgt_cfg_quad(CFG)) {
     sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
@@ -55,6 +62,7 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 7: return pick_cfg<7>(fmt, gauge, algo);
     case 8: return pick_cfg<8>(fmt, gauge, algo);
     case 9: return pick_cfg<9>(fmt, gauge, algo);
+    case 10: return pick_cfg<10>(fmt, gauge, algo);
   }
   return nullptr;
 }

@@ -7,18 +7,21 @@ namespace lgt {
 
 template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs in, int p) {
+  pdl_enter();
   const SweepArgs a = resolve_loop(in);
   sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_pair(SweepArgs in, int p) {
+  pdl_enter();
   const SweepArgs a = resolve_loop(in);
   sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_anchor(SweepArgs in, int p) {
+  pdl_enter();
   const SweepArgs a = resolve_loop(in);
   sweep_body_anchor<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
 }

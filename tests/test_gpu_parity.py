@@ -550,7 +550,7 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
 @pytest.mark.parametrize("algo", list(ALGOS))
 def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     """Every launch configuration (one or four threads per site, every block size,
-    pipelined through shared memory, lean) forms K(x) in the same order and groups the
+    pipelined through shared memory, lean, streaming) forms K(x) in the same order and groups the
     fused estimate by the same 8 sites; what remains is where the compiler fuses
     multiply-adds in each kernel (FP32 rounding, which a nearly degenerate SU(2)
     projection can amplify along a trajectory).  So the test compares what the
@@ -560,7 +560,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
-    ncfg = 10
+    ncfg = 11
     ref = None
     for k in range(ncfg):
         p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, **kw)
@@ -583,11 +583,44 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
             cfgs = lgt.lgt_get_stats(ctx).launch_config
         finally:
             lgt.lgt_destroy(ctx)
-        supported = k != 7 or bulk == "fp32_12"  # the pipelined layout stages 12-real links only
+        supported = k not in (7, 10) or bulk == "fp32_12"  # the staged layouts hold 12-real links only
         assert st == lgt.LGT_OK and cfgs[0] == (k if supported else 0) and res.theta < 1e-12
         if ref is None:
             ref = res.F
         assert abs(res.F - ref) < 1e-10, f"launch configuration {k}: F {res.F} vs {ref}"
+
+
+@pytest.mark.parametrize("gauge", list(GAUGES))
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_streaming_sweeps_match_the_pipelined_kernel(lgt, gauge, algo):
+    """The streaming configuration runs up to 64 half-sweeps per launch and starts
+    a slice of half-sweep h as soon as half-sweep h - 1 has finished it and its
+    two neighbours.  Its site update is the pipelined configuration's, so any
+    read of a link before its writer finished would show as a difference:
+    40 sweeps (80 half-sweeps, two launches) from a rough field, with the SR
+    counter and the reunitarisation schedule (every 3 sweeps) taken per item,
+    give the pipelined kernel's links bit for bit, and stay within FP32
+    rounding of the one-thread kernel.  12 slices of a ragged 6x10x14 volume
+    (4 tiles per slice, the last partial); a single odd half-sweep first."""
+    dims = (12, 6, 10, 14)
+    U = synth.field(dims, 0.5, 23)
+    kw = dict(dims=dims, bulk=lgt.LGT_FP32_12, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=9,
+              reunit_every=3)
+    out = {}
+    for k in (0, 7, 10):
+        ctx = lgt.lgt_create(lgt.lgt_params_default(launch_config=k + 1, **kw), U)
+        try:
+            lgt.lgt_half_sweep(ctx, 1)
+            lgt.lgt_sweep(ctx, 40)
+            out[k] = lgt.lgt_get_working_links(ctx, dims)
+            st = lgt.lgt_get_stats(ctx)
+            sb, _, _ = lgt.lgt_get_progress(ctx)
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st.launch_config[0] == k and sb == 41 and st.sweep_launches[0] == 81
+    assert np.array_equal(out[10], out[7])
+    assert np.abs(out[10] - out[0]).max() < 1e-4
+    assert max(unitarity_error(out[10])) < 1e-5
 
 
 @pytest.mark.parametrize("bulk", ["fp64", "fp32_12"])
