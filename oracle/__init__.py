@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liblgt_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LANDAU, COULOMB = 0, 1
+LANDAU, COULOMB, MAG = 0, 1, 2
 OR, SR, SA = 0, 1, 2
 
 _dp = ctypes.c_void_p
@@ -80,6 +80,8 @@ def _load():
             L.orc_su2_heatbath.restype = None
             L.orc_sa_beta.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
             L.orc_sa_beta.restype = ctypes.c_double
+            L.orc_mag_subgroup.argtypes = [_dp, ctypes.c_int, _dp, _dp]
+            L.orc_mag_subgroup.restype = None
             L.orc_set_threads.restype = None
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -246,3 +248,12 @@ def su2_heatbath(q, beta, seed=0, sweep=0, site=0, subgroup=0):
 def sa_beta(beta0, beta1, n, i):
     """beta of annealing sweep i of n (geometric from beta0 to beta1)."""
     return _load().orc_sa_beta(float(beta0), float(beta1), int(n), int(i))
+
+
+def mag_subgroup(links8: np.ndarray, s: int):
+    """Maximally Abelian gauge, subgroup s of one site update on the site's 8 links
+    (4 forward then 4 backward, complex 3x3): (v, r), r the maximising element."""
+    L8 = np.ascontiguousarray(links8, dtype=np.complex128).reshape(8, 3, 3)
+    v, r = np.zeros(3), np.zeros(4)
+    _load().orc_mag_subgroup(L8.ctypes.data, int(s), v.ctypes.data, r.ctypes.data)
+    return v, r

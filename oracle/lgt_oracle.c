@@ -39,6 +39,9 @@
  *     V -> V_s); parity is the 4-D parity, and by default g(x) also acts on
  *     the temporal links U_0(x) and U_0(x-0) so the result stays a gauge
  *     transform of the input.
+ *   - Maximally Abelian gauge (named in the abstract beside Landau and
+ *     Coulomb gauge; the text gives neither its functional nor its update):
+ *     see the section "maximally Abelian gauge" below.
  *
  * Precision: FP64 throughout, no fused multiply-add contraction
  * (-ffp-contract=off), sums in fixed order.  OpenMP runs the sites of one
@@ -60,7 +63,7 @@
 
 #define NC 3
 
-enum { ORC_LANDAU = 0, ORC_COULOMB = 1 };
+enum { ORC_LANDAU = 0, ORC_COULOMB = 1, ORC_MAG = 2 };
 enum { ORC_OR = 0, ORC_SR = 1, ORC_SA = 2 };
 
 /* ------------------------------------------------------------------ complex */
@@ -313,6 +316,103 @@ static su3 su2_embed(const double r[4], int i, int j) {
 
 static const int SUBGROUP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 
+/* ------------------------------------------- maximally Abelian gauge */
+/* Reading (the standard functional, which the text does not write down):
+ *   F_MAG[U] = 1/(N_c N_d V) sum_{x,mu} sum_a |U_mu(x)_aa|^2,  maximised (N_d = 4).
+ * Under g(x) = 1 + i eps T at one site the links U_mu(x) -> g U_mu(x) and
+ * U_mu(x-mu) -> U_mu(x-mu) g^dagger change F_MAG by 2 eps Re tr[i T X(x)]
+ * (times the normalisation), with
+ *   X(x) = sum_mu ( U_mu(x) D_mu(x)^dagger - D_mu(x-mu)^dagger U_mu(x-mu) ),
+ * D = the diagonal part of U.  So the gauge is reached where the traceless
+ * part Delta_MAG(x) of (X - X^dagger)/(2i) vanishes, and the precision is
+ *   theta_MAG = 1/(N_c V) sum_x tr[Delta_MAG(x) Delta_MAG(x)^dagger],
+ * the same construction as the Landau-gauge theta with K(x) replaced by X(x).
+ *
+ * Local update, per SU(2) subgroup (i, j) as in Sec. 3: with R the subgroup
+ * element, only the diagonal entries i, j of the site's 8 links change:
+ * (R U)_ii, (R U)_jj for the forward links, (U R^dagger)_ii, (U R^dagger)_jj for
+ * the backward ones.  Writing n.sigma = R^dagger sigma_3 R (on the block),
+ *   |(R U)_ii|^2 + |(R U)_jj|^2 = const + n.(s(U_ii, U_ji) - s(U_ij, U_jj)) / 2,
+ *   |(W R^dagger)_ii|^2 + |(W R^dagger)_jj|^2
+ *                        = const + n.(s(W_ii*, W_ij*) - s(W_ji*, W_jj*)) / 2,
+ * s(a, b) = (2 Re(a* b), 2 Im(a* b), |a|^2 - |b|^2): the site functional is
+ * linear in the unit vector n, maximal at n = v/|v| with v the sum of those
+ * vectors over the 8 links.  Left factors exp(i phi sigma_3) leave every
+ * |diagonal entry| unchanged, so the maximisers form a circle; take the one
+ * nearest the identity, the rotation of n onto e_3 about n x e_3:
+ *   r = (|v| + v_3, -v_2, v_1, 0) / norm     (r = (0, 1, 0, 0) if v = -|v| e_3).
+ * The subgroup steps run in the order (0,1), (0,2), (1,2) on the links as
+ * updated by the steps before; overrelaxation and stochastic relaxation act
+ * on r exactly as for Landau gauge (Sec. 3.1, 3.2). */
+static void mag_s(cplx a, cplx b, double sign, double v[3]) {
+  const cplx z = c_mul(c_conj(a), b);
+  v[0] += sign * 2.0 * z.re;
+  v[1] += sign * 2.0 * z.im;
+  v[2] += sign * (a.re * a.re + a.im * a.im - b.re * b.re - b.im * b.im);
+}
+
+/* the vector v of subgroup (i, j) for the site's current links */
+static void mag_vector(const su3 fwd[4], const su3 bwd[4], int i, int j, double v[3]) {
+  v[0] = v[1] = v[2] = 0.0;
+  for (int mu = 0; mu < 4; mu++) {
+    mag_s(fwd[mu].e[i][i], fwd[mu].e[j][i], 1.0, v);
+    mag_s(fwd[mu].e[i][j], fwd[mu].e[j][j], -1.0, v);
+    mag_s(c_conj(bwd[mu].e[i][i]), c_conj(bwd[mu].e[i][j]), 1.0, v);
+    mag_s(c_conj(bwd[mu].e[j][i]), c_conj(bwd[mu].e[j][j]), -1.0, v);
+  }
+}
+
+/* the subgroup element nearest the identity that maximises n.v */
+static void mag_maximum(const double v[3], double r[4]) {
+  const double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  r[0] = 1.0; r[1] = r[2] = r[3] = 0.0;
+  if (!(nv > 0.0)) return;
+  const double a = nv + v[2];
+  const double norm = sqrt(a * a + v[0] * v[0] + v[1] * v[1]);
+  if (!(norm > 0.0)) {
+    r[0] = 0.0; r[1] = 1.0;
+    return;
+  }
+  r[0] = a / norm;
+  r[1] = -v[1] / norm;
+  r[2] = v[0] / norm;
+  r[3] = 0.0;
+}
+
+/* sum over the four directions of sum_a |U_mu(x)_aa|^2 */
+static double site_mag_functional(const double *links, int64_t site) {
+  double s = 0.0;
+  for (int mu = 0; mu < 4; mu++) {
+    su3 u = load_link(links, site, mu);
+    for (int a = 0; a < NC; a++) s += u.e[a][a].re * u.e[a][a].re + u.e[a][a].im * u.e[a][a].im;
+  }
+  return s;
+}
+
+static su3 m_diag(const su3 *u) {
+  su3 d;
+  memset(&d, 0, sizeof d);
+  for (int a = 0; a < NC; a++) d.e[a][a] = u->e[a][a];
+  return d;
+}
+
+/* X(x) of the current links */
+static su3 mag_X(const lattice *l, const double *links, int64_t site) {
+  su3 X;
+  memset(&X, 0, sizeof X);
+  for (int mu = 0; mu < 4; mu++) {
+    su3 fwd = load_link(links, site, mu);
+    su3 bwd = load_link(links, site_shift(l, site, mu, -1), mu);
+    su3 df = m_diag(&fwd), db = m_diag(&bwd);
+    su3 dfd = m_dagger(&df), dbd = m_dagger(&db);
+    su3 t1 = m_mul(&fwd, &dfd);
+    su3 t2 = m_mul(&dbd, &bwd);
+    X = m_add(&X, &t1);
+    X = m_sub(&X, &t2);
+  }
+  return X;
+}
+
 /* ------------------------------------ simulated annealing: SU(2) heat bath */
 /* Simulated annealing (named by the paper as a preconditioner, Sec. 1; its
  * details are in a reference this text lacks) is read as sweeps whose SU(2)
@@ -442,6 +542,32 @@ static su3 local_gauge_update(const su3 *K, const update_rule *rule, const uint3
   return g;
 }
 
+/* Maximally Abelian gauge: the subgroup steps on the site's own links (the
+ * site functional is quadratic in g, so K(x) does not suffice).  fwd/bwd are
+ * the 4 forward and 4 backward links; they are updated in place; returns g. */
+static su3 mag_local_update(su3 fwd[4], su3 bwd[4], const update_rule *rule, const uint32_t draws[3]) {
+  su3 g = m_identity();
+  for (int s = 0; s < 3; s++) {
+    const int i = SUBGROUP[s][0], j = SUBGROUP[s][1];
+    double v[3], r[4];
+    mag_vector(fwd, bwd, i, j, v);
+    mag_maximum(v, r);
+    if (rule->algo == ORC_OR) {
+      su2_overrelax(r, rule->omega);
+    } else if ((uint64_t)draws[s] < rule->sr_thr) {
+      su2_square(r);
+    }
+    su3 R = su2_embed(r, i, j);
+    su3 Rd = m_dagger(&R);
+    for (int mu = 0; mu < 4; mu++) {
+      fwd[mu] = m_mul(&R, &fwd[mu]);
+      bwd[mu] = m_mul(&bwd[mu], &Rd);
+    }
+    g = m_mul(&R, &g);
+  }
+  return g;
+}
+
 /* Section 2 transformation, in place at one site:
  *   U_mu(x) <- g U_mu(x),  U_mu(x-mu) <- U_mu(x-mu) g^dagger
  * for every direction in the functional; Coulomb gauge optionally also the
@@ -468,15 +594,28 @@ typedef struct {
   int transform_temporal;
 } sweep_cfg;
 
-static void update_site(const lattice *l, double *links, int64_t site, const sweep_cfg *cfg, uint64_t sweep) {
-  su3 K = gather_K(l, links, site, cfg->gauge);
+/* g of one site update on the current links (which it does not touch) */
+static su3 site_g(const lattice *l, const double *links, int64_t site, const sweep_cfg *cfg, uint64_t sweep) {
   uint32_t u[3] = {0, 0, 0};
   if (cfg->rule.algo == ORC_SR) sr_draws(cfg->seed, sweep, site, u);
   update_rule rule = cfg->rule;
   rule.seed = cfg->seed;
   rule.sweep = sweep;
   rule.site = site;
-  su3 g = local_gauge_update(&K, &rule, u, NULL, NULL);
+  if (cfg->gauge == ORC_MAG) {
+    su3 fwd[4], bwd[4];
+    for (int mu = 0; mu < 4; mu++) {
+      fwd[mu] = load_link(links, site, mu);
+      bwd[mu] = load_link(links, site_shift(l, site, mu, -1), mu);
+    }
+    return mag_local_update(fwd, bwd, &rule, u);
+  }
+  su3 K = gather_K(l, links, site, cfg->gauge);
+  return local_gauge_update(&K, &rule, u, NULL, NULL);
+}
+
+static void update_site(const lattice *l, double *links, int64_t site, const sweep_cfg *cfg, uint64_t sweep) {
+  su3 g = site_g(l, links, site, cfg, sweep);
   apply_gauge_update(l, links, site, &g, cfg->gauge, cfg->transform_temporal);
 }
 
@@ -600,6 +739,7 @@ static int check_dims(const int32_t dims[4]) {
 
 /* Exact measurement, fixed summation order.
  * Landau: F (Section 2 functional), theta (Section 2 precision), plaquette.
+ * Maximally Abelian gauge: F_MAG and theta_MAG (see its section), plaquette.
  * Coulomb: F_t and theta_t per timeslice (spatial directions, N_d = 3,
  * V -> V_s); F = mean_t F_t, theta = max_t theta_t.  F_t / theta_t may be NULL. */
 int orc_measure(const int32_t dims[4], const double *links, int gauge, double *F, double *theta, double *plaq,
@@ -615,8 +755,18 @@ int orc_measure(const int32_t dims[4], const double *links, int gauge, double *F
   }
 #pragma omp parallel for schedule(static)
   for (int64_t x = 0; x < l.vol; x++) {
-    sf[x] = site_retrace(links, x, gauge);
-    st[x] = violation_norm(&l, links, x, gauge);
+    if (gauge == ORC_MAG) {
+      sf[x] = site_mag_functional(links, x);
+      su3 X = mag_X(&l, links, x);
+      su3 d = gauge_field_A(&X); /* traceless part of (X - X^dagger)/(2i) */
+      double v = 0.0;
+      for (int r = 0; r < NC; r++)
+        for (int c = 0; c < NC; c++) v += d.e[r][c].re * d.e[r][c].re + d.e[r][c].im * d.e[r][c].im;
+      st[x] = v;
+    } else {
+      sf[x] = site_retrace(links, x, gauge);
+      st[x] = violation_norm(&l, links, x, gauge);
+    }
     sp[x] = site_plaquettes(&l, links, x);
   }
   const int nd = gauge == ORC_COULOMB ? 3 : 4;
@@ -700,10 +850,7 @@ int orc_site_new_links(const int32_t dims[4], const double *links, int64_t site,
   const lattice l = make_lattice(dims);
   if (site < 0 || site >= l.vol) return -1;
   const sweep_cfg cfg = make_cfg(gauge, algo, omega, p, seed, transform_temporal);
-  su3 K = gather_K(&l, links, site, gauge);
-  uint32_t u[3] = {0, 0, 0};
-  if (algo == ORC_SR) sr_draws(seed, sweep, site, u);
-  su3 g = local_gauge_update(&K, &cfg.rule, u, NULL, NULL);
+  su3 g = site_g(&l, links, site, &cfg, sweep);
   su3 gd = m_dagger(&g);
   const int mu0 = (gauge == ORC_COULOMB && !transform_temporal) ? 1 : 0;
   for (int mu = 0; mu < 4; mu++) {
@@ -791,7 +938,7 @@ void orc_sr_draws(uint64_t seed, uint64_t sweep, int64_t site, uint32_t *out) { 
  * sweep0 .. sweep0+n-1, beta from the geometric schedule sa_beta. */
 int orc_sa_sweeps(const int32_t dims[4], double *links, int gauge, double beta0, double beta1, int n, uint64_t seed,
                   uint64_t sweep0, int transform_temporal) {
-  if (check_dims(dims) || n < 0 || !(beta0 > 0.0) || !(beta1 > 0.0)) return -1;
+  if (check_dims(dims) || n < 0 || !(beta0 > 0.0) || !(beta1 > 0.0) || gauge == ORC_MAG) return -1;
   const lattice l = make_lattice(dims);
   for (int i = 0; i < n; i++) {
     sweep_cfg cfg = make_cfg(gauge, ORC_SA, 1.0, 0.0, seed, transform_temporal);
@@ -868,4 +1015,17 @@ int orc_fix(const int32_t dims[4], double *links, int gauge, int algo, double om
   free(ft);
   free(tt);
   return rc;
+}
+
+/* Maximally Abelian gauge, one subgroup step on a site's links given
+ * directly: links8 = 4 forward then 4 backward links (18 doubles each);
+ * returns the vector v and the maximising element r (before overrelaxation). */
+void orc_mag_subgroup(const double *links8, int s, double *v_out, double *r_out) {
+  su3 fwd[4], bwd[4];
+  for (int mu = 0; mu < 4; mu++) {
+    to_su3(links8 + 18 * mu, &fwd[mu]);
+    to_su3(links8 + 18 * (4 + mu), &bwd[mu]);
+  }
+  mag_vector(fwd, bwd, SUBGROUP[s][0], SUBGROUP[s][1], v_out);
+  mag_maximum(v_out, r_out);
 }

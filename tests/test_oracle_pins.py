@@ -594,3 +594,169 @@ def test_annealing_then_relaxation_converges():
     O.sa_sweeps(U, 30, 1.0, 100.0, seed=7)
     r = O.fix(U, omega=1.7, tol=1e-14, max_sweeps=3000)
     assert r["converged"] and O.measure(U)["theta"] < 1e-14
+
+
+# ------------------------------------------------- maximally Abelian gauge
+def _diag_field(dims, rng):
+    """Abelian field: every link diagonal, exp(i phi_a) with sum phi_a = 0."""
+    phi = rng.uniform(-np.pi, np.pi, size=tuple(dims) + (4, 2))
+    U = np.zeros(tuple(dims) + (4, 3, 3), np.complex128)
+    U[..., 0, 0] = np.exp(1j * phi[..., 0])
+    U[..., 1, 1] = np.exp(1j * phi[..., 1])
+    U[..., 2, 2] = np.exp(-1j * (phi[..., 0] + phi[..., 1]))
+    return U
+
+
+def _mag_site_functional(R, fwd, bwd):
+    """sum of |diagonal|^2 of the site's links after g = R at the site (numpy)"""
+    s = 0.0
+    for U in fwd:
+        s += np.sum(np.abs(np.diagonal(R @ U)) ** 2)
+    for W in bwd:
+        s += np.sum(np.abs(np.diagonal(W @ dag(R))) ** 2)
+    return s
+
+
+def test_mag_functional_closed_forms():
+    """F_MAG = 1/(N_c N_d V) sum |U_aa|^2: 1 and theta_MAG = 0 on an Abelian (diagonal)
+    field, whatever its phases; on Haar-random links E|U_aa|^2 = 1/3 (|U_aa|^2 of a
+    Haar SU(3) matrix is Beta(1, 2)), so F_MAG = 1/3 within 5 standard errors."""
+    rng = np.random.default_rng(31)
+    dims = (4, 4, 2, 4)
+    m = O.measure(_diag_field(dims, rng), O.MAG)
+    assert abs(m["F"] - 1) < 1e-15 and m["theta"] < 1e-30
+    z = rng.normal(size=tuple(dims) + (4, 3, 3)) + 1j * rng.normal(size=tuple(dims) + (4, 3, 3))
+    q, r = np.linalg.qr(z)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    q = q * (d / np.abs(d))[..., None, :]
+    q = q / (np.linalg.det(q) ** (1 / 3))[..., None, None]
+    m = O.measure(np.ascontiguousarray(q), O.MAG)
+    n = q[..., 0, 0].size * 3
+    assert abs(m["F"] - 1 / 3) < 5 * np.sqrt(1 / 18 / n)
+    # the plaquette is the gauge-invariant one, unchanged by the choice of functional
+    assert abs(m["plaq"] - O.measure(np.ascontiguousarray(q))["plaq"]) < 1e-15
+
+
+def test_mag_theta_is_the_gradient_of_F():
+    """theta_MAG = 0 iff F_MAG is stationary under gauge transformations, and
+    quantitatively theta_MAG is the squared gauge gradient of F_MAG: the functional
+    is quadratic in the links, so under g = exp(i e lambda_a/2) at x,
+    dF/de_a = -2 tr(T_a Delta_MAG(x))/(N_c N_d V), twice the Landau-type expression
+    that _theta_from_gradient inverts."""
+    U = synth.field((2, 4, 2, 4), 0.6, 35)
+    m = O.measure(U, O.MAG)
+    th = _theta_from_gradient(U, O.MAG).sum() / U.shape[0] / 4
+    assert m["theta"] > 1e-3
+    assert abs(th - m["theta"]) < 1e-7 * m["theta"]
+
+
+def test_mag_subgroup_step_is_the_maximum():
+    """One subgroup step: the element r maximises the site's MAG functional over the
+    subgroup (brute force over random and gridded SU(2) elements), is stationary
+    (no generator increases it to first or second order), the maximum is
+    const + |v|/2, left factors exp(i phi sigma_3) keep the value (a circle of
+    maximisers), and r is the one of that circle nearest the identity (r3 = 0,
+    r0 >= 0)."""
+    rng = np.random.default_rng(36)
+    grid = su2_grid(2000, rng)[::9]
+    for trial in range(4):
+        links = np.stack([random_su3(rng) for _ in range(8)])
+        fwd, bwd = links[:4], links[4:]
+        for s, (i, j) in enumerate([(0, 1), (0, 2), (1, 2)]):
+            v, r = O.mag_subgroup(links, s)
+            def emb(q):
+                R = np.eye(3, dtype=np.complex128)
+                R[np.ix_([i, j], [i, j])] = su2_quaternion_matrix(q)
+                return R
+            f_r = _mag_site_functional(emb(r), fwd, bwd)
+            f_1 = _mag_site_functional(np.eye(3), fwd, bwd)
+            best = max(_mag_site_functional(emb(q), fwd, bwd) for q in grid)
+            assert f_r >= best - 1e-12
+            assert abs(f_r - (f_1 - v[2] / 2 + np.linalg.norm(v) / 2)) < 1e-12
+            for k in range(3):
+                for e in (1e-3, -1e-3):
+                    gen = np.zeros(4)
+                    gen[0], gen[k + 1] = np.cos(e), np.sin(e)
+                    R2 = emb(gen) @ emb(r)
+                    assert _mag_site_functional(R2, fwd, bwd) <= f_r + 1e-12
+            for phi in (0.3, 1.1, 2.5):
+                D = emb(np.array([np.cos(phi), 0, 0, np.sin(phi)]))
+                assert abs(_mag_site_functional(D @ emb(r), fwd, bwd) - f_r) < 1e-12
+            assert abs(r[3]) < 1e-15 and r[0] >= 0 and abs(np.linalg.norm(r) - 1) < 1e-15
+
+
+def _site_links(U, site):
+    """the 4 forward and 4 backward links of a site (numpy copies)"""
+    dims = U.shape[:4]
+    t, x3, x2, x1 = coords_of(site, dims)
+    fwd, bwd = [], []
+    for mu in range(4):
+        c = {0: t, 1: x1, 2: x2, 3: x3}
+        fwd.append(U[t, x3, x2, x1, mu].copy())
+        c[mu] = (c[mu] - 1) % dims[{0: 0, 1: 3, 2: 2, 3: 1}[mu]]
+        bwd.append(U[c[0], c[3], c[2], c[1], mu].copy())
+    return np.array(fwd), np.array(bwd)
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.7])
+def test_mag_site_update_composes_the_subgroup_steps(omega):
+    """A site update is the three subgroup steps (0,1), (0,2), (1,2) in turn, each
+    taken on the links as the steps before left them (forward links R U, backward
+    links U R^dagger, applied here in numpy), each element overrelaxed to first
+    order: the links the oracle's site update writes are those."""
+    U = synth.field((4, 4, 2, 4), 0.6, 39)
+    for site in (0, 5, 37, 90, 127):
+        fwd, bwd = _site_links(U, site)
+        for s, (i, j) in enumerate([(0, 1), (0, 2), (1, 2)]):
+            _, r = O.mag_subgroup(np.concatenate([fwd, bwd]), s)
+            q = np.array([1 - omega + omega * r[0], omega * r[1], omega * r[2], omega * r[3]])
+            q /= np.linalg.norm(q)
+            R = np.eye(3, dtype=np.complex128)
+            R[np.ix_([i, j], [i, j])] = su2_quaternion_matrix(q)
+            fwd = R @ fwd
+            bwd = bwd @ dag(R)
+        nf, nb = O.site_new_links(U, site, gauge=O.MAG, omega=omega)
+        assert np.abs(nf - fwd).max() < 1e-13 and np.abs(nb - bwd).max() < 1e-13
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.7])
+def test_mag_sweeps_raise_F_and_keep_the_field(omega):
+    """Relaxation (omega = 1) never lowers F_MAG: every subgroup step maximises the
+    site functional; overrelaxed sweeps raise it overall.  Plaquettes and unitarity
+    are kept (each update is a gauge transformation)."""
+    U = synth.field((4, 4, 2, 4), 0.5, 37)
+    P0 = plaquettes(U)
+    F = [O.measure(U, O.MAG)["F"]]
+    for s in range(12):
+        O.half_sweep(U, 0, gauge=O.MAG, omega=omega)
+        F.append(O.measure(U, O.MAG)["F"])
+        O.half_sweep(U, 1, gauge=O.MAG, omega=omega)
+        F.append(O.measure(U, O.MAG)["F"])
+    if omega == 1.0:
+        assert all(b >= a - 1e-14 for a, b in zip(F, F[1:]))
+    assert F[-1] > F[0] + 0.05
+    assert np.abs(plaquettes(U) - P0).max() < 1e-12
+    assert max(unitarity_error(U)) < 1e-12
+
+
+def test_mag_recovers_a_transformed_abelian_field():
+    """A random gauge transform of an Abelian field has F_MAG < 1; MAG fixing climbs back
+    to the global maximum F_MAG = 1 (theta_MAG -> 0), a case whose answer the
+    functional fixes without reference to the update."""
+    rng = np.random.default_rng(38)
+    dims = (4, 4, 4, 4)
+    A = _diag_field(dims, rng)
+    small = np.stack([expm_herm(0.35 * np.einsum("a,aij->ij", rng.normal(size=8), GELL_MANN))
+                      for _ in range(int(np.prod(dims)))]).reshape(tuple(dims) + (3, 3))
+    U = np.ascontiguousarray(transform_field(A, small))
+    assert O.measure(U, O.MAG)["F"] < 0.9
+    r = O.fix(U, gauge=O.MAG, omega=1.7, tol=1e-24, max_sweeps=3000, check_every=10)
+    m = O.measure(U, O.MAG)
+    assert r["converged"] and m["theta"] < 1e-24 and abs(m["F"] - 1) < 1e-13
+    assert np.abs(plaquettes(U) - plaquettes(A)).max() < 1e-12
+
+
+def test_mag_annealing_is_rejected():
+    U = synth.field((2, 2, 2, 2), 0.3, 1)
+    with pytest.raises(Exception):
+        O.sa_sweeps(U, 1, 1.0, 2.0, gauge=O.MAG)
