@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--workload", default="landau32", choices=["landau32", "coulomb", "landau64", "serve"],
+    ap.add_argument("--workload", default="landau32", choices=["landau32", "coulomb", "landau64", "serve", "mag"],
                     help="landau32 (default; the headline line), or one of the other workloads, each "
                          "printing its own line")
     ap.add_argument("--jobs", type=int, default=256, help="serve: number of jobs in the stream")
@@ -547,6 +547,58 @@ def run_landau64(args):
                       "runs": out, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}), flush=True)
 
 
+def run_mag(args):
+    """Maximally Abelian gauge.  The bulk sweep rate on the 32^4 field of the headline
+    workload (FP32-12 links, OR omega 1.7; 20 sweeps untimed, then 200 sweeps timed by
+    the sweep kernels' CUDA events; algorithmic bytes per site as the Landau bulk
+    kernel: the 8 links and G read and written once, 864 B) and the FP64 sweep rate
+    of the same field; then a 16^4 field (eps 0.5, seed 3) fixed to theta_MAG < 1e-12
+    through the ladder, and an 8^4 gauge-transformed Abelian field fixed back to
+    F_MAG = 1."""
+    import torch
+    from paper_1305_3440_gb300 import lgt, synth
+    stream = torch.cuda.Stream()
+    peaks, src = measured_peaks()
+    out = {}
+    dims = (32, 32, 32, 32)
+    vol = int(np.prod(dims))
+    dev = torch.from_numpy(synth.field(dims, 0.5, 2)).cuda()
+    for name, bulk, bytes_per_site in [("bulk_fp32_12", lgt.LGT_FP32_12, algorithmic_bytes_per_site("fp32_12")),
+                                       ("fp64", lgt.LGT_FP64, 2304)]:
+        p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_MAG, bulk=bulk, omega=1.7)
+        ctx = lgt.lgt_create(p, dev, stream=stream)
+        n = 200 if bulk != lgt.LGT_FP64 else 20
+        kind = 0 if bulk != lgt.LGT_FP64 else 1
+        lgt.lgt_sweep(ctx, 20)
+        s0 = lgt.lgt_get_stats(ctx)
+        lgt.lgt_sweep(ctx, n)
+        s1 = lgt.lgt_get_stats(ctx)
+        F, theta, _ = lgt.lgt_measure(ctx)
+        lgt.lgt_destroy(ctx)
+        avg = (s1.sweep_ms[kind] - s0.sweep_ms[kind]) / 1e3 / (s1.sweep_launches[kind] - s0.sweep_launches[kind])
+        gbs = bytes_per_site * (vol // 2) / avg / 1e9
+        out[name] = {"sweeps": n, "avg_half_sweep_us": avg * 1e6, "site_updates_per_s": (vol // 2) / avg,
+                     "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peaks["hbm_gbs"],
+                     "bytes_per_site_update": bytes_per_site, "launch_config": list(s1.launch_config),
+                     "F_after": F, "theta_after": theta}
+    del dev
+    dims = (16, 16, 16, 16)
+    dev = torch.from_numpy(synth.field(dims, 0.5, 3)).cuda()
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_MAG, bulk=lgt.LGT_FP32_12, omega=1.7, theta_tol=1e-12,
+                               max_sweeps=30000)
+    ctx = lgt.lgt_create(p, dev, stream=stream)
+    t, st, res, stats = _timed_fix(lgt, ctx, dev, stream)
+    lgt.lgt_destroy(ctx)
+    out["fix_16x4"] = {"status": st, "seconds": t, "sweeps_bulk": res.sweeps_bulk, "sweeps_polish": res.sweeps_fp64,
+                       "F": res.F, "theta": res.theta,
+                       "site_updates_per_s": (res.sweeps_bulk + res.sweeps_fp64) * int(np.prod(dims)) / t}
+    print(json.dumps({"workload": "mag", "metric": "site updates/s (maximally Abelian gauge sweeps, 32^4)",
+                      "value": out["bulk_fp32_12"]["site_updates_per_s"], "unit": "site updates/s",
+                      "config": {"workload": "SU(3) maximally Abelian gauge: 32^4 eps 0.5 seed 2 sweep rates; "
+                                             "16^4 eps 0.5 seed 3 fixed to theta_MAG < 1e-12"},
+                      "runs": out, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}), flush=True)
+
+
 def serve_specs(n_jobs: int, seed: int = 4):
     """The served stream: dims uniform over six lattices, Landau/Coulomb 50/50,
     tol 1e-12/1e-14, eps ~ U[0.3, 0.7], job seed 1000 + j."""
@@ -649,6 +701,8 @@ def main():
         run_landau64(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "mag":
+        run_mag(args)
     else:
         run_ours(args)
 

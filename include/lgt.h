@@ -73,7 +73,20 @@ typedef enum {
   LGT_ENOTFOUND = 9   /* unknown job id */
 } lgt_status;
 
-typedef enum { LGT_LANDAU = 0, LGT_COULOMB = 1 } lgt_gauge;
+/* LGT_MAG: the maximally Abelian gauge, which the paper's abstract names
+ * beside Landau and Coulomb gauge without giving its functional.  Reading:
+ * F_MAG = 1/(N_c 4 V) sum_{x,mu} sum_a |U_mu(x)_aa|^2, maximised; theta_MAG =
+ * 1/(N_c V) sum_x tr[Delta Delta^dagger], Delta the traceless part of
+ * (X - X^dagger)/(2i), X(x) = sum_mu (U_mu(x) D_mu(x)^dagger -
+ * D_mu(x-mu)^dagger U_mu(x-mu)), D = diagonal part (F_MAG is stationary iff
+ * theta_MAG = 0).  The local update maximises the site's F_MAG over each SU(2)
+ * subgroup in closed form (of the circle of maximisers, the element nearest
+ * the identity), then overrelaxation or stochastic relaxation as for Landau
+ * gauge.  lgt_result.F / theta and lgt_measure report F_MAG / theta_MAG.
+ * Launch configurations 0-3 only (others fall back to 0); after promotion it
+ * polishes in FP64 whatever `polish` says; no simulated annealing; not
+ * served (lgt_submit: LGT_EINVAL). */
+typedef enum { LGT_LANDAU = 0, LGT_COULOMB = 1, LGT_MAG = 2 } lgt_gauge;
 typedef enum { LGT_OR = 0, LGT_SR = 1 } lgt_algo; /* Sec. 3.1 / Sec. 3.2 */
 typedef enum {
   LGT_FP64 = 0,    /* all sweeps in FP64 */
@@ -172,7 +185,7 @@ typedef struct {
  *                            in order from a counter and start an item once
  *                            the previous half-sweep has finished its slice
  *                            and both neighbours (bounded waits: a wait over
- *                            2 s fails the call with LGT_ECUDA).
+ *                            2 s fails the call with LGT_ETIMEOUT).
  * A configuration that a phase's kernel lacks (4-10 after promotion; 7 and 10
  * on FP32-18 links) falls back to configuration 0 for that phase.  Every
  * configuration forms K(x) and the fused estimate in the same order; results

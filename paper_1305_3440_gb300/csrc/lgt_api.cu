@@ -103,8 +103,12 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("lattice too large (V/2 must fit in 32 bits)");
     return LGT_EINVAL;
   }
-  if (p->gauge != LGT_LANDAU && p->gauge != LGT_COULOMB) {
+  if (p->gauge != LGT_LANDAU && p->gauge != LGT_COULOMB && p->gauge != LGT_MAG) {
     lgt_set_error("gauge %d unknown", p->gauge);
+    return LGT_EINVAL;
+  }
+  if (p->gauge == LGT_MAG && p->sa_sweeps > 0) {
+    lgt_set_error("simulated annealing is not available for the maximally Abelian gauge");
     return LGT_EINVAL;
   }
   if (p->algo != LGT_OR && p->algo != LGT_SR) {
@@ -181,6 +185,9 @@ static int fmt_of(int32_t prec) { return prec == LGT_FP32_18 ? FMT_F32_18 : (pre
 
 size_t lgt_ctx_device_bytes(const lgt_params *p) {
   const Geom g = lgt_make_geom(p->dims);
+  lgt_params own = *p;
+  if (own.gauge == LGT_MAG) own.polish = LGT_POLISH_FP64;  // as lgt_create
+  p = &own;
   size_t b = field_bytes(FMT_F64, g.vh) + workspace_bytes(g, 64) + 4096;
   if (p->bulk != LGT_FP64) b += field_bytes(fmt_of(p->bulk), g.vh) + g_bytes(g.vh);
   if (p->bulk != LGT_FP64 && p->polish == LGT_POLISH_ANCHOR) b += k0_bytes(g.vh) + d_bytes(g.vh) - g_bytes(g.vh);
@@ -307,7 +314,7 @@ static lgt_status sync_stream(lgt_ctx *c) {
   resolve_events(c);
   if (streaming && (*c->h_err & LGT_ERR_STREAM_WAIT)) {
     lgt_set_error("a streaming sweep launch timed out waiting for a neighbouring slice; the field is invalid");
-    return LGT_ECUDA;
+    return LGT_ETIMEOUT;
   }
   return LGT_OK;
 }
@@ -374,6 +381,11 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
     lgt_set_error("lgt_create: device allocation failed (injected by LGT_FAULT)");
     return LGT_ENOMEM;
   }
+  // the maximally Abelian gauge polishes in FP64 (the pair and anchored
+  // polishes are built on K(x), which its quadratic functional lacks)
+  lgt_params own = *params;
+  if (own.gauge == LGT_MAG) own.polish = LGT_POLISH_FP64;
+  params = &own;
   lgt_ctx *c = new lgt_ctx();
   memset((void *)c, 0, sizeof *c);
   c->pending = new std::vector<lgt_ctx::Pending>();
@@ -382,7 +394,7 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   c->g = lgt_make_geom(params->dims);
   c->stream = (cudaStream_t)cuda_stream;
   c->bulk_fmt = fmt_of(params->bulk);
-  c->cfg.gauge = params->gauge == LGT_COULOMB ? GAUGE_COULOMB : GAUGE_LANDAU;
+  c->cfg.gauge = params->gauge == LGT_COULOMB ? GAUGE_COULOMB : (params->gauge == LGT_MAG ? GAUGE_MAG : GAUGE_LANDAU);
   c->cfg.algo = params->algo == LGT_SR ? ALGO_SR : ALGO_OR;
   c->cfg.omega = params->omega;
   c->cfg.sr_thr = sr_threshold(params->p);
@@ -428,8 +440,8 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   c->cfg_bulk = c->cfg_polish = lgt_cfg_of_block(params->block_size);
   if (params->launch_config > 0) {
     const int k = params->launch_config - 1;
-    c->cfg_bulk = lgt_cfg_supported(c->u32 ? c->bulk_fmt : (int)FMT_F64, k) ? k : 0;
-    c->cfg_polish = lgt_cfg_supported(polish_fmt, k) ? k : 0;
+    c->cfg_bulk = lgt_cfg_supported_gauge(c->u32 ? c->bulk_fmt : (int)FMT_F64, c->cfg.gauge, k) ? k : 0;
+    c->cfg_polish = lgt_cfg_supported_gauge(polish_fmt, c->cfg.gauge, k) ? k : 0;
   } else if (!params->block_size) {
     cudaError_t te = cudaSuccess;
     if (c->u32) c->cfg_bulk = lgt_tune_sweep(g, c->bulk_fmt, c->cfg, c->u32, c->G, c->ws, c->stream, &te);
@@ -603,7 +615,8 @@ static lgt_status measure(lgt_ctx *c, int with_plaq, double coulomb_target, Meas
   const int fmt = work_fmt(c);
   const void *links = c->phase == 0 ? c->u32 : c->u64;
   const int bt = batch_begin(c, 2);
-  LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream));
+  LGT_CUDA(launch_measure(fmt, c->g, links, c->ws, with_plaq, coulomb_target, 128, c->stream,
+                          c->prm.gauge == LGT_MAG ? 1 : 0));
   batch_end(c, bt);
   c->stats.measure_launches++;
   c->stats.launches++;

@@ -94,7 +94,7 @@ int lgt_tune_sweep(const Geom &g, int fmt, const SweepCfg &cfg, void *links, voi
   float best_ms = 1e30f;
   int best = 0;
   for (int k = 0; k < LGT_NCFG && e == cudaSuccess; k++) {
-    if (!lgt_cfg_supported(fmt, k)) continue;
+    if (!lgt_cfg_supported_gauge(fmt, cfg.gauge, k)) continue;
     e = launch_half_sweeps(fmt, g, links, G, ws, cfg, 0, 2, 0, 0, 0, 0, k, st, aux);
     for (int trial = 0; trial < 3 && e == cudaSuccess; trial++) {
       e = cudaEventRecord(e0, st);

@@ -28,7 +28,7 @@ enum { FMT_PAIR = 3 };
 // Anchored polish (lgt_anchor.cuh): not a link format but the sweep over a
 // fixed anchor field (FP32-12 copy + K0 pairs) with D = G - 1 as pairs.
 enum { FMT_ANCHOR = 4 };
-enum { GAUGE_LANDAU = 0, GAUGE_COULOMB = 1 };
+enum { GAUGE_LANDAU = 0, GAUGE_COULOMB = 1, GAUGE_MAG = 2 };  // MAG: maximally Abelian gauge
 enum { ALGO_OR = 0, ALGO_SR = 1, ALGO_SA = 2 };  // SA: simulated-annealing heat bath
 
 #define LGT_RE(a, b) (2 * (3 * (a) + (b)))
@@ -555,6 +555,48 @@ __device__ __forceinline__ void block_sum(T v[NV], double *out) {
     }
   }
   __syncthreads();
+}
+
+// --------------------------------------------- maximally Abelian gauge
+// The abstract names the maximally Abelian gauge; the text gives neither its
+// functional nor its update.  Reading: F_MAG = 1/(N_c N_d V) sum_{x,mu} sum_a
+// |U_mu(x)_aa|^2, maximised.  Its gauge gradient at x is carried by
+//   X(x) = sum_mu ( U_mu(x) D_mu(x)^dagger - D_mu(x-mu)^dagger U_mu(x-mu) )
+// (D the diagonal part), theta_MAG = 1/(N_c V) sum_x tr[Delta Delta^dagger]
+// with Delta the traceless part of (X - X^dagger)/(2i).  For an SU(2)
+// subgroup element R on rows/columns (i, j), the site's functional is
+// const + n.v/2 with n.sigma = R^dagger sigma_3 R and v summed over the 8
+// links from s(a, b) = (2 Re(a* b), 2 Im(a* b), |a|^2 - |b|^2): forward links
+// give s((gU)_ii, (gU)_ji) - s((gU)_ij, (gU)_jj), backward links
+// s(conj (Ug+)_ii, conj (Ug+)_ij) - s(conj (Ug+)_ji, conj (Ug+)_jj).  The
+// maximum is n = v/|v|; of its circle of elements (left factors
+// exp(i phi sigma_3) keep every |diagonal entry|) the one nearest the identity
+// is r = (|v| + v_3, -v_2, v_1, 0)/norm, or (0, 1, 0, 0) when v = -|v| e_3.
+
+// v += sign * s(a, b), a = (are, aim), b = (bre, bim)
+template <typename R>
+__device__ __forceinline__ void mag_s(R are, R aim, R bre, R bim, R sign, R v[3]) {
+  const R zre = are * bre + aim * bim, zim = are * bim - aim * bre;  // conj(a) b
+  v[0] += sign * (R(2) * zre);
+  v[1] += sign * (R(2) * zim);
+  v[2] += sign * ((are * are + aim * aim) - (bre * bre + bim * bim));
+}
+
+template <typename R>
+__device__ __forceinline__ void mag_maximum(const R v[3], R &r0, R &r1, R &r2, R &r3) {
+  r0 = R(1), r1 = R(0), r2 = R(0), r3 = R(0);
+  const R n2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  if (!(n2 > R(0))) return;
+  const R a = sqrt(n2) + v[2];
+  const R m2 = a * a + v[0] * v[0] + v[1] * v[1];
+  if (!(m2 > R(0))) {
+    r0 = R(0), r1 = R(1);
+    return;
+  }
+  const R inv = rsqrt_t(m2);
+  r0 = a * inv;
+  r1 = -v[1] * inv;
+  r2 = v[0] * inv;
 }
 
 }  // namespace lgt

@@ -123,6 +123,7 @@ struct MeasArgs {
   uint8_t *active;      // [nt]
   double coulomb_target;
   int with_plaq;
+  int mag;  // maximally Abelian gauge: slot 0 sums |U_aa|^2, slot 2 tr Delta_MAG^2
 };
 
 // Arguments of the fused estimate's finishing reduction (one block per slice).
@@ -191,7 +192,8 @@ struct SweepCfg {
 //    10: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
 // Every configuration forms K(x) in the same order and groups the fused
 // estimate by the same 8 sites; results differ only where the compiler fuses
-// multiply-adds differently in two kernels (FP32 rounding).
+// multiply-adds differently in two kernels (FP32 rounding).  The maximally
+// Abelian gauge has kernels in configurations 0-3 only.
 constexpr int LGT_NCFG = 11;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
@@ -211,6 +213,13 @@ __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) 
 __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
   return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
          (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c)) || fmt == FMT_F32_12);
+}
+// the maximally Abelian gauge has kernels in the one-thread-per-site configurations 0-3
+__host__ __device__ constexpr bool lgt_cfg_mag(int c) { return c >= 0 && c <= 3; }
+// whether a (format, gauge) pair has kernels for a configuration
+__host__ __device__ constexpr bool lgt_cfg_supported_gauge(int fmt, int gauge, int c) {
+  return lgt_cfg_supported(fmt, c) &&
+         (gauge != GAUGE_MAG || (lgt_cfg_mag(c) && (fmt == FMT_F64 || fmt == FMT_F32_18 || fmt == FMT_F32_12)));
 }
 // dynamic shared memory of the pipelined and streaming configurations: 2 buffers x 27 chunks x 16 B per thread
 constexpr int LGT_PIPE_SMEM_PER_THREAD = 2 * 27 * 16;
@@ -266,7 +275,7 @@ cudaError_t launch_fused_finish_batch(const BatchFused *jobs, int n, int total_b
 // w.totals / w.slice_F / w.slice_theta.  If coulomb_target >= 0 the slice
 // mask is set to (theta_t >= coulomb_target).  with_plaq: also plaquettes.
 cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
-                           double coulomb_target, int block, cudaStream_t st);
+                           double coulomb_target, int block, cudaStream_t st, int mag = 0);
 
 // AoS complex128 (device) -> SoA of format fmt, with SU(3) / finiteness check
 // (err bit 1 set on failure).

@@ -180,7 +180,7 @@ static cudaError_t half_sweep(int fmt, const Geom &g, void *links, void *G, cons
                               int parity, unsigned long long sweep, int reunit, int use_mask, int cfg,
                               cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every, bool pdl) {
   sweep_fn fn = pick_sweep(fmt, c, cfg);
-  if (!fn || !lgt_cfg_supported(fmt, cfg)) return cudaErrorInvalidValue;
+  if (!fn || !lgt_cfg_supported_gauge(fmt, c.gauge, cfg)) return cudaErrorInvalidValue;
   SweepArgs a;
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   a.aux = aux;
@@ -219,7 +219,7 @@ cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, con
     return cudaSuccess;
   }
   sweep_fn fn = pick_sweep(fmt, c, cfg);
-  if (!fn || !lgt_cfg_supported(fmt, cfg)) return cudaErrorInvalidValue;
+  if (!fn || !lgt_cfg_supported_gauge(fmt, c.gauge, cfg)) return cudaErrorInvalidValue;
   // launches of at most LGT_STREAM_MAX_HALF half-sweeps (and 2^30 tiles: the
   // ticket and slice counters are 32-bit)
   const long long tiles_half = (long long)ceil_div(g.vs_half, lgt_cfg_threads(cfg)) * g.nt;
@@ -266,9 +266,10 @@ void fill_meas_args(MeasArgs *a, const Geom &g, const void *links, const Workspa
 }
 
 cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
-                           double coulomb_target, int block, cudaStream_t st) {
+                           double coulomb_target, int block, cudaStream_t st, int mag) {
   MeasArgs a;
   fill_meas_args(&a, g, links, w, with_plaq, coulomb_target);
+  a.mag = mag;
   dim3 grid(ceil_div(g.vs_half, block), g.nt, 2);
   if (fmt == FMT_F64) k_measure<FMT_F64><<<grid, block, 0, st>>>(a);
   else if (fmt == FMT_F32_18) k_measure<FMT_F32_18><<<grid, block, 0, st>>>(a);

@@ -77,7 +77,33 @@ __device__ __forceinline__ void measure_body(const MeasArgs &a, int t, int p, in
     double XL[18], XS[18];
     mat_zero(XL);
     mat_zero(XS);
-    for (int mu = 0; mu < 4; mu++) {
+    if (a.mag) {  // maximally Abelian gauge: sum_a |U_aa|^2 and X(x) (see lgt_device.cuh)
+      for (int mu = 0; mu < 4; mu++) {
+        double u[18], y[18];
+        load_d<FMT>(a.links, a.g.vh, p, mu, i, u);
+#pragma unroll
+        for (int x = 0; x < 3; x++) {
+          v[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
+#pragma unroll
+          for (int z = 0; z < 3; z++) {  // y = U D^dagger
+            y[LGT_RE(x, z)] = u[LGT_RE(x, z)] * u[LGT_RE(z, z)] + u[LGT_IM(x, z)] * u[LGT_IM(z, z)];
+            y[LGT_IM(x, z)] = u[LGT_IM(x, z)] * u[LGT_RE(z, z)] - u[LGT_RE(x, z)] * u[LGT_IM(z, z)];
+          }
+        }
+        acc_antiherm(XL, y, 1.0);
+        load_d<FMT>(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+#pragma unroll
+        for (int x = 0; x < 3; x++)
+#pragma unroll
+          for (int z = 0; z < 3; z++) {  // y = D^dagger U
+            y[LGT_RE(x, z)] = u[LGT_RE(x, x)] * u[LGT_RE(x, z)] + u[LGT_IM(x, x)] * u[LGT_IM(x, z)];
+            y[LGT_IM(x, z)] = u[LGT_RE(x, x)] * u[LGT_IM(x, z)] - u[LGT_IM(x, x)] * u[LGT_RE(x, z)];
+          }
+        acc_antiherm(XL, y, -1.0);
+      }
+      v[2] = traceless_norm(XL);
+    }
+    for (int mu = 0; mu < 4 && !a.mag; mu++) {
       double u[18];
       load_d<FMT>(a.links, a.g.vh, p, mu, i, u);
       const double rt = u[LGT_RE(0, 0)] + u[LGT_RE(1, 1)] + u[LGT_RE(2, 2)];
@@ -91,8 +117,10 @@ __device__ __forceinline__ void measure_body(const MeasArgs &a, int t, int p, in
       acc_antiherm(XL, u, -1.0);
       if (mu > 0) acc_antiherm(XS, u, -1.0);
     }
-    v[2] = traceless_norm(XL);
-    v[3] = traceless_norm(XS);
+    if (!a.mag) {
+      v[2] = traceless_norm(XL);
+      v[3] = traceless_norm(XS);
+    }
     if (a.with_plaq) {
       for (int mu = 0; mu < 4; mu++)
         for (int nu = mu + 1; nu < 4; nu++) {

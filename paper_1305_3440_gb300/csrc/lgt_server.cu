@@ -740,6 +740,10 @@ extern "C" lgt_status lgt_submit(lgt_server *s, const lgt_params *params, const 
     lgt_set_error("lgt_submit: simulated annealing runs in lgt_fix only (sa_sweeps must be 0)");
     return LGT_EINVAL;
   }
+  if (params->gauge == LGT_MAG) {
+    lgt_set_error("lgt_submit: the maximally Abelian gauge runs in lgt_fix only");
+    return LGT_EINVAL;
+  }
   const size_t need = lgt_ctx_device_bytes(params) + aos_bytes_of(lgt_make_geom(params->dims));
   if (need > s->budget) {
     lgt_set_error("job needs %zu device bytes, more than the server budget %zu", need, s->budget);

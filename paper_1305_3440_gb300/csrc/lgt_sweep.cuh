@@ -604,6 +604,176 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
   cp_async_wait<0>();  // nothing of this thread's in flight at exit
 }
 
+// ------------------------------------------------ maximally Abelian gauge
+// v of subgroup (I, J) for the site's links as the running g leaves them:
+// the (I, J) blocks of g U_mu(x) and U_mu(x-mu) g^dagger, formed from the
+// links (loaded again: L1/L2 hits after the first pass) and g.
+template <int FMT, typename R, int I, int J>
+__device__ __forceinline__ void mag_vector(const SweepArgs &a, int p, int i, const Coords &c, const R g[18], R v[3]) {
+  typedef LinkIO<FMT> IO;
+  const int q = p ^ 1;
+  v[0] = v[1] = v[2] = R(0);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; mu++) {
+    R u[18];
+    IO::load(a.links, a.g.vh, p, mu, i, u);
+    // (g U)_ab = sum_k g_ak U_kb
+    R f[2][2][2];  // [a in (I, J)][b in (I, J)][re, im]
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        const int ra = x ? J : I, cb = y ? J : I;
+        R re = R(0), im = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          re += g[LGT_RE(ra, k)] * u[LGT_RE(k, cb)] - g[LGT_IM(ra, k)] * u[LGT_IM(k, cb)];
+          im += g[LGT_RE(ra, k)] * u[LGT_IM(k, cb)] + g[LGT_IM(ra, k)] * u[LGT_RE(k, cb)];
+        }
+        f[x][y][0] = re, f[x][y][1] = im;
+      }
+    mag_s<R>(f[0][0][0], f[0][0][1], f[1][0][0], f[1][0][1], R(1), v);   // s((gU)_II, (gU)_JI)
+    mag_s<R>(f[0][1][0], f[0][1][1], f[1][1][0], f[1][1][1], R(-1), v);  // - s((gU)_IJ, (gU)_JJ)
+    IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+    // (U g^dagger)_ab = sum_k U_ak conj(g_bk)
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        const int ra = x ? J : I, cb = y ? J : I;
+        R re = R(0), im = R(0);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          re += u[LGT_RE(ra, k)] * g[LGT_RE(cb, k)] + u[LGT_IM(ra, k)] * g[LGT_IM(cb, k)];
+          im += u[LGT_IM(ra, k)] * g[LGT_RE(cb, k)] - u[LGT_RE(ra, k)] * g[LGT_IM(cb, k)];
+        }
+        f[x][y][0] = re, f[x][y][1] = im;
+      }
+    // s(conj B_II, conj B_IJ) - s(conj B_JI, conj B_JJ)
+    mag_s<R>(f[0][0][0], -f[0][0][1], f[0][1][0], -f[0][1][1], R(1), v);
+    mag_s<R>(f[1][0][0], -f[1][0][1], f[1][1][0], -f[1][1][1], R(-1), v);
+  }
+}
+
+// one subgroup step: the maximum of subgroup (I, J), overrelaxed or squared
+// (Sec. 3.1, 3.2), applied to g's rows I, J
+template <int FMT, typename R, int ALGO, int I, int J>
+__device__ __forceinline__ void mag_step(const SweepArgs &a, int p, int i, const Coords &c, R g[18], R omega,
+                                         uint64_t sr_thr, uint32_t draw) {
+  R v[3];
+  mag_vector<FMT, R, I, J>(a, p, i, c, g, v);
+  R r0, r1, r2, r3;
+  mag_maximum<R>(v, r0, r1, r2, r3);
+  if (ALGO == ALGO_OR) {
+    r0 = (R(1) - omega) + omega * r0;
+    r1 *= omega;
+    r2 *= omega;
+    r3 *= omega;
+    const R inv = rsqrt_t(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    r0 *= inv;
+    r1 *= inv;
+    r2 *= inv;
+    r3 *= inv;
+  } else if ((uint64_t)draw < sr_thr) {
+    const R a0 = r0 * r0 - (r1 * r1 + r2 * r2 + r3 * r3);
+    const R two_r0 = R(2) * r0;
+    r1 *= two_r0;
+    r2 *= two_r0;
+    r3 *= two_r0;
+    r0 = a0;
+  }
+  // R_s = [[r0 + i r3, r2 + i r1], [-r2 + i r1, r0 - i r3]] on rows (I, J)
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const R gire = g[LGT_RE(I, k)], giim = g[LGT_IM(I, k)];
+    const R gjre = g[LGT_RE(J, k)], gjim = g[LGT_IM(J, k)];
+    g[LGT_RE(I, k)] = r0 * gire - r3 * giim + r2 * gjre - r1 * gjim;
+    g[LGT_IM(I, k)] = r0 * giim + r3 * gire + r2 * gjim + r1 * gjre;
+    g[LGT_RE(J, k)] = -r2 * gire - r1 * giim + r0 * gjre + r3 * gjim;
+    g[LGT_IM(J, k)] = -r2 * giim + r1 * gire + r0 * gjim - r3 * gjre;
+  }
+}
+
+// The half-sweep of the maximally Abelian gauge (one thread per site, any
+// link format; R = float for the FP32 formats, double for FP64).  The fused
+// estimate takes sum_a |U_aa|^2 over the site's 8 links (the parity-0 sums
+// give F_MAG, every link counted once) and tr Delta_MAG^2 from X(x), both
+// before the update.
+template <int FMT, typename R, int ALGO>
+__device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t, int bx) {
+  typedef LinkIO<FMT> IO;
+  if (a.active && !a.active[t]) return;
+  const int j = bx * blockDim.x + threadIdx.x;
+  R acc[2] = {R(0), R(0)};
+  if (j < a.g.vs_half) {
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    R X[18];
+    mat_zero(X);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; mu++) {
+      R u[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      // X += U D^dagger: X_ab += U_ab conj(U_bb)
+#pragma unroll
+      for (int x = 0; x < 3; x++)
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+          X[LGT_RE(x, y)] += u[LGT_RE(x, y)] * u[LGT_RE(y, y)] + u[LGT_IM(x, y)] * u[LGT_IM(y, y)];
+          X[LGT_IM(x, y)] += u[LGT_IM(x, y)] * u[LGT_RE(y, y)] - u[LGT_RE(x, y)] * u[LGT_IM(y, y)];
+        }
+#pragma unroll
+      for (int x = 0; x < 3; x++) acc[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+      // X -= D^dagger U: X_ab -= conj(U_aa) U_ab
+#pragma unroll
+      for (int x = 0; x < 3; x++)
+#pragma unroll
+        for (int y = 0; y < 3; y++) {
+          X[LGT_RE(x, y)] -= u[LGT_RE(x, x)] * u[LGT_RE(x, y)] + u[LGT_IM(x, x)] * u[LGT_IM(x, y)];
+          X[LGT_IM(x, y)] -= u[LGT_RE(x, x)] * u[LGT_IM(x, y)] - u[LGT_IM(x, x)] * u[LGT_RE(x, y)];
+        }
+#pragma unroll
+      for (int x = 0; x < 3; x++) acc[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
+    }
+    R unused;
+    violation_of_K(X, unused, acc[1]);  // Delta: traceless part of (X - X^dagger)/(2i)
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    R g[18];
+    mat_zero(g);
+    g[LGT_RE(0, 0)] = g[LGT_RE(1, 1)] = g[LGT_RE(2, 2)] = R(1);
+    const R omega = (R)a.omega;
+    mag_step<FMT, R, ALGO, 0, 1>(a, p, i, c, g, omega, a.sr_thr, draws.x);
+    mag_step<FMT, R, ALGO, 0, 2>(a, p, i, c, g, omega, a.sr_thr, draws.y);
+    mag_step<FMT, R, ALGO, 1, 2>(a, p, i, c, g, omega, a.sr_thr, draws.z);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; mu++) {
+      const int nb = cb_shift(a.g, c, mu, -1);
+      R u[18], r[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      mat_mul(g, u, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, p, mu, i, r);
+      IO::load(a.links, a.g.vh, q, mu, nb, u);
+      mat_mul_dag(u, g, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, q, mu, nb, r);
+    }
+    if constexpr (sizeof(R) == sizeof(float)) {
+      if (a.G) {
+        float gx[18], r[18];
+        GIO::load(a.G, a.g.vh, p, i, gx);
+        mat_mul(g, gx, r);
+        if (a.reunit) reunitarise(r);
+        GIO::store(a.G, a.g.vh, p, i, r);
+      }
+    }
+  }
+  fused_store<R, 1>(a, p, t, bx, acc);
+}
+
 // FP32 link formats, four threads per site: thread m of the site's quad owns
 // direction m (for Coulomb gauge thread 0 owns the temporal links, which the
 // transformation also moves).  Each thread loads its forward and backward

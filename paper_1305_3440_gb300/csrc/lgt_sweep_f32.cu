@@ -1,7 +1,8 @@
 // lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
 // storage), one instantiation per gauge, algorithm and launch configuration
 // (one or four threads per site; pipelined through shared memory; streaming
-// several half-sweeps per launch).
+// several half-sweeps per launch); the maximally Abelian gauge in the
+// one-thread-per-site configurations 0-3.
 #include "lgt_sweep.cuh"
 
 namespace lgt {
@@ -15,7 +16,9 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
     return;
   }
   const SweepArgs a = resolve_loop(in);
-  if constexpr (lgt_cfg_quad(CFG)) {
+  if constexpr (GAUGE == GAUGE_MAG) {
+    sweep_body_mag<FMT, float, ALGO>(a, p, blockIdx.y, blockIdx.x);
+  } else if constexpr (lgt_cfg_quad(CFG)) {
     sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
   } else if constexpr (lgt_cfg_pipe(CFG)) {
     if constexpr (FMT == FMT_F32_12)
@@ -40,6 +43,12 @@ static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
   LGT_PICK(FMT_F32_12, GAUGE_LANDAU, ALGO_SR)
   LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_OR)
   LGT_PICK(FMT_F32_12, GAUGE_COULOMB, ALGO_SR)
+  if constexpr (lgt_cfg_mag(CFG)) {  // maximally Abelian gauge: one thread per site, plain layouts
+    LGT_PICK(FMT_F32_18, GAUGE_MAG, ALGO_OR)
+    LGT_PICK(FMT_F32_18, GAUGE_MAG, ALGO_SR)
+    LGT_PICK(FMT_F32_12, GAUGE_MAG, ALGO_OR)
+    LGT_PICK(FMT_F32_12, GAUGE_MAG, ALGO_SR)
+  }
   if constexpr (CFG == 0) {  // the annealing sweeps run in configuration 0 only
     LGT_PICK(FMT_F32_18, GAUGE_LANDAU, ALGO_SA)
     LGT_PICK(FMT_F32_18, GAUGE_COULOMB, ALGO_SA)

@@ -9,7 +9,11 @@ template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs in, int p) {
   pdl_enter();
   const SweepArgs a = resolve_loop(in);
-  sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  if constexpr (GAUGE == GAUGE_MAG) {
+    sweep_body_mag<FMT_F64, double, ALGO>(a, p, blockIdx.y, blockIdx.x);
+  } else {
+    sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  }
 }
 
 template <int GAUGE, int ALGO, int CFG>
@@ -28,6 +32,13 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
 
 template <int CFG>
 static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
+  if (gauge == GAUGE_MAG) {  // maximally Abelian gauge: FP64 only here, configurations 0-3
+    if constexpr (lgt_cfg_mag(CFG)) {
+      if (fmt == FMT_F64 && algo == ALGO_OR) return k_sweep_f64<GAUGE_MAG, ALGO_OR, CFG>;
+      if (fmt == FMT_F64 && algo == ALGO_SR) return k_sweep_f64<GAUGE_MAG, ALGO_SR, CFG>;
+    }
+    return nullptr;
+  }
   if (fmt == FMT_F64) {
     if constexpr (CFG == 0) {  // the annealing sweeps run in configuration 0 only
       if (algo == ALGO_SA)

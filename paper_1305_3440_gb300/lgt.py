@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "liblgt.so")
 
 LGT_OK, LGT_EINVAL, LGT_ENOMEM, LGT_ECUDA, LGT_ENOTCONV, LGT_EAGAIN, LGT_ETIMEOUT, LGT_EBUSY, \
     LGT_ECANCELLED, LGT_ENOTFOUND = range(10)
-LGT_LANDAU, LGT_COULOMB = 0, 1
+LGT_LANDAU, LGT_COULOMB, LGT_MAG = 0, 1, 2
 LGT_OR, LGT_SR = 0, 1
 LGT_FP64, LGT_FP32_18, LGT_FP32_12 = 0, 1, 2
 LGT_POLISH_PAIR, LGT_POLISH_FP64, LGT_POLISH_ANCHOR = 0, 1, 2

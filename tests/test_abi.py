@@ -80,6 +80,17 @@ def test_bad_params_rejected_before_any_device_work(lgt, field, value):
     assert lgt.lgt_last_error()
 
 
+def test_gauge_range_and_mag_without_annealing(lgt):
+    """gauge 3 is unknown; the maximally Abelian gauge takes no annealing sweeps.
+    Both are refused by the parameter check, before any device work."""
+    import numpy as np
+    links = np.zeros((4, 4, 4, 4, 4, 3, 3), np.complex128)
+    for kw in (dict(gauge=3), dict(gauge=lgt.LGT_MAG, sa_sweeps=2)):
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_create(lgt.lgt_params_default(dims=(4, 4, 4, 4), **kw), links)
+        assert e.value.status == lgt.LGT_EINVAL
+
+
 @pytest.mark.parametrize("b0,b1", [(0.0, 1.0), (2.0, 1.0), (1.0, float("inf"))])
 def test_annealing_schedule_rejected(lgt, b0, b1):
     import numpy as np

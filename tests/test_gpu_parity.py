@@ -807,3 +807,126 @@ def test_annealing_is_not_served(lgt):
         assert e.value.status == lgt.LGT_EINVAL
     finally:
         lgt.lgt_server_destroy(srv)
+
+
+# ------------------------------------------------- maximally Abelian gauge
+def _abelian_transformed(dims, seed, spread=0.35):
+    """A diagonal (Abelian) field under a random gauge transformation near 1: its
+    maximally Abelian gauge has F_MAG = 1."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(-np.pi, np.pi, size=tuple(dims) + (4, 2))
+    A = np.zeros(tuple(dims) + (4, 3, 3), np.complex128)
+    A[..., 0, 0] = np.exp(1j * phi[..., 0])
+    A[..., 1, 1] = np.exp(1j * phi[..., 1])
+    A[..., 2, 2] = np.exp(-1j * (phi[..., 0] + phi[..., 1]))
+    from lattice_np import GELL_MANN, expm_herm, transform_field
+    n = int(np.prod(dims))
+    G = np.stack([expm_herm(spread * np.einsum("a,aij->ij", rng.normal(size=8), GELL_MANN))
+                  for _ in range(n)]).reshape(tuple(dims) + (3, 3))
+    return A, np.ascontiguousarray(transform_field(A, G))
+
+
+@pytest.mark.parametrize("dims", [DIMS_RAGGED, (2, 2, 2, 2)])
+def test_mag_measurement_matches_oracle(lgt, dims):
+    """F_MAG, theta_MAG and the plaquette of the exact FP64 measurement kernel."""
+    U = synth.field(dims, 0.5, 61)
+    ctx = lgt.lgt_create(lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_MAG), U)
+    try:
+        F, theta, plaq = lgt.lgt_measure(ctx)
+    finally:
+        lgt.lgt_destroy(ctx)
+    m = O.measure(U, O.MAG)
+    assert abs(F - m["F"]) < 1e-14 and abs(theta - m["theta"]) < 1e-12 * m["theta"]
+    assert abs(plaq - m["plaq"]) < 1e-14
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_18", "fp32_12"])
+@pytest.mark.parametrize("algo", list(ALGOS))
+@pytest.mark.parametrize("parity", [0, 1])
+def test_mag_half_sweep_matches_oracle(lgt, bulk, algo, parity):
+    """One half-sweep of the maximally Abelian gauge against the oracle, every launch
+    configuration 0-3: FP64 within 1e-12; FP32 link storage with a bound derived
+    from the update: the subgroup element is n = v/|v|, so FP32 rounding of v
+    (~1e-7 of its terms, which are O(1)) moves n by ~1e-7/|v|; on this rough field
+    the smallest |v| is ~0.25 against a median ~3, so the worst sites may reach a
+    few 1e-6 per step, compounded over three steps: max 5e-5, and 99.9% of the
+    entries within 1e-6."""
+    U = synth.field(DIMS_RAGGED, 0.5, 62)
+    b = getattr(lgt, "LGT_" + bulk.upper())
+    ref = U.copy()
+    O.half_sweep(ref, parity, gauge=O.MAG, algo=ALGOS[algo], omega=1.7, p=0.8, seed=63)
+    for k in range(4):
+        got = gpu_half(lgt, U, parity, bulk=b, gauge=lgt.LGT_MAG, algo=ALGOS[algo], omega=1.7, p=0.8, seed=63,
+                       reunit_every=0, launch_config=k + 1)
+        err = np.abs(got - ref)
+        if bulk == "fp64":
+            assert err.max() < 1e-12, (k, err.max())
+        else:
+            assert err.max() < 5e-5 and np.mean(err < 1e-6) > 0.999, (k, err.max(), np.mean(err < 1e-6))
+
+
+def test_mag_sweeps_match_the_oracle(lgt):
+    """Ten FP64 sweeps (both parities, fused estimates on) follow the oracle's
+    trajectory to 1e-11."""
+    U = synth.field(DIMS_RAGGED, 0.5, 64)
+    got = gpu_run(lgt, U, 10, gauge=lgt.LGT_MAG, omega=1.7)
+    ref = U.copy()
+    O.sweeps(ref, 10, gauge=O.MAG, omega=1.7)
+    assert np.abs(got - ref).max() < 1e-11
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_12"])
+def test_mag_fix_matches_oracle(lgt, bulk):
+    """lgt_fix in the maximally Abelian gauge: the FP64 path ends where the oracle's
+    fix ends (same F_MAG to 1e-10), the mixed ladder (FP32-12 bulk, FP64 polish)
+    converges to the same maximum, and both outputs are gauge transforms of the
+    input (plaquettes to 1e-12) certified by the oracle."""
+    dims = (4, 6, 4, 8)
+    U = synth.field(dims, 0.4, 65)
+    ref = U.copy()
+    r = O.fix(ref, gauge=O.MAG, omega=1.7, tol=1e-13, max_sweeps=20000, check_every=10)
+    assert r["converged"]
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_MAG, bulk=getattr(lgt, "LGT_" + bulk.upper()),
+                               omega=1.7, theta_tol=1e-13, max_sweeps=20000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+        cfgs = lgt.lgt_get_stats(ctx).launch_config
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and all(0 <= k <= 3 for k in cfgs)
+    m = O.measure(V, O.MAG)
+    assert m["theta"] < 1e-13 and abs(m["F"] - res.F) < 1e-12
+    assert abs(res.F - r["F"]) < 1e-10, (res.F, r["F"])
+    assert np.abs(plaquettes(V) - plaquettes(U)).max() < 1e-12
+
+
+def test_mag_recovers_a_transformed_abelian_field(lgt):
+    """A gauge-transformed Abelian field: the ladder climbs back to F_MAG = 1."""
+    dims = (8, 8, 8, 8)
+    A, U = _abelian_transformed(dims, 66)
+    p = lgt.lgt_params_default(dims=dims, gauge=lgt.LGT_MAG, bulk=lgt.LGT_FP32_12, omega=1.7, theta_tol=1e-14,
+                               max_sweeps=20000)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and abs(res.F - 1) < 1e-12
+    assert np.abs(plaquettes(V) - plaquettes(A)).max() < 1e-12
+
+
+def test_mag_is_not_served_nor_annealed(lgt):
+    srv = lgt.lgt_server_create(1 << 30, 0)
+    try:
+        with pytest.raises(lgt.LgtError) as e:
+            lgt.lgt_submit(srv, lgt.lgt_params_default(dims=(4, 4, 4, 4), gauge=lgt.LGT_MAG),
+                           synth.field((4, 4, 4, 4), 0.3, 1))
+        assert e.value.status == lgt.LGT_EINVAL
+    finally:
+        lgt.lgt_server_destroy(srv)
+    with pytest.raises(lgt.LgtError):
+        lgt.lgt_create(lgt.lgt_params_default(dims=(4, 4, 4, 4), gauge=lgt.LGT_MAG, sa_sweeps=3),
+                       synth.field((4, 4, 4, 4), 0.3, 1))
