@@ -35,9 +35,9 @@ def ready(done, h, t, tiles_x, nt):
     return all(done[(t + d) % nt] >= need for d in (-1, 0, 1))
 
 
-def run(nt, tiles_x, n_half, nblocks, seed):
+def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
     """Replays the blocks' protocol; returns the number of waits that found the
-    slices not ready."""
+    slices not ready.  `ready` is the dependency rule (the kernel's by default)."""
     rng = random.Random(seed)
     total = tiles_x * nt * n_half
     done = [0] * nt
@@ -127,3 +127,18 @@ def test_skew_keeps_a_single_block_from_waiting():
     per half-sweep its next item is always ready when it looks (no waits), where
     an unshifted order would have to wait at every half-sweep boundary."""
     assert run(16, 4, 10, 1, 0) == 0
+
+
+def test_a_weaker_rule_is_caught():
+    """The model has teeth: waiting for the item's own slice only (not its two
+    neighbours, whose sites share the temporal links) lets items of consecutive
+    half-sweeps touch the same links at once, and the replay reports it."""
+    def own_slice_only(done, h, t, tiles_x, nt):
+        return h == 0 or done[t] >= h * tiles_x
+    caught = 0
+    for seed in range(20):
+        try:
+            run(8, 2, 6, 12, seed, ready=own_slice_only)
+        except AssertionError:
+            caught += 1
+    assert caught > 0
