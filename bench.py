@@ -47,10 +47,23 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--workload", default="landau32", choices=["landau32", "coulomb", "landau64", "serve", "mag"],
+    ap.add_argument("--workload", default="landau32",
+                    choices=["landau32", "coulomb", "landau64", "serve", "mag", "profile"],
                     help="landau32 (default; the headline line), or one of the other workloads, each "
-                         "printing its own line")
+                         "printing its own line; profile: a short fixed run of the sweep kernels for ncu")
     ap.add_argument("--jobs", type=int, default=256, help="serve: number of jobs in the stream")
+    prof = ap.add_argument_group("profile", "the short fixed run of --workload profile")
+    prof.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
+    prof.add_argument("--eps", type=float, default=0.5)
+    prof.add_argument("--seed", type=int, default=2)
+    prof.add_argument("--gauge", default="landau", choices=["landau", "coulomb", "mag"])
+    prof.add_argument("--bulk", default="fp32_12", choices=["fp32_12", "fp32_18", "fp64"])
+    prof.add_argument("--omega", type=float, default=1.7)
+    prof.add_argument("--bulk-sweeps", type=int, default=8)
+    prof.add_argument("--polish-sweeps", type=int, default=4)
+    prof.add_argument("--polish", default="anchor", choices=["anchor", "pair", "fp64"])
+    prof.add_argument("--launch-config", type=int, default=-1,
+                      help="force launch configuration k of the sweep kernels (-1: autotuned)")
     return ap.parse_args()
 
 
@@ -691,6 +704,40 @@ def run_serve(args):
           flush=True)
 
 
+def run_profile(args):
+    """A short, fixed run of the sweep kernels for profilers (ncu -k ... -c ...):
+    one context on cuda:0, `--bulk-sweeps` sweeps in the bulk precision, promotion
+    (G applied to the FP64 input, then the polish set-up), `--polish-sweeps` polish
+    sweeps, one exact measurement.  Profilers serialise launches, which misleads
+    the autotuner: pass `--launch-config` to profile the configuration a normal run
+    picks.  At 32^4 the FP32 links (201 MB for 12 reals) are larger than the 129 MB
+    L2 while the whole context stays under 2 GB of device memory (FP64: 3 GB)."""
+    import torch
+    from paper_1305_3440_gb300 import lgt, synth
+    dims = tuple(args.dims)
+    dev = torch.from_numpy(synth.field(dims, args.eps, args.seed)).cuda()
+    bulk = {"fp32_12": lgt.LGT_FP32_12, "fp32_18": lgt.LGT_FP32_18, "fp64": lgt.LGT_FP64}[args.bulk]
+    gauge = {"landau": lgt.LGT_LANDAU, "coulomb": lgt.LGT_COULOMB, "mag": lgt.LGT_MAG}[args.gauge]
+    polish = {"anchor": lgt.LGT_POLISH_ANCHOR, "pair": lgt.LGT_POLISH_PAIR, "fp64": lgt.LGT_POLISH_FP64}[args.polish]
+    p = lgt.lgt_params_default(dims=dims, gauge=gauge, omega=args.omega, bulk=bulk, polish=polish,
+                               launch_config=args.launch_config + 1)
+    ctx = lgt.lgt_create(p, dev)
+    try:
+        lgt.lgt_sweep(ctx, args.bulk_sweeps)
+        lgt.lgt_promote(ctx)
+        lgt.lgt_sweep(ctx, args.polish_sweeps)
+        F, theta, plaq = lgt.lgt_measure(ctx)
+        st = lgt.lgt_get_stats(ctx)
+        print(json.dumps({"workload": "profile", "dims": list(dims), "gauge": args.gauge, "bulk": args.bulk,
+                          "sweeps": [args.bulk_sweeps, args.polish_sweeps], "F": F, "theta": theta,
+                          "plaquette": plaq, "launch_config": list(st.launch_config),
+                          "sweep_ms": list(st.sweep_ms), "sweep_launches": list(st.sweep_launches)}), flush=True)
+        if not np.isfinite(F):
+            raise SystemExit("non-finite F")
+    finally:
+        lgt.lgt_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -703,6 +750,8 @@ def main():
         run_serve(args)
     elif args.workload == "mag":
         run_mag(args)
+    elif args.workload == "profile":
+        run_profile(args)
     else:
         run_ours(args)
 

@@ -24,14 +24,23 @@ __device__ __forceinline__ int batch_row(const int *begins, int stride_bytes, in
   return lo;
 }
 
+// Snake order over the whole batched grid (as the single-lattice sweeps): a
+// half-sweep of parity 1 visits the blocks from the last, so it starts on the
+// lattices and slices the parity-0 half-sweep finished last.  Every row of a
+// batch is filled with the same order setting.
+__device__ __forceinline__ int batch_block(const BatchSweep *jobs, int p) {
+  return (jobs[0].a.snake && (p & 1)) ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+}
+
 template <int FMT, int GAUGE, int ALGO>
 __global__ void __launch_bounds__(256) k_sweep_batch(const BatchSweep *jobs, int n, int p, int s) {
-  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, blockIdx.x);
+  const int b = batch_block(jobs, p);
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, b);
   const BatchSweep &J = jobs[k];
   SweepArgs a = J.a;
   a.sweep += (unsigned long long)s;
   a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
-  const int local = blockIdx.x - J.block_begin;
+  const int local = b - J.block_begin;
   const int t = local / J.nbx;
   sweep_dispatch<FMT, GAUGE, ALGO>(a, p, t, local - t * J.nbx, J.nbx);
 }
@@ -53,12 +62,13 @@ __global__ void __launch_bounds__(256) k_measure_batch(const BatchMeas *jobs, in
 // SM), as launch configuration 8 of the single-lattice kernels.
 template <int FMT, int GAUGE, int ALGO>
 __global__ void __launch_bounds__(128, 4) k_sweep_batch_lean(const BatchSweep *jobs, int n, int p, int s) {
-  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, blockIdx.x);
+  const int b = batch_block(jobs, p);
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, b);
   const BatchSweep &J = jobs[k];
   SweepArgs a = J.a;
   a.sweep += (unsigned long long)s;
   a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
-  const int local = blockIdx.x - J.block_begin;
+  const int local = b - J.block_begin;
   const int t = local / J.nbx;
   sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, t, local - t * J.nbx);
 }

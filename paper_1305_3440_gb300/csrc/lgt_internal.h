@@ -107,6 +107,9 @@ struct SweepArgs {
   int *err;
   int n_half;
   int stream_tiles;  // tiles (of blockDim.x sites) per scheduled item
+  // snake order: a half-sweep of parity 1 visits the (slice, tile) list from
+  // its end, so it starts on the links the parity-0 half-sweep touched last
+  int snake;
 };
 
 // Arguments of one lattice's exact measurement.

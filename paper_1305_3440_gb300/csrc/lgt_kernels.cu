@@ -100,6 +100,12 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
     return n >= 1 && n <= 64 ? n : LGT_STREAM_TILES;
   }();
   a->stream_tiles = tiles;
+  // LGT_SWEEP_SNAKE=0 in the environment: every half-sweep in forward order
+  static const int snake = [] {
+    const char *v = getenv("LGT_SWEEP_SNAKE");
+    return (v && v[0] == '0') ? 0 : 1;
+  }();
+  a->snake = snake;
 }
 
 // SMs of the current device, looked up once per device ordinal

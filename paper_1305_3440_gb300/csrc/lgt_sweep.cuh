@@ -84,6 +84,26 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Snake order.  Blocks are dispatched in increasing linear index, so a launch
+// walks the lattice slice by slice and the lines it touched last are the ones
+// still in L2 when it ends.  A half-sweep of parity 1 therefore visits the
+// (slice, tile) list from its end: it starts on the slices the parity-0
+// half-sweep finished last, reads most of their links from L2 and overwrites
+// those dirty lines before they are written back, and the next parity-0
+// half-sweep starts where it ended.  Sites of one parity touch disjoint links,
+// so the order changes no result; the estimate slots follow the logical tile.
+__device__ __forceinline__ bool sweep_reversed(const SweepArgs &a, int p) { return a.snake && (p & 1); }
+// (slice, tile) of this block in a (tiles per slice, slices) grid
+__device__ __forceinline__ void sweep_block_tile(const SweepArgs &a, int p, int &t, int &bx) {
+  if (sweep_reversed(a, p)) {
+    t = (int)gridDim.y - 1 - (int)blockIdx.y;
+    bx = (int)gridDim.x - 1 - (int)blockIdx.x;
+  } else {
+    t = (int)blockIdx.y;
+    bx = (int)blockIdx.x;
+  }
+}
+
 // A device loop's sweep kernels take the sweep number (SR counter) and the
 // reunitarisation flag from the loop state (see LoopState).
 __device__ __forceinline__ SweepArgs resolve_loop(const SweepArgs &in) {
@@ -309,8 +329,10 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
   const int total = tiles_x * a.g.nt;
   const float4 *L = reinterpret_cast<const float4 *>(a.links);
   const float4 *Gs = reinterpret_cast<const float4 *>(a.G);
-  auto issue = [&](int tile, int buf) {
-    if (tile < total) {
+  const bool rev = sweep_reversed(a, p);
+  auto issue = [&](int slot, int buf) {
+    if (slot < total) {
+      const int tile = rev ? total - 1 - slot : slot;
       const int t = tile / tiles_x, j = (tile - t * tiles_x) * T + tid;
       if (!(a.active && !a.active[t]) && j < a.g.vs_half) {
         const Coords c = coords_in_slice(a.g, p, t, j);
@@ -333,11 +355,12 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
     }
     cp_async_commit();  // possibly empty: every iteration commits exactly one group
   };
-  int tile = (int)blockIdx.x;
-  issue(tile, 0);
-  for (int it = 0; tile < total; it++, tile += (int)gridDim.x) {
-    issue(tile + (int)gridDim.x, (it + 1) & 1);
+  int slot = (int)blockIdx.x;  // position in the visiting order
+  issue(slot, 0);
+  for (int it = 0; slot < total; it++, slot += (int)gridDim.x) {
+    issue(slot + (int)gridDim.x, (it + 1) & 1);
     cp_async_wait<1>();  // this thread's copies of the current tile have landed
+    const int tile = rev ? total - 1 - slot : slot;
     const int t = tile / tiles_x, bx = tile - t * tiles_x;
     if (a.active && !a.active[t]) continue;  // the whole tile belongs to one slice
     const int j = bx * T + tid;

@@ -16,17 +16,21 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
     return;
   }
   const SweepArgs a = resolve_loop(in);
-  if constexpr (GAUGE == GAUGE_MAG) {
-    sweep_body_mag<FMT, float, ALGO>(a, p, blockIdx.y, blockIdx.x);
-  } else if constexpr (lgt_cfg_quad(CFG)) {
-    sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
-  } else if constexpr (lgt_cfg_pipe(CFG)) {
-    if constexpr (FMT == FMT_F32_12)
+  if constexpr (lgt_cfg_pipe(CFG)) {
+    if constexpr (FMT == FMT_F32_12 && GAUGE != GAUGE_MAG)
       sweep_body_f32_pipe<GAUGE, ALGO>(a, p, (a.g.vs_half + (int)blockDim.x - 1) / (int)blockDim.x);
+    return;
+  }
+  int t, bx;
+  sweep_block_tile(a, p, t, bx);
+  if constexpr (GAUGE == GAUGE_MAG) {
+    sweep_body_mag<FMT, float, ALGO>(a, p, t, bx);
+  } else if constexpr (lgt_cfg_quad(CFG)) {
+    sweep_body_f32_quad<FMT, GAUGE, ALGO>(a, p, t, bx);
   } else if constexpr (lgt_cfg_lean(CFG)) {
-    sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x);
+    sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, t, bx);
   } else {
-    sweep_body_f32<FMT, GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+    sweep_body_f32<FMT, GAUGE, ALGO>(a, p, t, bx, gridDim.x);
   }
 }
 

@@ -9,10 +9,12 @@ template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_f64(SweepArgs in, int p) {
   pdl_enter();
   const SweepArgs a = resolve_loop(in);
+  int t, bx;
+  sweep_block_tile(a, p, t, bx);
   if constexpr (GAUGE == GAUGE_MAG) {
-    sweep_body_mag<FMT_F64, double, ALGO>(a, p, blockIdx.y, blockIdx.x);
+    sweep_body_mag<FMT_F64, double, ALGO>(a, p, t, bx);
   } else {
-    sweep_body_f64<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+    sweep_body_f64<GAUGE, ALGO>(a, p, t, bx, gridDim.x);
   }
 }
 
@@ -20,14 +22,18 @@ template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_pair(SweepArgs in, int p) {
   pdl_enter();
   const SweepArgs a = resolve_loop(in);
-  sweep_body_pair<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  int t, bx;
+  sweep_block_tile(a, p, t, bx);
+  sweep_body_pair<GAUGE, ALGO>(a, p, t, bx, gridDim.x);
 }
 
 template <int GAUGE, int ALGO, int CFG>
 __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) k_sweep_anchor(SweepArgs in, int p) {
   pdl_enter();
   const SweepArgs a = resolve_loop(in);
-  sweep_body_anchor<GAUGE, ALGO>(a, p, blockIdx.y, blockIdx.x, gridDim.x);
+  int t, bx;
+  sweep_block_tile(a, p, t, bx);
+  sweep_body_anchor<GAUGE, ALGO>(a, p, t, bx, gridDim.x);
 }
 
 template <int CFG>
