@@ -232,6 +232,26 @@ LGT_API lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double *p
  * normalisation: spatial directions, N_d = 3, V_s).  Host arrays of N_t. */
 LGT_API lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *theta_t);
 
+/* The sweeps' own estimate of F and theta (Sec. 4 checks the precision after
+ * every few sweeps; here the sweep kernels form it from the K(x) every site
+ * update already has in registers, and lgt_fix's checks read it).  After a
+ * full sweep (parity 0, then parity 1) it describes that sweep:
+ *   F from Re tr K(x) of the even sites before their update: every link
+ *     counted once, so this is the F of the field the sweep started from;
+ *   theta from tr[Delta Delta^dagger] of every site's K(x), Delta the
+ *     traceless part of (K - K^dagger)/(2i) (the Sec. 2 violation at a site
+ *     whose neighbours carry g = 1): the even sites on the field the sweep
+ *     started from, the odd sites on the field after its even half (lagging
+ *     the field by half a sweep).
+ * Maximally Abelian gauge: F_MAG from sum_a |U_aa|^2 of the even sites' links
+ * and theta_MAG from X(x), likewise.  Sums in FP64 (per site in the sweep's
+ * precision).  F, theta: as lgt_measure reports them (Coulomb: mean F_t, max
+ * theta_t).  F_t, theta_t (nullable): host arrays of N_t, per timeslice in the
+ * Coulomb normalisation (Landau: the slice's share in that normalisation).
+ * Slices masked off as converged report theta_t = 0.  Meaningless before the
+ * first full sweep after lgt_create / lgt_load. */
+LGT_API lgt_status lgt_estimate(lgt_ctx *ctx, double *F, double *theta, double *F_t, double *theta_t);
+
 /* Gauge-fix to theta < theta_tol (Sec. 4 driver) through the precision
  * ladder: bulk FP32 sweeps until the exact working-field theta drops below
  * theta_switch, then promotion (the accumulated gauge transformation G,
@@ -287,6 +307,23 @@ typedef struct {
  * from CUDA events recorded on the context's stream around each batch of
  * consecutive half-sweep launches (nothing else runs inside a batch). */
 LGT_API lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out);
+
+/* Test support; the paper has no counterpart.  Fault injection for the bounded
+ * waits of the streaming launch configuration (10), so that their error path
+ * can be exercised on a GPU without any device fault.  Until the next
+ * lgt_load, every streaming launch that lgt_sweep / lgt_half_sweep issue on
+ * this context (lgt_fix's device loops are not affected) waits at most wait_ns
+ * nanoseconds for a neighbouring slice (0: the built-in 2 s; larger values:
+ * LGT_EINVAL) and takes its first work item at ticket skip_items instead of 0,
+ * so the first skip_items items of its first half-sweep never run (0: none).
+ * The slices those items cover then never become ready for the next
+ * half-sweep: its items wait until the limit, a block raises the launch's
+ * abort flag and the context's error word, every block ends, and the call
+ * returns LGT_ETIMEOUT -- as does every later synchronisation of the context
+ * until lgt_load clears the error.  The field is then invalid.  Every wait is
+ * bounded and every block exits; a launch with fewer than two half-sweeps
+ * never waits. */
+LGT_API lgt_status lgt_inject_stream_stall(lgt_ctx *ctx, uint64_t wait_ns, uint32_t skip_items);
 
 /* Release every resource of the context.  NULL is ignored. */
 LGT_API void lgt_destroy(lgt_ctx *ctx);

@@ -82,6 +82,10 @@ def _load():
             L.orc_sa_beta.restype = ctypes.c_double
             L.orc_mag_subgroup.argtypes = [_dp, ctypes.c_int, _dp, _dp]
             L.orc_mag_subgroup.restype = None
+            L.orc_site_conditioning.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                ctypes.c_uint64, _dp]
+            L.orc_parity_violation.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, _dp]
             L.orc_set_threads.restype = None
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -174,6 +178,27 @@ def local_update(K: np.ndarray, algo=OR, omega=1.0, p=0.0, draws=(0, 0, 0)):
     _load().orc_local_update(K.ctypes.data, algo, omega, p, dr.ctypes.data, g.ctypes.data,
                              W.ctypes.data, R.ctypes.data)
     return g, W, R
+
+
+def site_conditioning(links, parity, gauge=LANDAU, algo=OR, omega=1.0, p=0.0, seed=0, sweep=0):
+    """Per-site conditioning of the site updates of one parity on these links
+    (test infrastructure for the FP32 parity bounds; see the C source): an array
+    of shape (N_t, N_3, N_2, N_1), NaN at the sites of the other parity."""
+    d = _dims_of(links)
+    out = np.full(links.shape[:4], np.nan)
+    _check(_load().orc_site_conditioning(d, links.ctypes.data, gauge, parity, algo, omega, p, seed, sweep,
+                                         out.ctypes.data), "orc_site_conditioning")
+    return out
+
+
+def parity_violation(links, parity, gauge=LANDAU):
+    """Per timeslice, the sum of tr[Delta Delta^dagger] (Sec. 2) over the sites of
+    one parity (test infrastructure for the fused estimate).  Shape (N_t,)."""
+    d = _dims_of(links)
+    out = np.zeros(links.shape[0])
+    _check(_load().orc_parity_violation(d, links.ctypes.data, gauge, parity, out.ctypes.data),
+           "orc_parity_violation")
+    return out
 
 
 def gather_K(links, site, gauge=LANDAU):

@@ -544,13 +544,16 @@ static su3 local_gauge_update(const su3 *K, const update_rule *rule, const uint3
 
 /* Maximally Abelian gauge: the subgroup steps on the site's own links (the
  * site functional is quadratic in g, so K(x) does not suffice).  fwd/bwd are
- * the 4 forward and 4 backward links; they are updated in place; returns g. */
-static su3 mag_local_update(su3 fwd[4], su3 bwd[4], const update_rule *rule, const uint32_t draws[3]) {
+ * the 4 forward and 4 backward links; they are updated in place; returns g.
+ * trace_v (nullable) receives the vector v of each step (3 x 3 doubles). */
+static su3 mag_local_update(su3 fwd[4], su3 bwd[4], const update_rule *rule, const uint32_t draws[3],
+                            double trace_v[3][3]) {
   su3 g = m_identity();
   for (int s = 0; s < 3; s++) {
     const int i = SUBGROUP[s][0], j = SUBGROUP[s][1];
     double v[3], r[4];
     mag_vector(fwd, bwd, i, j, v);
+    if (trace_v) memcpy(trace_v[s], v, sizeof v);
     mag_maximum(v, r);
     if (rule->algo == ORC_OR) {
       su2_overrelax(r, rule->omega);
@@ -608,7 +611,7 @@ static su3 site_g(const lattice *l, const double *links, int64_t site, const swe
       fwd[mu] = load_link(links, site, mu);
       bwd[mu] = load_link(links, site_shift(l, site, mu, -1), mu);
     }
-    return mag_local_update(fwd, bwd, &rule, u);
+    return mag_local_update(fwd, bwd, &rule, u, NULL);
   }
   su3 K = gather_K(l, links, site, cfg->gauge);
   return local_gauge_update(&K, &rule, u, NULL, NULL);
@@ -907,6 +910,106 @@ void orc_local_update(const double *K, int algo, double omega, double p, const u
     if (W_out) from_su3(&W[s], W_out + 18 * s);
     if (R_out) from_su3(&R[s], R_out + 18 * s);
   }
+}
+
+/* Conditioning of the site updates of one parity on the current links.
+ * TEST INFRASTRUCTURE for the FP32 parity bounds: a site update computed in
+ * FP32 is off from the FP64 one by about (rounding of its input) x (this
+ * number), to first order.  The steps follow the update rule (overrelaxation
+ * or stochastic relaxation), so each subgroup sees what the steps before it
+ * left.
+ *   Landau, Coulomb: kappa = 1 / min_s |q_s|, q_s the quaternion projection of
+ *     the running W's (i, j) block before step s (Sec. 3 closed form: the
+ *     subgroup element is (q0, -q)/|q|, whose first-order change is at most
+ *     |dq| / |q|).
+ *   Maximally Abelian gauge: kappa = sum_s sqrt(2 / (|v_s| (|v_s| + v_s3))):
+ *     the element r = (|v| + v_3, -v_2, v_1, 0) / sqrt(2 |v| (|v| + v_3))
+ *     depends on v through n = v/|v| (|dn| <= |dv| / |v|) and, near
+ *     n = -e_3, through the rotation axis n x e_3 (|dr| grows as
+ *     1 / sqrt(1 + n_3)); the three steps compound, so their terms add.
+ * out[site] (V doubles) for the sites of `parity` (Coulomb: of every slice),
+ * left untouched elsewhere; +infinity where a step is degenerate. */
+int orc_site_conditioning(const int32_t dims[4], const double *links, int gauge, int parity, int algo, double omega,
+                          double p, uint64_t seed, uint64_t sweep, double *out) {
+  if (check_dims(dims)) return -1;
+  if (algo != ORC_OR && algo != ORC_SR) return -1;
+  const lattice l = make_lattice(dims);
+  sweep_cfg cfg = make_cfg(gauge, algo, omega, p, seed, 1);
+  const int64_t nh = l.vol / 2;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < nh; k++) {
+    const int64_t site = parity_site(&l, parity, k);
+    uint32_t u[3] = {0, 0, 0};
+    if (algo == ORC_SR) sr_draws(seed, sweep, site, u);
+    update_rule rule = cfg.rule;
+    rule.seed = seed;
+    rule.sweep = sweep;
+    rule.site = site;
+    double kappa = 0.0;
+    if (gauge == ORC_MAG) {
+      su3 fwd[4], bwd[4];
+      for (int mu = 0; mu < 4; mu++) {
+        fwd[mu] = load_link(links, site, mu);
+        bwd[mu] = load_link(links, site_shift(&l, site, mu, -1), mu);
+      }
+      double v[3][3];
+      mag_local_update(fwd, bwd, &rule, u, v);
+      for (int s = 0; s < 3; s++) {
+        const double nv = sqrt(v[s][0] * v[s][0] + v[s][1] * v[s][1] + v[s][2] * v[s][2]);
+        const double d = nv * (nv + v[s][2]);
+        kappa += d > 0.0 ? sqrt(2.0 / d) : INFINITY;
+      }
+    } else {
+      su3 K = gather_K(&l, links, site, gauge), W[3];
+      local_gauge_update(&K, &rule, u, W, NULL);
+      double qmin = INFINITY;
+      for (int s = 0; s < 3; s++) {
+        const int i = SUBGROUP[s][0], j = SUBGROUP[s][1];
+        double q[4];
+        su2_project(W[s].e[i][i], W[s].e[i][j], W[s].e[j][i], W[s].e[j][j], q);
+        const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        if (nq < qmin) qmin = nq;
+      }
+      kappa = qmin > 0.0 ? 1.0 / qmin : INFINITY;
+    }
+    out[site] = kappa;
+  }
+  return 0;
+}
+
+/* Per timeslice, the sum over the sites of one parity of the site violation
+ * tr[Delta(x) Delta(x)^dagger] of Sec. 2 (Delta from the A_mu of the links;
+ * maximally Abelian gauge: from X(x)) on the current links.  TEST
+ * INFRASTRUCTURE: the sweeps' fused estimate of theta adds exactly these over
+ * its two half-sweeps, each on the field that half-sweep started from.
+ * out_t: N_t doubles. */
+int orc_parity_violation(const int32_t dims[4], const double *links, int gauge, int parity, double *out_t) {
+  if (check_dims(dims)) return -1;
+  const lattice l = make_lattice(dims);
+  double *sv = (double *)malloc(sizeof(double) * (size_t)l.vol);
+  if (!sv) return -2;
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < l.vol; x++) {
+    if (site_parity(&l, x) != (parity & 1)) {
+      sv[x] = 0.0;
+    } else if (gauge == ORC_MAG) {
+      su3 X = mag_X(&l, links, x);
+      su3 d = gauge_field_A(&X);
+      double v = 0.0;
+      for (int r = 0; r < NC; r++)
+        for (int c = 0; c < NC; c++) v += d.e[r][c].re * d.e[r][c].re + d.e[r][c].im * d.e[r][c].im;
+      sv[x] = v;
+    } else {
+      sv[x] = violation_norm(&l, links, x, gauge);
+    }
+  }
+  for (int64_t t = 0; t < l.n[0]; t++) {
+    double s = 0.0;
+    for (int64_t k = 0; k < l.vol_s; k++) s += sv[t * l.vol_s + k];
+    out_t[t] = s;
+  }
+  free(sv);
+  return 0;
 }
 
 /* K(x) of the current links (18 doubles) */

@@ -233,6 +233,10 @@ struct lgt_ctx {
   cudaGraphExec_t loop_exec[2];
   int loop_sweep_launches[2];      // sweep kernel launches in one chunk of each loop
   int *h_err;                      // pinned copy of the workspace's error word
+  // fault injection for the streaming launches of lgt_sweep / lgt_half_sweep
+  // (lgt_inject_stream_stall; cleared by lgt_load)
+  unsigned long long inj_wait_ns;
+  unsigned inj_skip;
 };
 
 static void resolve_events(lgt_ctx *c);
@@ -340,6 +344,8 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
     src = c->stage;
   }
   LGT_CUDA(cudaMemsetAsync(c->ws.err, 0, sizeof(int), c->stream));
+  c->inj_wait_ns = 0;
+  c->inj_skip = 0;
   LGT_CUDA(cudaMemsetAsync(c->ws.active, 1, (size_t)g.nt, c->stream));
   LGT_CUDA(launch_ingest(FMT_F64, g, src, c->u64, c->ws.err, c->stream));
   c->stats.launches++;
@@ -550,7 +556,10 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
   const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
   const int reunit_every = c->phase == 0 ? c->prm.reunit_every : 0;
   int launches = 0;
-  LGT_CUDA(launch_half_sweeps(fmt, c->g, links, G, c->ws, c->cfg, first_parity, n_half, c->sweep_index, c->sweeps_bulk,
+  SweepCfg sc = c->cfg;
+  sc.stream_wait_ns = c->inj_wait_ns;
+  sc.stream_skip = c->inj_skip;
+  LGT_CUDA(launch_half_sweeps(fmt, c->g, links, G, c->ws, sc, first_parity, n_half, c->sweep_index, c->sweeps_bulk,
                               reunit_every, use_mask, lc, c->stream, anch ? c->k0 : nullptr, nullptr, &launches));
   c->last_sites = lgt_cfg_sites(lc);
   const int64_t done = (first_parity + n_half) / 2;  // sweeps whose odd half ran
@@ -668,6 +677,47 @@ extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *thet
     LGT_CUDA(cudaMemcpyAsync(theta_t, ctx->ws.slice_theta, nb, cudaMemcpyDeviceToHost, ctx->stream));
   }
   return sync_stream(ctx);
+}
+
+extern "C" lgt_status lgt_estimate(lgt_ctx *ctx, double *F, double *theta, double *F_t, double *theta_t) {
+  if (!ctx) {
+    lgt_set_error("lgt_estimate: NULL context");
+    return LGT_EINVAL;
+  }
+  Meas m;
+  lgt_status st = estimate(ctx, -1.0, &m);
+  if (st != LGT_OK) return st;
+  if (F) *F = m.F;
+  if (theta) *theta = m.theta;
+  if (F_t || theta_t) {
+    // per-slice sums (parity-0 Re tr K, both parities' tr Delta^2), normalised per slice
+    const int nt = ctx->g.nt;
+    std::vector<double> sl((size_t)nt * 2);
+    LGT_CUDA(cudaMemcpyAsync(sl.data(), ctx->ws.fused_slice, sizeof(double) * sl.size(), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    st = sync_stream(ctx);
+    if (st != LGT_OK) return st;
+    const double vs = 2.0 * (double)ctx->g.vs_half, nd = ctx->cfg.gauge == GAUGE_COULOMB ? 3.0 : 4.0;
+    for (int t = 0; t < nt; t++) {
+      if (F_t) F_t[t] = sl[2 * t] / (3.0 * nd * vs);
+      if (theta_t) theta_t[t] = sl[2 * t + 1] / (3.0 * vs);
+    }
+  }
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_inject_stream_stall(lgt_ctx *ctx, uint64_t wait_ns, uint32_t skip_items) {
+  if (!ctx) {
+    lgt_set_error("lgt_inject_stream_stall: NULL context");
+    return LGT_EINVAL;
+  }
+  if (wait_ns > LGT_STREAM_WAIT_NS) {
+    lgt_set_error("lgt_inject_stream_stall: wait_ns above the built-in bound of %llu ns", LGT_STREAM_WAIT_NS);
+    return LGT_EINVAL;
+  }
+  ctx->inj_wait_ns = wait_ns;
+  ctx->inj_skip = skip_items;
+  return LGT_OK;
 }
 
 // --------------------------------------------------------------- promotion

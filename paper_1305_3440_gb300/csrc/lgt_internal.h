@@ -110,6 +110,11 @@ struct SweepArgs {
   // snake order: a half-sweep of parity 1 visits the (slice, tile) list from
   // its end, so it starts on the links the parity-0 half-sweep touched last
   int snake;
+  // streaming launches: the bound on one wait, and the first ticket (0 in a
+  // normal run; > 0 leaves the first items of the launch undone, which makes the
+  // bounded waits expire: fault injection for tests)
+  unsigned long long stream_wait_ns;
+  unsigned stream_skip;
 };
 
 // Arguments of one lattice's exact measurement.
@@ -168,6 +173,9 @@ struct SweepCfg {
   unsigned long long seed;
   int transform_temporal;
   double beta = 0.0;         // ALGO_SA: inverse temperature of the sweep
+  // streaming launches: wait bound (0: LGT_STREAM_WAIT_NS) and first ticket (see SweepArgs)
+  unsigned long long stream_wait_ns = 0;
+  unsigned stream_skip = 0;
 };
 
 // Single-lattice half-sweep kernels, one per (format, gauge, algorithm,

@@ -106,6 +106,8 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
     return (v && v[0] == '0') ? 0 : 1;
   }();
   a->snake = snake;
+  a->stream_wait_ns = c.stream_wait_ns ? c.stream_wait_ns : LGT_STREAM_WAIT_NS;
+  a->stream_skip = c.stream_skip;
 }
 
 // SMs of the current device, looked up once per device ordinal

@@ -416,8 +416,8 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
 // of smaller tickets, which running blocks hold; a block waits only while it
 // holds no unfinished item of its own, so the launch cannot deadlock, however
 // many of its blocks are resident.  Every wait is bounded in time: after
-// LGT_STREAM_WAIT_NS the block raises the abort flag and bit 1 of the error
-// word, and every block ends.
+// stream_wait_ns (LGT_STREAM_WAIT_NS unless a test sets it) the block raises
+// the abort flag and bit 1 of the error word, and every block ends.
 __device__ __forceinline__ unsigned long long lgt_clock_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -458,12 +458,13 @@ __device__ __forceinline__ bool stream_ready(const unsigned *done, const StreamI
   return a >= need && b >= need && c >= need;
 }
 // bounded wait for stream_ready (thread 0 of a block); false: the launch gives up
-__device__ __forceinline__ bool stream_wait(unsigned *ctr, int *err, const StreamItem &it, int items_x, int nt) {
+__device__ __forceinline__ bool stream_wait(unsigned *ctr, int *err, const StreamItem &it, int items_x, int nt,
+                                            unsigned long long limit_ns) {
   const unsigned long long t0 = lgt_clock_ns();
   for (unsigned k = 0; k < (1u << 26); k++) {
     if (stream_ready(ctr + 2, it, items_x, nt)) return true;
     if (lgt_ld_acquire(ctr + 1)) return false;  // another block gave up
-    if (lgt_clock_ns() - t0 > LGT_STREAM_WAIT_NS) break;
+    if (lgt_clock_ns() - t0 > limit_ns) break;
     __nanosleep(128);
   }
   atomicExch(ctr + 1, 1u);
@@ -529,7 +530,7 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
     }
     __syncthreads();
   };
-  share(tid == 0 ? atomicAdd(ctr, 1u) : 0u);
+  share(tid == 0 ? atomicAdd(ctr, 1u) + in.stream_skip : 0u);
   unsigned cur = s_next;
   int staged = s_ready, buf = 0;  // staged: the current tile's loads are issued
   if (cur < total && staged) {
@@ -549,14 +550,14 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
     a.reunit = in.reunit_every > 0 ? (int)(((count0 + sw + 1) % in.reunit_every) == 0) : in.reunit;
     const bool on = !(in.active && !in.active[it.t]);
     unsigned ticket = 0;
-    if (tid == 0) ticket = atomicAdd(ctr, 1u);  // the next item's ticket, used at the last tile
+    if (tid == 0) ticket = atomicAdd(ctr, 1u) + in.stream_skip;  // the next item's ticket, used at the last tile
     unsigned nxt = 0;
     int nxt_ready = 0;
     // one copy of the site update: unrolled, the body would outgrow the instruction cache
 #pragma unroll 1
     for (int u = 0; u < ntl; u++) {
       if (!staged) {  // first tile of an item that was not ready: wait, then load it
-        if (tid == 0) s_go = stream_wait(ctr, in.err, it, items_x, nt) ? 1 : 0;
+        if (tid == 0) s_go = stream_wait(ctr, in.err, it, items_x, nt, in.stream_wait_ns) ? 1 : 0;
         __syncthreads();
         if (!s_go) {  // uniform: every thread read the same flag
           abort = true;

@@ -87,6 +87,7 @@ _sigs = {
     "lgt_half_sweep": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lgt_measure": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)], ctypes.c_int),
     "lgt_measure_slices": ([_vp, _vp, _vp], ctypes.c_int),
+    "lgt_estimate": ([_vp, _P(ctypes.c_double), _P(ctypes.c_double), _vp, _vp], ctypes.c_int),
     "lgt_fix": ([_vp, _P(lgt_result)], ctypes.c_int),
     "lgt_promote": ([_vp], ctypes.c_int),
     "lgt_get_links": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
@@ -95,6 +96,7 @@ _sigs = {
     "lgt_load": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "lgt_get_stats": ([_vp, _P(lgt_stats)], ctypes.c_int),
     "lgt_destroy": ([_vp], None),
+    "lgt_inject_stream_stall": ([_vp, ctypes.c_uint64, ctypes.c_uint32], ctypes.c_int),
     "lgt_measure_noalloc": ([_P(ctypes.c_int32), _vp, _vp, _vp], ctypes.c_int),
     "lgt_server_create": ([ctypes.c_size_t, ctypes.c_int, _P(_vp)], ctypes.c_int),
     "lgt_submit": ([_vp, _P(lgt_params), _vp, _P(ctypes.c_uint64)], ctypes.c_int),
@@ -194,6 +196,20 @@ def lgt_measure_slices(ctx, nt: int):
     th_t = np.zeros(int(nt))
     _check(_lib.lgt_measure_slices(ctx, F_t.ctypes.data, th_t.ctypes.data))
     return F_t, th_t
+
+
+def lgt_estimate(ctx, nt: int):
+    """(F, theta, F_t, theta_t) of the sweeps' fused estimate of the last full sweep."""
+    F, th = ctypes.c_double(), ctypes.c_double()
+    F_t = np.zeros(int(nt))
+    th_t = np.zeros(int(nt))
+    _check(_lib.lgt_estimate(ctx, ctypes.byref(F), ctypes.byref(th), F_t.ctypes.data, th_t.ctypes.data))
+    return F.value, th.value, F_t, th_t
+
+
+def lgt_inject_stream_stall(ctx, wait_ns: int, skip_items: int) -> None:
+    """Test support: bounded-wait fault injection for streaming launches (see lgt.h)."""
+    _check(_lib.lgt_inject_stream_stall(ctx, int(wait_ns), int(skip_items)))
 
 
 def lgt_fix(ctx):

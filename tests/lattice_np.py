@@ -134,3 +134,51 @@ def su2_matrices(quats):
     m[:, 1, 0] = -r2 + 1j * r1
     m[:, 1, 1] = r0 - 1j * r3
     return m
+
+
+# ----------------------------------------------- FP32 parity bounds
+U_FP32 = 2.0 ** -24  # unit roundoff of binary32
+
+
+def parity_field(dims):
+    t, x3, x2, x1 = np.indices(tuple(dims))
+    return (t + x3 + x2 + x1) & 1
+
+
+def link_endpoint(site_values, parity):
+    """Per link (z, mu): the value at the link's endpoint of the given parity --
+    z if z has that parity, else z + mu.  Shape (N_t, N_3, N_2, N_1, 4)."""
+    par = parity_field(site_values.shape)
+    return np.stack([np.where(par == parity, site_values, shift(site_values, mu, 1)) for mu in range(4)], axis=-1)
+
+
+def fp32_half_sweep_bound(kappa, parity, c):
+    """Per link: c u kappa(w), w the link's endpoint of the updated parity (the
+    site whose update wrote it)."""
+    return c * U_FP32 * link_endpoint(kappa, parity)
+
+
+def fp32_sweep_bound(kappa_even, kappa_odd, c=16.0, a=2.0):
+    """Per link, the first-order FP32 error of one full sweep (even half, then odd
+    half) from the conditioning kappa of every site update (the oracle's, on the
+    field each half starts from).  A site update turns an error d of its K(x) into
+    an error ~ a d kappa of g (a = 2 bounds the overrelaxation factor omega < 2 and
+    the doubled angle of a stochastic-relaxation square); its own K carries the
+    rounding eps = 8u of 8 FP32 links and 7 sums (root-sum-square), so c = a eps /
+    u = 16.  The odd site y also reads the 8 links the even half wrote, each off
+    by ~ c u kappa of its writer: its K is off by eps (1 + a nu(y)), nu the
+    root-sum-square of the 8 neighbours' kappa.  A link is written once in each
+    half, by its even endpoint x and its odd endpoint y:
+        B = c u (kappa(x) + kappa(y) (1 + a nu(y))).
+    Shape (N_t, N_3, N_2, N_1, 4)."""
+    par = parity_field(kappa_even.shape)
+    kap = np.where(par == 0, kappa_even, kappa_odd)
+    nu = np.sqrt(sum(shift(kap, mu, s) ** 2 for mu in range(4) for s in (1, -1)))
+    return c * U_FP32 * (link_endpoint(kap, 0) + link_endpoint(kap, 1) * (1 + a * link_endpoint(nu, 1)))
+
+
+def check_fp32_bound(err, bound, floor=5e-6):
+    """Every entry within max(floor, its link's bound); returns (worst err / allowed,
+    entries above the floor, links whose bound exceeds the floor)."""
+    allowed = np.maximum(floor, bound)[..., None, None]
+    return float((err / allowed).max()), int((err > floor).sum()), int((bound > floor).sum())

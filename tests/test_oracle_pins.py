@@ -760,3 +760,123 @@ def test_mag_annealing_is_rejected():
     U = synth.field((2, 2, 2, 2), 0.3, 1)
     with pytest.raises(Exception):
         O.sa_sweeps(U, 1, 1.0, 2.0, gauge=O.MAG)
+
+
+# ------------------------------- conditioning of a site update (test support)
+def test_site_conditioning_is_the_smallest_subgroup_maximum():
+    """Landau and Coulomb: kappa = 1/min_s |q_s|.  At omega = 1 each step reaches
+    its block's maximum Re tr(R_s W_s) = 2|q_s| (the closed form's value, pinned
+    against brute force above), so kappa = 2 / min_s of that value: every site of
+    both parities of a rough field."""
+    dims = (4, 4, 2, 6)
+    U = synth.field(dims, 0.6, 71)
+    for gauge in (O.LANDAU, O.COULOMB):
+        for p in (0, 1):
+            kap = O.site_conditioning(U, p, gauge=gauge, omega=1.0)
+            for site in range(int(np.prod(dims))):
+                c = coords_of(site, dims)
+                if parity_of(site, dims) != p:
+                    assert np.isnan(kap[c])
+                    continue
+                g, W, R = O.local_update(O.gather_K(U, site, gauge), O.OR, 1.0)
+                vals = [np.real(np.trace((R[s] @ W[s])[np.ix_([i, j], [i, j])])) for s, (i, j) in enumerate(SUBGROUPS)]
+                assert abs(kap[c] - 2 / min(vals)) < 1e-12 * kap[c]
+
+
+def test_landau_conditioning_bounds_the_step_sensitivity():
+    """The first-order change of the closed-form element r = (q0, -q)/|q| is at
+    most |dq|/|q| (finite differences of the oracle's maximum on perturbed blocks;
+    the ratio reaches 1 for perturbations across q)."""
+    rng = np.random.default_rng(72)
+    worst = 0.0
+    for _ in range(400):
+        M = (rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))) * rng.uniform(0.05, 3)
+        d = (rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))) * 1e-8
+        q = lambda m: np.array([np.real(m[0, 0] + m[1, 1]), np.imag(m[0, 1] + m[1, 0]),
+                                np.real(m[0, 1] - m[1, 0]), np.imag(m[0, 0] - m[1, 1])]) / 2
+        dr = np.linalg.norm(O.su2_maximum(M + d) - O.su2_maximum(M))
+        ratio = dr / (np.linalg.norm(q(M + d) - q(M)) / np.linalg.norm(q(M)))
+        worst = max(worst, ratio)
+    assert 0.5 < worst < 1 + 1e-5
+
+
+def _mag_chain_kappa(U, site, omega):
+    """kappa of a maximally Abelian site update, from the pinned subgroup steps
+    composed in numpy (as test_mag_site_update_composes_the_subgroup_steps)."""
+    fwd, bwd = _site_links(U, site)
+    kap = 0.0
+    for s, (i, j) in enumerate([(0, 1), (0, 2), (1, 2)]):
+        v, r = O.mag_subgroup(np.concatenate([fwd, bwd]), s)
+        nv = np.linalg.norm(v)
+        kap += np.sqrt(2 / (nv * (nv + v[2])))
+        q = np.array([1 - omega + omega * r[0], omega * r[1], omega * r[2], omega * r[3]])
+        q /= np.linalg.norm(q)
+        R = np.eye(3, dtype=np.complex128)
+        R[np.ix_([i, j], [i, j])] = su2_quaternion_matrix(q)
+        fwd = R @ fwd
+        bwd = bwd @ dag(R)
+    return kap
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.7])
+def test_mag_conditioning_sums_the_steps(omega):
+    """Maximally Abelian gauge: kappa = sum_s sqrt(2/(|v_s|(|v_s| + v_s3))), v_s of
+    each step on the links as the steps before left them."""
+    U = synth.field((4, 4, 2, 4), 0.6, 73)
+    for p in (0, 1):
+        kap = O.site_conditioning(U, p, gauge=O.MAG, omega=omega)
+        for site in (0, 1, 5, 37, 90, 127):
+            c = coords_of(site, U.shape[:4])
+            if parity_of(site, U.shape[:4]) == p:
+                assert abs(kap[c] - _mag_chain_kappa(U, site, omega)) < 1e-12 * kap[c]
+
+
+def test_mag_conditioning_is_twice_the_derivative_of_the_maximum():
+    """The term sqrt(2/(|v|(|v| + v_3))) is twice the spectral norm of the
+    derivative of the maximiser r(v) (the oracle's, by finite differences of the
+    links: |dr| <= term/2 |dv| to first order, with equality in the worst
+    direction), including near v = -|v| e_3 where the rotation axis turns fast."""
+    rng = np.random.default_rng(74)
+    worst = 0.0
+    base = synth.field((2, 2, 2, 2), 0.9, 75).reshape(-1, 3, 3)
+    for k in range(300):
+        L8 = base[rng.choice(len(base), 8, replace=False)].copy()
+        if k % 3 == 0:  # steer v towards -e_3: swap the first two rows of the forward links
+            L8[:4] = L8[:4][:, [1, 0, 2], :]
+        v, r = O.mag_subgroup(L8, 0)
+        nv = np.linalg.norm(v)
+        term = np.sqrt(2 / (nv * (nv + v[2])))
+        d = (rng.normal(size=L8.shape) + 1j * rng.normal(size=L8.shape)) * 1e-9
+        v2, r2 = O.mag_subgroup(L8 + d, 0)
+        worst = max(worst, np.linalg.norm(r2 - r) / (term / 2 * np.linalg.norm(v2 - v)))
+    assert 0.3 < worst < 1 + 1e-4
+
+
+# ------------------------------------- the sweeps' fused estimate (test support)
+@pytest.mark.parametrize("gauge", [O.LANDAU, O.COULOMB])
+def test_parity_violation_is_the_violation_of_K(gauge):
+    """The per-parity sums of tr[Delta Delta^dagger] (Delta from the A_mu, Sec. 2)
+    equal those of the traceless part of (K - K^dagger)/(2i), K(x) the site's
+    local matrix (the identity the sweep kernels' estimate relies on; numpy from
+    gather_K), and the two parities add up to the measured theta."""
+    dims = (4, 2, 4, 6)
+    U = synth.field(dims, 0.6, 76)
+    vs = dims[1] * dims[2] * dims[3]
+    m = O.measure(U, gauge)
+    both = np.zeros(dims[0])
+    for p in (0, 1):
+        got = O.parity_violation(U, p, gauge)
+        expect = np.zeros(dims[0])
+        for site in range(int(np.prod(dims))):
+            if parity_of(site, dims) != p:
+                continue
+            K = O.gather_K(U, site, gauge)
+            D = (K - dag(K)) / 2j
+            D -= np.eye(3) * np.trace(D) / 3
+            expect[coords_of(site, dims)[0]] += np.sum(np.abs(D) ** 2)
+        assert np.allclose(got, expect, rtol=1e-12, atol=0)
+        both += got
+    if gauge == O.COULOMB:
+        assert np.allclose(both / (3 * vs), m["theta_t"], rtol=1e-12, atol=0)
+    else:
+        assert abs(both.sum() / (3 * np.prod(dims)) - m["theta"]) < 1e-12 * m["theta"]

@@ -4,13 +4,15 @@ Some callers of this library cannot allocate device memory -- an application
 that hands out every byte of HBM through its own memory plan, or code that must
 measure where no allocation may happen -- so they cannot create a context.  This
 test checks that the no-allocation variant, called through the C ABI on links
-in device memory, gives what the context-based lgt_measure / lgt_measure_slices
-give, on two calls in a row (the shared scratch keeps the previous call's
-contents).  The file is named to be collected last.
+in device memory, gives what the FP64 oracle's measurement gives and what the
+context-based lgt_measure / lgt_measure_slices give, on two calls in a row (the
+shared scratch keeps the previous call's contents).  The file is named to be
+collected last.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1305_3440_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -39,6 +41,8 @@ def test_no_alloc_measure_matches_context_measure(lgt, dims):
         Ft, tht = lgt.lgt_measure_slices(ctx, nt)
     finally:
         lgt.lgt_destroy(ctx)
+    ref = O.measure(U)
+    ref_c = O.measure(U, O.COULOMB)
     stream = torch.cuda.Stream()
     out = torch.empty(8 + 2 * nt, dtype=torch.float64, device="cuda")
     for call in range(2):
@@ -52,6 +56,12 @@ def test_no_alloc_measure_matches_context_measure(lgt, dims):
         assert np.allclose(o[8:8 + nt], Ft, rtol=0, atol=1e-13)
         assert np.allclose(o[8 + nt:], tht, rtol=1e-13, atol=0)
         assert abs(o[4] - tht.max()) < 1e-13 * tht.max() and abs(o[3] - Ft.mean()) < 1e-13
+        assert abs(o[5] - tht.mean()) < 1e-13 * tht.mean() and o[6] == 0.0 and o[7] == 0.0
+        # the oracle on the same field: Landau F, theta, plaquette; Coulomb F_t, theta_t
+        assert abs(o[0] - ref["F"]) < 1e-13 and abs(o[2] - ref["plaq"]) < 1e-13
+        assert abs(o[1] - ref["theta"]) < 1e-13 * ref["theta"]
+        assert np.allclose(o[8:8 + nt], ref_c["F_t"], rtol=0, atol=1e-13)
+        assert np.allclose(o[8 + nt:], ref_c["theta_t"], rtol=1e-13, atol=0)
 
 
 def test_no_alloc_measure_rejects_sizes_beyond_its_scratch(lgt):
