@@ -142,6 +142,12 @@ typedef struct {
   int32_t reserved;           /* must be 0 */
   double sa_beta0, sa_beta1;  /* inverse temperature of the first and the last annealing sweep,
                                  0 < sa_beta0 <= sa_beta1 (geometric in between) */
+  double omega_late;          /* omega schedule (OR): the relaxation sweeps before promotion (all
+                                 sweeps when bulk = LGT_FP64) run at omega until a check of theta
+                                 (every check_every sweeps, on the sweeps' estimate) finds theta <
+                                 theta_omega, and at omega_late from then on; [1, 2), 0: no
+                                 schedule.  Sweeps after promotion run at omega_polish. */
+  double theta_omega;         /* switch point of the omega schedule, >= 0 */
 } lgt_params;
 
 typedef struct {
@@ -195,7 +201,7 @@ typedef struct {
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,
  * transform_temporal 1, block_size 0, launch_config 0, polish LGT_POLISH_ANCHOR, omega_polish 1.3,
- * sa_sweeps 0, sa_beta0 1, sa_beta1 100
+ * sa_sweeps 0, sa_beta0 1, sa_beta1 100, omega_late 0 (no omega schedule), theta_omega 0
  * (after promotion the residual is short-wavelength noise, which a smaller
  * omega removes fastest).  dims are zeroed.  Never fails for p != NULL. */
 LGT_API lgt_status lgt_params_default(lgt_params *p);

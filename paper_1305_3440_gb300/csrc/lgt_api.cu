@@ -85,6 +85,8 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->sa_beta0 = 1.0;
   p->sa_beta1 = 100.0;
   p->omega_polish = 1.3;
+  p->omega_late = 0.0;
+  p->theta_omega = 0.0;
   return LGT_OK;
 }
 
@@ -125,6 +127,14 @@ lgt_status lgt_validate_params(const lgt_params *p) {
   }
   if (p->algo == LGT_OR && p->omega_polish != 0.0 && !(p->omega_polish >= 1.0 && p->omega_polish < 2.0)) {
     lgt_set_error("omega_polish = %g outside [1, 2) (0: same as omega)", p->omega_polish);
+    return LGT_EINVAL;
+  }
+  if (p->omega_late != 0.0 && !(p->omega_late >= 1.0 && p->omega_late < 2.0)) {
+    lgt_set_error("omega_late = %g outside [1, 2) (0: no omega schedule)", p->omega_late);
+    return LGT_EINVAL;
+  }
+  if (!(p->theta_omega >= 0.0)) {
+    lgt_set_error("theta_omega must be >= 0");
     return LGT_EINVAL;
   }
   if (p->algo == LGT_SR && !(p->p >= 0.0 && p->p <= 1.0)) {
@@ -233,6 +243,7 @@ struct lgt_ctx {
   cudaGraphExec_t loop_exec[2];
   int loop_sweep_launches[2];      // sweep kernel launches in one chunk of each loop
   int *h_err;                      // pinned copy of the workspace's error word
+  int omega_switched;              // the omega schedule has moved to omega_late
   // fault injection for the streaming launches of lgt_sweep / lgt_half_sweep
   // (lgt_inject_stream_stall; cleared by lgt_load)
   unsigned long long inj_wait_ns;
@@ -364,7 +375,8 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
   c->anchored = c->d_dirty = 0;
   c->sa_pending = c->prm.sa_sweeps > 0;
   c->active_slices = g.nt;
-  c->cfg.omega = c->prm.omega;  // omega_polish takes over at promotion
+  c->cfg.omega = c->prm.omega;  // omega_late may take over (omega schedule), omega_polish at promotion
+  c->omega_switched = 0;
   c->sweeps_bulk = c->sweeps_fp64 = 0;
   c->sweep_index = c->prm.sweep_offset;
   return LGT_OK;
@@ -647,6 +659,18 @@ static lgt_status estimate(lgt_ctx *c, double coulomb_target, Meas *m) {
   return LGT_OK;
 }
 
+// Omega schedule: the relaxation sweeps before promotion (every sweep of an
+// FP64 run) switch to omega_late at the first check with theta < theta_omega.
+static bool omega_schedule_open(const lgt_ctx *c) {
+  return c->prm.omega_late != 0.0 && !c->omega_switched && (c->phase == 0 || c->prm.bulk == LGT_FP64);
+}
+static void omega_check(lgt_ctx *c, double theta) {
+  if (omega_schedule_open(c) && theta < c->prm.theta_omega) {
+    c->cfg.omega = c->prm.omega_late;
+    c->omega_switched = 1;
+  }
+}
+
 extern "C" lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double *plaq) {
   if (!ctx) {
     lgt_set_error("lgt_measure: NULL context");
@@ -834,6 +858,10 @@ static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64
   L.active = c->active_slices;
   L.iters = 0;
   L.max_iters = (int)(*remaining / k);
+  L.omega = c->cfg.omega;
+  L.omega_late = c->prm.omega_late;
+  L.theta_omega = c->prm.theta_omega;
+  L.omega_switch = omega_schedule_open(c) ? 1 : 0;
   if (c->phase == 3) {  // end the launch where the anchor is due for renewal
     const int64_t left = LGT_REANCHOR_SWEEPS - c->anchor_sweeps;
     const int64_t cap = left > 0 ? (left + k - 1) / k : 1;
@@ -853,6 +881,10 @@ static lgt_status run_loop(lgt_ctx *c, int slot, double *best, int *stall, int64
   if (kind == 0) c->sweeps_bulk += n;
   else c->sweeps_fp64 += n;
   *remaining = L.remaining;
+  if (L.omega_switch == 0 && omega_schedule_open(c)) {  // the device loop switched omega
+    c->cfg.omega = L.omega;
+    c->omega_switched = 1;
+  }
   if (best) *best = L.best;
   if (stall) *stall = L.stall;
   c->last_sites = lgt_cfg_sites(lc);
@@ -940,6 +972,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
     const double target = c->prm.theta_switch;
     st = measure(c, 0, coulomb ? target : -1.0, &m);
     if (st != LGT_OK) return st;
+    omega_check(c, m.theta);
     double best = m.theta;
     int stall = 0;
     while (m.theta >= target && remaining > 0 && stall < LGT_STALL_CHECKS) {
@@ -954,6 +987,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
       remaining -= n;
       st = estimate(c, coulomb ? target : -1.0, &m);
       if (st != LGT_OK) return st;
+      omega_check(c, m.theta);
       if (m.theta < best) {
         best = m.theta;
         stall = 0;
@@ -978,6 +1012,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
   } else {
     st = measure(c, 0, coulomb ? tol : -1.0, &m);
     if (st != LGT_OK) return st;
+    omega_check(c, m.theta);
   }
   while (m.theta >= tol && remaining > 0) {
     st = anchor_refresh(c);
@@ -992,6 +1027,7 @@ extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
       remaining -= n;
       st = estimate(c, coulomb ? tol : -1.0, &m);
       if (st != LGT_OK) return st;
+      omega_check(c, m.theta);
     }
     certified = false;
     if (m.theta < tol) {  // the estimate says converged: certify with the exact measurement

@@ -78,6 +78,11 @@ struct LoopState {
   int bulk;                  // 1: bulk rules (target, stall), 0: polish rules (target)
   int active;                // slices the next sweeps update
   int iters, max_iters;      // chunks run by this launch, and their cap
+  // omega schedule: the sweeps' OR parameter (read by the sweep kernels), and,
+  // while omega_switch is set, the check that moves it to omega_late once the
+  // estimate drops below theta_omega
+  double omega, omega_late, theta_omega;
+  int omega_switch;
 };
 
 struct SweepArgs {
@@ -85,7 +90,7 @@ struct SweepArgs {
   void *links;
   void *G;
   const void *aux;  // anchored polish: K0
-  // device loop: sweep = loop->sweep + sweep, reunitarise when
+  // device loop: sweep = loop->sweep + sweep, omega = loop->omega, reunitarise when
   // (loop->count + sweep + 1) % reunit_every == 0 (sweep holds the offset in the chunk)
   const LoopState *loop;
 

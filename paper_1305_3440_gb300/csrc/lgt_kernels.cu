@@ -625,6 +625,10 @@ __global__ void k_loop_decide(LoopState *L, const double *tot, int gauge, int k,
   L->remaining -= k;
   L->iters += 1;
   L->theta = theta;
+  if (L->omega_switch && theta < L->theta_omega) {  // omega schedule: the later sweeps at omega_late
+    L->omega = L->omega_late;
+    L->omega_switch = 0;
+  }
   bool go = theta >= L->target;
   if (L->bulk) {
     if (theta < L->best) {

@@ -79,6 +79,7 @@ struct Job {
   uint64_t sweep_index = 0;
   double best = 0.0;
   int stall = 0;
+  bool omega_switched = false;  // omega schedule: the sweeps run at omega_late
   bool measure_only = true;  // next tick measures without sweeping
   bool certify = false;      // that measurement certifies convergence (with the plaquette)
   int nthis = 0;             // sweeps in the current tick
@@ -610,6 +611,13 @@ void worker_main(lgt_server *s) {
           j->sweep_index += (uint64_t)j->nthis;
         }
         j->measure_only = false;
+        // omega schedule, as lgt_fix: the sweeps before promotion (every sweep of
+        // an FP64 job) move to omega_late at the first check below theta_omega
+        if (j->prm.omega_late != 0.0 && !j->omega_switched && (j->phase == 0 || j->prm.bulk == LGT_FP64) &&
+            theta < j->prm.theta_omega) {
+          j->cfg.omega = j->prm.omega_late;
+          j->omega_switched = true;
+        }
         const bool certified = exact && j->certify;
         j->certify = false;
         if (j->phase == 0) {

@@ -104,12 +104,14 @@ __device__ __forceinline__ void sweep_block_tile(const SweepArgs &a, int p, int 
   }
 }
 
-// A device loop's sweep kernels take the sweep number (SR counter) and the
-// reunitarisation flag from the loop state (see LoopState).
+// A device loop's sweep kernels take the sweep number (SR counter), the OR
+// parameter (omega schedule) and the reunitarisation flag from the loop state
+// (see LoopState).
 __device__ __forceinline__ SweepArgs resolve_loop(const SweepArgs &in) {
   SweepArgs a = in;
   if (a.loop) {
     const unsigned long long off = a.sweep;
+    a.omega = a.loop->omega;
     a.sweep = a.loop->sweep + off;
     a.reunit = a.reunit_every > 0 && ((a.loop->count + (long long)off + 1) % a.reunit_every) == 0;
   }
@@ -490,9 +492,11 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
   // (with a device loop, in.sweep is the launch's offset in the chunk)
   unsigned long long sweep0 = in.sweep;
   long long count0 = in.count_base;
+  double omega = in.omega;
   if (in.loop) {
     sweep0 = in.loop->sweep + in.sweep;
     count0 = in.loop->count + (long long)in.sweep;
+    omega = in.loop->omega;
   }
   // stage tile `tile` of slice it.t in half-sweep it.h
   auto issue = [&](const StreamItem &it, int tile, int buf) {
@@ -546,6 +550,7 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
     const int p = (p0 + it.h) & 1;
     const int sw = (p0 + it.h) >> 1;  // sweep of the launch
     SweepArgs a = in;
+    a.omega = omega;
     a.sweep = sweep0 + (unsigned long long)sw;
     a.reunit = in.reunit_every > 0 ? (int)(((count0 + sw + 1) % in.reunit_every) == 0) : in.reunit;
     const bool on = !(in.active && !in.active[it.t]);

@@ -40,7 +40,7 @@ class lgt_params(ctypes.Structure):
                 ("reunit_every", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("polish", ctypes.c_int32), ("launch_config", ctypes.c_int32), ("omega_polish", ctypes.c_double),
                 ("sa_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sa_beta0", ctypes.c_double),
-                ("sa_beta1", ctypes.c_double)]
+                ("sa_beta1", ctypes.c_double), ("omega_late", ctypes.c_double), ("theta_omega", ctypes.c_double)]
 
 
 class lgt_result(ctypes.Structure):

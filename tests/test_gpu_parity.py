@@ -6,6 +6,8 @@ entry in FP64 and 5e-6 on FP32 link storage; converged runs agree in F to
 a global gauge rotation or another Gribov copy changes them, so links are only
 compared after a fixed number of sweeps).
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -818,6 +820,69 @@ def test_streaming_wait_times_out_and_the_context_recovers(lgt, skip):
     finally:
         lgt.lgt_destroy(ctx)
     assert np.array_equal(got, fresh)
+
+
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_omega_schedule_switches_at_a_check(lgt, graphs, monkeypatch):
+    """The omega schedule (Sec. 3.1 overrelaxation with a late omega): lgt_fix
+    sweeps at omega until a check finds the estimate below theta_omega, then at
+    omega_late.  theta_omega sits between theta of the input and theta after the
+    first chunk of 10 sweeps, so the result of 20 sweeps is 10 oracle sweeps at
+    omega = 1.7 and 10 at omega_late = 1.2 (FP64, 1e-11), whether the chunks run
+    as the device loop or from the host (LGT_FIX_GRAPHS=0)."""
+    monkeypatch.setenv("LGT_FIX_GRAPHS", graphs)
+    dims = (4, 6, 4, 8)
+    U = synth.field(dims, 0.5, 25)
+    th0 = O.measure(U)["theta"]
+    ref = U.copy()
+    O.sweeps(ref, 10, omega=1.7)
+    th10 = O.measure(ref)["theta"]
+    switch = np.sqrt(th0 * th10)
+    p = lgt.lgt_params_default(dims=dims, omega=1.7, omega_late=1.2, theta_omega=switch, max_sweeps=20)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        got = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_ENOTCONV and res.sweeps_fp64 == 20
+    O.sweeps(ref, 10, omega=1.2, sweep0=10)
+    assert np.abs(got - ref).max() < 1e-11
+    late = U.copy()
+    O.sweeps(late, 20, omega=1.2)
+    assert np.abs(got - late).max() > 1e-6  # the first chunk did run at omega = 1.7
+
+
+@pytest.mark.parametrize("bulk", ["fp64", "fp32_12"])
+def test_omega_schedule_converges_to_the_oracle_F(lgt, bulk):
+    """A fix with the schedule (omega 1.5, then 1.1 below theta 1e-4) ends at the
+    oracle's converged F (1e-10; the oracle relaxes at a fixed omega = 1.7) and the
+    oracle certifies theta < 1e-14 on the returned field; served alike."""
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 0.3, 1)
+    ref = U.copy()
+    r = O.fix(ref, omega=1.7, tol=1e-14, max_sweeps=1000)
+    kw = dict(dims=dims, bulk=getattr(lgt, "LGT_" + bulk.upper()), omega=1.5, omega_late=1.1, theta_omega=1e-4,
+              max_sweeps=1000)
+    ctx = lgt.lgt_create(lgt.lgt_params_default(**kw), U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_OK and abs(res.F - r["F"]) < 1e-10
+    assert O.measure(V)["theta"] < 1e-14
+    srv = lgt.lgt_server_create(1 << 30, 0)
+    try:
+        jid = lgt.lgt_submit(srv, lgt.lgt_params_default(**kw), U)
+        while True:
+            st2, res2 = lgt.lgt_poll(srv, jid)
+            if st2 != lgt.LGT_EAGAIN:
+                break
+            time.sleep(0.002)
+    finally:
+        lgt.lgt_server_destroy(srv)
+    assert st2 == lgt.LGT_OK and abs(res2.F - r["F"]) < 1e-10
 
 
 # ------------------------------------------------ simulated annealing
