@@ -52,6 +52,9 @@ def parse():
                     help="landau32 (default; the headline line), or one of the other workloads, each "
                          "printing its own line; profile: a short fixed run of the sweep kernels for ncu")
     ap.add_argument("--jobs", type=int, default=256, help="serve: number of jobs in the stream")
+    ap.add_argument("--serve-jobs", type=int, default=32,
+                    help="landau32: jobs of the served-stream sample reported beside the headline")
+    ap.add_argument("--no-serve", action="store_true", help="landau32: skip the served-stream sample")
     prof = ap.add_argument_group("profile", "the short fixed run of --workload profile")
     prof.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
     prof.add_argument("--eps", type=float, default=0.5)
@@ -403,10 +406,10 @@ def run_ours(args):
     if not args.no_fp64_compare and rank == 0:
         runs = [("fp32_18_bulk", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_18, omega=OMEGA)),
                 ("sr_p0.8", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_12, algo=lgt.LGT_SR, p=0.8, seed=SEED)),
-                # an omega schedule, not the workload's: omega = 1.7 only down to theta = 1e-4,
-                # then 1.1 (the sweeps after the switch need far fewer sweeps at omega 1.1)
+                # an omega schedule, not the workload's fixed omega: 1.7 until the sweeps'
+                # estimate of theta drops below 1e-2, then 1.1
                 ("omega_schedule_1.7_to_1.1", DIMS, dev_in,
-                 dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, theta_switch=1e-4, omega_polish=1.1)),
+                 dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, omega_late=1.1, theta_omega=1e-2)),
                 # simulated annealing first (200 heat-bath sweeps, beta 1 -> 100), then the ladder
                 ("annealing_200", DIMS, dev_in,
                  dict(bulk=lgt.LGT_FP32_12, omega=OMEGA, sa_sweeps=200, sa_beta0=1.0, sa_beta1=100.0))]
@@ -429,6 +432,12 @@ def run_ours(args):
             finally:
                 lgt.lgt_destroy(cv)
     lgt.lgt_destroy(ctx)
+    # ---- a bounded sample of the served stream (p50/p99 latency beside jobs/s)
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        specs, gaps = serve_specs(args.serve_jobs)
+        serve = serve_stream(lgt, specs, gaps, cap_jobs=len(specs))
+        serve["workload"] = f"the first {len(specs)} jobs of the served stream: " + SERVE_WORKLOAD
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -449,7 +458,7 @@ def run_ours(args):
                 "gpu_launches": stats_kernel["launches"],
                 "device_loop": {"graph_launches": stats_kernel.get("loop_launches", 0),
                                 "chunks": stats_kernel.get("loop_chunks", 0)},
-                "clocks": clocks, "cpu_baseline": cpu}
+                "clocks": clocks, "cpu_baseline": cpu, "serve_sample": serve}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -626,38 +635,43 @@ def serve_specs(n_jobs: int, seed: int = 4):
     return specs, gaps
 
 
-def run_serve(args):
-    """Continuous batching.  Capacity: the first 64 jobs of the stream in a closed
-    loop (at most 12 outstanding, so inputs are generated as the GPU drains them);
-    then the whole stream with Poisson arrivals at 80% of that capacity.  Latency
-    is submit-to-completion of each job (lgt_result.seconds)."""
+# The served jobs fix no omega, so they run the measured omega schedule: overrelaxation
+# at 1.7 until the sweeps' estimate of theta drops below 1e-2, then 1.1 (on GB300 the
+# best or within 1% of it for every lattice of the stream, Landau and Coulomb, eps 0.3
+# to 0.7: about half the sweeps of a fixed 1.7).
+SERVE_OMEGA = dict(omega=1.7, omega_late=1.1, theta_omega=1e-2)
+
+
+def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstanding: int = 12):
+    """Continuous batching, measured twice on one job list.  Capacity: the first
+    cap_jobs jobs in a closed loop (at most max_outstanding outstanding, so inputs
+    are generated as the GPU drains them).  Then every job of the list with Poisson
+    arrivals at `load` x capacity.  Latency is submit-to-completion of each job
+    (lgt_result.seconds); the breakdown is per lattice size."""
     import queue
     import threading
-    from paper_1305_3440_gb300 import lgt, synth
-    specs, gaps = serve_specs(args.jobs)
+    from paper_1305_3440_gb300 import synth
 
     def params(sp):
         return lgt.lgt_params_default(dims=sp["dims"], gauge=sp["gauge"], theta_tol=sp["tol"],
-                                      bulk=lgt.LGT_FP32_12, max_sweeps=100000)
+                                      bulk=lgt.LGT_FP32_12, max_sweeps=100000, **SERVE_OMEGA)
 
     def producer(qu, subset):
         for sp in subset:
             qu.put((sp, synth.field(sp["dims"], sp["eps"], sp["seed"])))
         qu.put(None)
 
-    def drain(srv, pending, lat, status, sites):
+    def drain(srv, pending, done):
         for j in list(pending):
             st, res = lgt.lgt_poll(srv, j)
             if st != lgt.LGT_EAGAIN:
-                lat.append(res.seconds)
-                status.append(st)
-                sites.append(pending.pop(j))
+                done.append((pending.pop(j), res.seconds, st))
 
-    def run_stream(subset, rate, max_outstanding):
+    def run_stream(subset, rate, max_out):
         srv = lgt.lgt_server_create(150 << 30, 0)
         qu = queue.Queue(maxsize=4)
         threading.Thread(target=producer, args=(qu, subset), daemon=True).start()
-        pending, lat, status, sites = {}, [], [], []
+        pending, done = {}, []
         t0 = time.perf_counter()
         t_next = t0
         k = 0
@@ -670,38 +684,55 @@ def run_serve(args):
                 t_next += gaps[k] / rate
                 while time.perf_counter() < t_next:
                     time.sleep(0.0005)
-                    drain(srv, pending, lat, status, sites)
-            while max_outstanding and len(pending) >= max_outstanding:
+                    drain(srv, pending, done)
+            while max_out and len(pending) >= max_out:
                 time.sleep(0.001)
-                drain(srv, pending, lat, status, sites)
+                drain(srv, pending, done)
             jid = lgt.lgt_submit(srv, params(sp), U)
-            pending[jid] = int(np.prod(sp["dims"]))
+            pending[jid] = sp
             del U
             k += 1
-            drain(srv, pending, lat, status, sites)
+            drain(srv, pending, done)
         while pending:
             time.sleep(0.001)
-            drain(srv, pending, lat, status, sites)
+            drain(srv, pending, done)
         wall = time.perf_counter() - t0
         lgt.lgt_server_destroy(srv)
-        return wall, np.array(lat), status
+        return wall, done
 
-    cap_jobs = specs[:min(64, len(specs))]
-    wall_c, lat_c, st_c = run_stream(cap_jobs, None, 12)
-    capacity = len(cap_jobs) / wall_c
-    rate = 0.8 * capacity
-    wall, lat, st = run_stream(specs, rate, 0)
-    print(json.dumps({"workload": "serve", "metric": "p50/p99 job latency (s) at 80% of capacity",
-                      "jobs": len(specs), "capacity_jobs_per_s": capacity, "offered_rate_jobs_per_s": rate,
-                      "jobs_per_s": len(specs) / wall, "p50_s": float(np.percentile(lat, 50)),
-                      "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
-                      "closed_loop_p50_s": float(np.percentile(lat_c, 50)),
-                      "all_converged": all(x == lgt.LGT_OK for x in list(st) + list(st_c)),
-                      "config": {"workload": f"{len(specs)} jobs, dims in {{16^4, 24^4, 32^4, 16^3x32, 32^3x64, "
-                                             "48^4}, Landau/Coulomb 50/50, tol 1e-12/1e-14, eps U[0.3,0.7], "
-                                             "seeds 1000+j, 150 GB budget, FP32-12 bulk + anchored polish; capacity "
-                                             "from the first 64 jobs in a closed loop (12 outstanding)"}}),
-          flush=True)
+    cap_list = specs[:min(cap_jobs, len(specs))]
+    wall_c, done_c = run_stream(cap_list, None, max_outstanding)
+    capacity = len(cap_list) / wall_c
+    rate = load * capacity
+    wall, done = run_stream(specs, rate, 0)
+    lat = np.array([d[1] for d in done])
+    per_size = {}
+    for sp, sec, _ in done:
+        key = "x".join(str(v) for v in sp["dims"][::-1]) + (" coulomb" if sp["gauge"] else " landau")
+        per_size.setdefault(key, []).append(sec)
+    breakdown = {k: {"jobs": len(v), "p50_s": float(np.percentile(v, 50)), "p99_s": float(np.percentile(v, 99)),
+                     "max_s": float(np.max(v))} for k, v in sorted(per_size.items())}
+    return {"jobs": len(specs), "capacity_jobs_per_s": capacity, "capacity_jobs": len(cap_list),
+            "offered_rate_jobs_per_s": rate, "jobs_per_s": len(specs) / wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
+            "closed_loop_p50_s": float(np.percentile([d[1] for d in done_c], 50)),
+            "all_converged": all(d[2] == lgt.LGT_OK for d in done + done_c), "per_size": breakdown}
+
+
+SERVE_WORKLOAD = ("dims in {16^4, 24^4, 32^4, 16^3x32, 32^3x64, 48^4}, Landau/Coulomb 50/50, tol 1e-12/1e-14, "
+                  "eps U[0.3,0.7], seeds 1000+j, 150 GB budget, FP32-12 bulk + anchored polish, omega 1.7 -> 1.1 "
+                  "below theta 1e-2, Poisson arrivals at 80% of the capacity measured closed-loop (12 outstanding) "
+                  "on the same list")
+
+
+def run_serve(args):
+    """The served stream of the full job list: capacity from the whole list in a
+    closed loop, then the list again with Poisson arrivals at 80% of it."""
+    from paper_1305_3440_gb300 import lgt
+    specs, gaps = serve_specs(args.jobs)
+    r = serve_stream(lgt, specs, gaps, cap_jobs=len(specs))
+    print(json.dumps(dict({"workload": "serve", "metric": "p50/p99 job latency (s) at 80% of capacity",
+                           "config": {"workload": f"{len(specs)} jobs, " + SERVE_WORKLOAD}}, **r)), flush=True)
 
 
 def run_profile(args):
