@@ -108,6 +108,9 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->snake = snake;
   a->stream_wait_ns = c.stream_wait_ns ? c.stream_wait_ns : LGT_STREAM_WAIT_NS;
   a->stream_skip = c.stream_skip;
+  a->t_offset = c.t_offset;
+  a->t_first = c.t_first;
+  a->t_count = c.t_count > 0 ? c.t_count : g.nt;
 }
 
 // SMs of the current device, looked up once per device ordinal
@@ -165,7 +168,7 @@ static cudaError_t launch_sweep_kernel(sweep_fn fn, int cfg, const Geom &g, Swee
     const int smem = LGT_PIPE_SMEM_PER_THREAD * block;
     cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)ceil_div(g.vs_half, block) * g.nt * a.n_half;
+    const long long tiles = (long long)ceil_div(g.vs_half, block) * a.t_count * a.n_half;
     const long long cap = (long long)device_sms() * lgt_cfg_minblocks(cfg);
     const int blocks = (int)(tiles < cap ? tiles : cap);
     if (lgt_cfg_stream(cfg)) {  // counters start at zero in every launch
@@ -176,7 +179,7 @@ static cudaError_t launch_sweep_kernel(sweep_fn fn, int cfg, const Geom &g, Swee
     // could only be placed as they exit: measured a little slower, left plain)
     return launch_fn(fn, dim3(blocks), block, smem, st, a, parity & 1, false);
   }
-  return launch_fn(fn, dim3(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), g.nt), block, 0, st, a, parity & 1, pdl);
+  return launch_fn(fn, dim3(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), a.t_count), block, 0, st, a, parity & 1, pdl);
 }
 
 static sweep_fn pick_sweep(int fmt, const SweepCfg &c, int cfg) {
@@ -189,7 +192,7 @@ static cudaError_t half_sweep(int fmt, const Geom &g, void *links, void *G, cons
                               cudaStream_t st, const void *aux, const LoopState *loop, int reunit_every, bool pdl) {
   sweep_fn fn = pick_sweep(fmt, c, cfg);
   if (!fn || !lgt_cfg_supported_gauge(fmt, c.gauge, cfg)) return cudaErrorInvalidValue;
-  SweepArgs a;
+  SweepArgs a{};
   fill_sweep_args(&a, g, links, G, w, c, sweep, reunit, use_mask);
   a.aux = aux;
   a.loop = loop;
@@ -238,7 +241,7 @@ cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, con
     const int n = (int)((n_half - h0) < per_launch ? (n_half - h0) : per_launch);
     const int p = (p0 + h0) & 1;
     const long long s0 = (p0 + h0 - p) / 2;  // sweeps of the run before this launch's first
-    SweepArgs a;
+    SweepArgs a{};
     fill_sweep_args(&a, g, links, G, w, c, sweep0 + (unsigned long long)s0, 0, use_mask);
     a.aux = aux;
     a.loop = loop;
@@ -271,11 +274,12 @@ void fill_meas_args(MeasArgs *a, const Geom &g, const void *links, const Workspa
   a->active = w.active;
   a->coulomb_target = coulomb_target;
   a->with_plaq = with_plaq;
+  a->mag = 0;  // the maximally Abelian gauge's measurement is asked for explicitly (launch_measure)
 }
 
 cudaError_t launch_measure(int fmt, const Geom &g, const void *links, const Workspace &w, int with_plaq,
                            double coulomb_target, int block, cudaStream_t st, int mag) {
-  MeasArgs a;
+  MeasArgs a{};
   fill_meas_args(&a, g, links, w, with_plaq, coulomb_target);
   a.mag = mag;
   dim3 grid(ceil_div(g.vs_half, block), g.nt, 2);
@@ -605,7 +609,7 @@ __global__ void __launch_bounds__(256) k_fused_finish(FusedArgs a) { fused_finis
 
 cudaError_t launch_fused_finish(const Geom &g, const Workspace &w, int gauge, int sweep_sites, double coulomb_target,
                                 cudaStream_t st) {
-  FusedArgs a;
+  FusedArgs a{};
   fill_fused_args(&a, g, w, gauge, sweep_sites, coulomb_target);
   k_fused_finish<<<g.nt, 256, 0, st>>>(a);
   return cudaGetLastError();
@@ -642,6 +646,30 @@ __global__ void k_loop_decide(LoopState *L, const double *tot, int gauge, int k,
   // only whole chunks run on the device; the host takes a shorter last chunk
   go = go && L->remaining >= k && L->iters < L->max_iters;
   cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_slice_mask(uint8_t *active, int nt, int lo, int hi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nt) active[t] = (t >= lo && t < hi) ? 1 : 0;
+}
+
+cudaError_t launch_slice_mask(uint8_t *active, int nt, int lo, int hi, cudaStream_t st) {
+  k_slice_mask<<<(nt + 127) / 128, 128, 0, st>>>(active, nt, lo, hi);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_unit_aos(double *aos, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double *u = aos + k * 18;
+#pragma unroll
+  for (int e = 0; e < 18; e++) u[e] = (e == 0 || e == 8 || e == 16) ? 1.0 : 0.0;
+}
+
+cudaError_t launch_fill_unit_aos(double *aos, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_unit_aos<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(aos, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_loop_decide(LoopState *L, const double *fused_totals, int gauge, int k, int vs_half,

@@ -391,7 +391,7 @@ cudaError_t tick(lgt_server *s) {
         Job *j = order[k];
         if (j->sweep_fmt() != seg.fmt || j->cfg.gauge != seg.gauge || j->cfg.algo != seg.algo) break;
         if (sw >= j->nthis) continue;
-        BatchSweep r;
+        BatchSweep r{};
         fill_sweep_args(&r.a, j->g, j->sweep_links(), (j->phase == 0 || j->phase == 3) ? j->G : nullptr, j->ws,
                         j->cfg, j->sweep_index, 0, j->prm.gauge == LGT_COULOMB ? 1 : 0);
         r.a.aux = j->phase == 3 ? j->k0 : nullptr;
@@ -412,7 +412,7 @@ cudaError_t tick(lgt_server *s) {
   int fblocks = 0;
   for (Job *j : live) {
     if (j->measure_only) continue;
-    BatchFused r;
+    BatchFused r{};
     fill_fused_args(&r.a, j->g, j->ws, j->cfg.gauge, kServerBlock, coulomb_target(j));  // one thread per site
     r.block_begin = fblocks;
     r.nbx = 0;
@@ -432,7 +432,7 @@ cudaError_t tick(lgt_server *s) {
     size_t k = i;
     for (; k < morder.size() && morder[k]->work_fmt() == seg.fmt; k++) {
       Job *j = morder[k];
-      BatchMeas r;
+      BatchMeas r{};
       fill_meas_args(&r.a, j->g, j->work_links(), j->ws, j->certify ? 1 : 0, coulomb_target(j));
       r.block_begin = seg.blocks;
       r.nbx = j->nbx;
