@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--workload", default="landau32",
-                    choices=["landau32", "coulomb", "landau64", "serve", "mag", "profile"],
+                    choices=["landau32", "coulomb", "landau64", "serve", "mag", "profile", "slab"],
                     help="landau32 (default; the headline line), or one of the other workloads, each "
                          "printing its own line; profile: a short fixed run of the sweep kernels for ncu")
     ap.add_argument("--jobs", type=int, default=256, help="serve: number of jobs in the stream")
@@ -735,6 +735,75 @@ def run_serve(args):
                            "config": {"workload": f"{len(specs)} jobs, " + SERVE_WORKLOAD}}, **r)), flush=True)
 
 
+def run_slab(args):
+    """Temporal slab decomposition (Sec. 5).  One process: the 32^4 field cut into
+    1, 2 and 4 slabs on this GPU (the boundary links move by device copies), FP32-12
+    sweeps (omega 1.7, lean launch configuration 8, as the whole-lattice context
+    forced to the same configuration), time per sweep against the whole lattice:
+    the cost of the protocol's extra launches and copies.  Under torchrun (N GPUs):
+    one slab of 32 slices per rank, a 32^3 x (32 N) lattice (weak scaling), the
+    boundary links over NCCL; site updates per second over all ranks."""
+    import torch
+    from paper_1305_3440_gb300 import lgt, synth
+    from paper_1305_3440_gb300.slab import DistRing, GpuSlab, LocalRing, SlabDriver
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    n_sweeps = 100
+    L = 32
+    dims = (L * world, 32, 32, 32)
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, omega=1.7, launch_config=9)
+    out = {}
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            fn(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(n_sweeps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    if world == 1:
+        U = synth.field(dims, 0.5, 2)
+        ctx = lgt.lgt_create(p, U, stream=stream)
+        t = timed(lambda n: lgt.lgt_sweep(ctx, n))
+        lgt.lgt_destroy(ctx)
+        out["whole"] = {"us_per_sweep": t / n_sweeps * 1e6}
+        for n in (1, 2, 4):
+            Ls = dims[0] // n
+            eng = [GpuSlab(p, r * Ls, Ls, np.ascontiguousarray(U[r * Ls:(r + 1) * Ls]), stream) for r in range(n)]
+            drv = SlabDriver(eng, LocalRing(n))
+            ts = timed(drv.sweep)
+            out[f"slabs_{n}"] = {"us_per_sweep": ts / n_sweeps * 1e6, "overhead": ts / t - 1.0,
+                                 "boundary_bytes_per_transfer": eng[0].nbytes}
+            for e in eng:
+                e.close()
+        value = n_sweeps * int(np.prod(dims)) / (out["slabs_4"]["us_per_sweep"] * n_sweeps / 1e6)
+    else:
+        U = synth.field((L,) + dims[1:], 0.5, 2 + rank)  # this rank's slab (weak scaling, synthetic)
+        eng = GpuSlab(p, rank * L, L, U, stream)
+        drv = SlabDriver([eng], DistRing())
+        t = timed(drv.sweep)
+        t_max, upd = aggregate_over_ranks(t, float(n_sweeps * int(np.prod(U.shape[:4]))), device=f"cuda:{local}")
+        value = upd / t_max
+        out[f"ranks_{world}"] = {"us_per_sweep": t_max / n_sweeps * 1e6, "boundary_bytes_per_transfer": eng.nbytes}
+        eng.close()
+    if rank == 0:
+        print(json.dumps({"workload": "slab", "metric": "site updates/s (temporal slabs, FP32-12 sweeps)",
+                          "value": value, "unit": "site updates/s", "n_gpus": world, "scaling": "weak",
+                          "config": {"workload": f"SU(3) Landau {dims[1]}^3 x {dims[0]}, eps 0.5, {n_sweeps} sweeps, "
+                                                 f"slabs of {dims[0] if world == 1 else L} slices"},
+                          "runs": out}), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_profile(args):
     """A short, fixed run of the sweep kernels for profilers (ncu -k ... -c ...):
     one context on cuda:0, `--bulk-sweeps` sweeps in the bulk precision, promotion
@@ -783,6 +852,8 @@ def main():
         run_mag(args)
     elif args.workload == "profile":
         run_profile(args)
+    elif args.workload == "slab":
+        run_slab(args)
     else:
         run_ours(args)
 

@@ -314,6 +314,66 @@ typedef struct {
  * consecutive half-sweep launches (nothing else runs inside a batch). */
 LGT_API lgt_status lgt_get_stats(lgt_ctx *ctx, lgt_stats *out);
 
+/* ------------------------------------------------- temporal slabs (Sec. 5) */
+/* The paper's multi-GPU method (Sec. 5): the lattice is cut along t into
+ * slabs, one per device; in every half-sweep each slab needs the temporal links
+ * U_0(t_min - 1) of the inactive parity from the slab before it, and the
+ * update of its first slice changes them, so they go back.  A slab context
+ * holds the owned slices and a halo for those links; a driver moves them
+ * between slabs (the package's slab module: its steps follow the paper's
+ * list, with the return transfer overlapped with the interior slices).
+ *
+ * lgt_slab_create: params->dims[0] = L, the slab's owned slices (even, >= 2);
+ * they are the global slices t0 .. t0 + L - 1 of a lattice of nt_global
+ * slices (t0 even, so a site's parity is that of the whole lattice).  links:
+ * the owned slices in the public layout (L * N_3 * N_2 * N_1 sites), host or
+ * device memory.  Landau or Coulomb gauge, OR or SR (random streams counted by
+ * the global site, so slabs reproduce the whole lattice's sweeps bit for bit),
+ * no annealing; the field stays in its bulk precision (no promotion).  The
+ * context holds L + 2 slices: two halo slices, the second receiving
+ * U_0(t_min - 1).  lgt_load takes owned slices as well; lgt_get_links and
+ * lgt_get_working_links return the owned slices of the working field
+ * (FP64-widened); lgt_estimate reports the owned slices (F_t, theta_t: L
+ * entries; F, theta: their mean, Coulomb: max theta_t).  lgt_sweep,
+ * lgt_half_sweep, lgt_measure, lgt_measure_slices, lgt_fix and lgt_promote
+ * return LGT_EINVAL on a slab.  Errors as lgt_create. */
+LGT_API lgt_status lgt_slab_create(const lgt_params *params, int32_t nt_global, int32_t t0, const double *links,
+                                   int links_on_device, void *cuda_stream, lgt_ctx **out);
+
+/* Half-sweep of `parity` (Sec. 3: all sites of one parity at once) over the
+ * owned slices first .. first + count - 1 (0-based within the slab) of a slab.
+ * Enqueued on the context's stream, not synchronised (lgt_slab_sync).  The
+ * sweep counter (SR stream, reunitarisation schedule) advances after a parity-1
+ * call that covers the last owned slice.  The links U_0(t_min - 1) must be in
+ * the halo when the first owned slice is updated. */
+LGT_API lgt_status lgt_slab_half_sweep(lgt_ctx *ctx, int32_t parity, int32_t first, int32_t count);
+
+/* Bytes of one boundary transfer of a slab: the temporal links of one parity
+ * of one slice in the working storage format (FP64: 144 B per link, FP32-18:
+ * 72 B, FP32-12: 48 B). */
+LGT_API lgt_status lgt_slab_boundary_bytes(lgt_ctx *ctx, size_t *bytes);
+
+/* Copy the temporal links U_0 of `parity` on owned slice `slice` (-1: the
+ * halo, U_0(t_min - 1)) between the slab and buf (device memory of
+ * lgt_slab_boundary_bytes bytes): into the slab if into_slab != 0, out of it
+ * otherwise.  Layout of buf: the storage chunks one after the other, each the
+ * slice's sites of that parity in within-parity order.  Enqueued on the
+ * context's stream, not synchronised. */
+LGT_API lgt_status lgt_slab_boundary(lgt_ctx *ctx, int32_t slice, int32_t parity, void *buf, int32_t into_slab);
+
+/* Synchronise the context's stream (and report a failure of what it ran). */
+LGT_API lgt_status lgt_slab_sync(lgt_ctx *ctx);
+
+/* Exact per-timeslice sums of the working field, FP64 (Sec. 2), in host
+ * memory sums[N_t][5] (a slab: its L owned slices): sum over the slice's sites
+ * of [0] sum_mu Re tr U_mu(x), [1] the same over mu = 1..3, [2] tr[Delta
+ * Delta^dagger] (all four directions), [3] the same over mu = 1..3, [4] the six
+ * plaquettes Re tr U_P.  F = sum [0] / (3 * 4 * V), theta = sum [2] / (3 V),
+ * Coulomb F_t = [1] / (9 V_s), theta_t = [3] / (3 V_s).  On a slab, [2] needs
+ * both parities of the halo current and [4] of the last owned slice reads
+ * the slice after the slab (not held: invalid there). */
+LGT_API lgt_status lgt_measure_slice_sums(lgt_ctx *ctx, double *sums);
+
 /* Test support; the paper has no counterpart.  Fault injection for the bounded
  * waits of the streaming launch configuration (10), so that their error path
  * can be exercised on a GPU without any device fault.  Until the next

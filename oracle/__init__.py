@@ -51,6 +51,9 @@ def _load():
             L.orc_half_sweep.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_int, _dp, _dp]
+            L.orc_half_sweep_offset.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                                ctypes.c_uint64, ctypes.c_int, _dp, ctypes.c_int64]
             L.orc_sweeps.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                      ctypes.c_int, ctypes.c_int, _dp]
@@ -129,12 +132,19 @@ def measure(links: np.ndarray, gauge: int = LANDAU):
 
 
 def half_sweep(links, parity, gauge=LANDAU, algo=OR, omega=1.0, p=0.0, seed=0, sweep=0,
-               transform_temporal=1, active=None, order=None):
-    """In-place half-sweep over one parity."""
+               transform_temporal=1, active=None, order=None, site_offset=0):
+    """In-place half-sweep over one parity.  site_offset: the links are a slab of a
+    larger lattice and the random streams are keyed by site + site_offset."""
     d = _dims_of(links)
     act = None
     if active is not None:
         act = np.ascontiguousarray(active, dtype=np.uint8)
+    if site_offset:
+        assert order is None
+        _check(_load().orc_half_sweep_offset(d, links.ctypes.data, gauge, parity, algo, omega, p, seed, sweep,
+                                             transform_temporal, None if act is None else act.ctypes.data,
+                                             int(site_offset)), "orc_half_sweep_offset")
+        return links
     od = None
     if order is not None:
         od = np.ascontiguousarray(order, dtype=np.int64)

@@ -595,16 +595,17 @@ typedef struct {
   update_rule rule;
   uint64_t seed;
   int transform_temporal;
+  int64_t site_offset; /* added to a site's index where it keys random streams (a slab of a larger lattice) */
 } sweep_cfg;
 
 /* g of one site update on the current links (which it does not touch) */
 static su3 site_g(const lattice *l, const double *links, int64_t site, const sweep_cfg *cfg, uint64_t sweep) {
   uint32_t u[3] = {0, 0, 0};
-  if (cfg->rule.algo == ORC_SR) sr_draws(cfg->seed, sweep, site, u);
+  if (cfg->rule.algo == ORC_SR) sr_draws(cfg->seed, sweep, site + cfg->site_offset, u);
   update_rule rule = cfg->rule;
   rule.seed = cfg->seed;
   rule.sweep = sweep;
-  rule.site = site;
+  rule.site = site + cfg->site_offset;
   if (cfg->gauge == ORC_MAG) {
     su3 fwd[4], bwd[4];
     for (int mu = 0; mu < 4; mu++) {
@@ -816,6 +817,7 @@ static sweep_cfg make_cfg(int gauge, int algo, double omega, double p, uint64_t 
   c.rule.site = 0;
   c.seed = seed;
   c.transform_temporal = transform_temporal;
+  c.site_offset = 0;
   return c;
 }
 
@@ -828,6 +830,22 @@ int orc_half_sweep(const int32_t dims[4], double *links, int gauge, int parity, 
   const lattice l = make_lattice(dims);
   const sweep_cfg cfg = make_cfg(gauge, algo, omega, p, seed, transform_temporal);
   half_sweep(&l, links, parity & 1, &cfg, sweep, active, order);
+  return 0;
+}
+
+/* As orc_half_sweep on a slab of a larger lattice held with its own geometry:
+ * the random streams are keyed by site + site_offset, the site's index in the
+ * whole lattice (the slab's first slice at global slice t0: site_offset =
+ * t0 * V_s minus the slices held before it).  Which sites are updated is the
+ * caller's `active` mask. */
+int orc_half_sweep_offset(const int32_t dims[4], double *links, int gauge, int parity, int algo, double omega,
+                          double p, uint64_t seed, uint64_t sweep, int transform_temporal, const uint8_t *active,
+                          int64_t site_offset) {
+  if (check_dims(dims)) return -1;
+  const lattice l = make_lattice(dims);
+  sweep_cfg cfg = make_cfg(gauge, algo, omega, p, seed, transform_temporal);
+  cfg.site_offset = site_offset;
+  half_sweep(&l, links, parity & 1, &cfg, sweep, active, NULL);
   return 0;
 }
 

@@ -244,6 +244,11 @@ struct lgt_ctx {
   int loop_sweep_launches[2];      // sweep kernel launches in one chunk of each loop
   int *h_err;                      // pinned copy of the workspace's error word
   int omega_switched;              // the omega schedule has moved to omega_late
+  // temporal slab (lgt_slab_create): local slices 0 and 1 are the halo (local
+  // slice 1 holds U_0 of the global slice before the slab), 2 .. nt-1 the owned
+  // slices t0 .. t0 + nt - 3
+  int slab;
+  int32_t slab_t0, slab_nt_global;
   // fault injection for the streaming launches of lgt_sweep / lgt_half_sweep
   // (lgt_inject_stream_stall; cleared by lgt_load)
   unsigned long long inj_wait_ns;
@@ -483,7 +488,24 @@ extern "C" lgt_status lgt_create(const lgt_params *params, const double *links, 
   return LGT_OK;
 }
 
+// A slab's local field in public layout in the staging buffer: the two halo
+// slices unit links, then the caller's owned slices.
+static lgt_status slab_stage(lgt_ctx *c, const double *links, int links_on_device) {
+  const Geom &g = c->g;
+  const size_t slice_doubles = (size_t)g.vs_half * 2 * 4 * 18;
+  if (!c->stage) LGT_CUDA(cudaMalloc(&c->stage, slice_doubles * g.nt * sizeof(double)));
+  LGT_CUDA(launch_fill_unit_aos(c->stage, (long long)(2 * slice_doubles / 18), c->stream));
+  LGT_CUDA(cudaMemcpyAsync(c->stage + 2 * slice_doubles, links, slice_doubles * (g.nt - 2) * sizeof(double),
+                           links_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  return LGT_OK;
+}
+
 extern "C" lgt_status lgt_load(lgt_ctx *ctx, const double *links, int links_on_device) {
+  if (ctx && ctx->slab && links) {
+    lgt_status st = slab_stage(ctx, links, links_on_device);
+    if (st != LGT_OK) return st;
+    return load_field(ctx, ctx->stage, 1);
+  }
   if (!ctx) {
     lgt_set_error("lgt_load: NULL context");
     return LGT_EINVAL;
@@ -556,7 +578,7 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
   const bool anch = c->phase == 3;
   const int fmt = anch ? (int)FMT_ANCHOR : work_fmt(c);
   void *links = (c->phase == 0 || anch) ? c->u32 : c->u64;
-  void *G = (c->phase == 0 || anch) ? c->G : nullptr;
+  void *G = ((c->phase == 0 && !c->slab) || anch) ? c->G : nullptr;  // a slab is never promoted
   const int kind = c->phase == 0 ? 0 : 1;
   if (n_half <= 0) return LGT_OK;
   if (anch) {
@@ -590,6 +612,10 @@ static lgt_status run_halves(lgt_ctx *c, int first_parity, int n_half, int use_m
 static lgt_status run_sweeps(lgt_ctx *c, int n, int use_mask) { return run_halves(c, 0, 2 * n, use_mask); }
 
 extern "C" lgt_status lgt_half_sweep(lgt_ctx *ctx, int32_t parity) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_half_sweep: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx || (parity != 0 && parity != 1)) {
     lgt_set_error("lgt_half_sweep: bad arguments");
     return LGT_EINVAL;
@@ -600,6 +626,10 @@ extern "C" lgt_status lgt_half_sweep(lgt_ctx *ctx, int32_t parity) {
 }
 
 extern "C" lgt_status lgt_sweep(lgt_ctx *ctx, int32_t n) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_sweep: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx || n < 0) {
     lgt_set_error("lgt_sweep: bad arguments");
     return LGT_EINVAL;
@@ -672,6 +702,10 @@ static void omega_check(lgt_ctx *c, double theta) {
 }
 
 extern "C" lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double *plaq) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_measure: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx) {
     lgt_set_error("lgt_measure: NULL context");
     return LGT_EINVAL;
@@ -686,6 +720,10 @@ extern "C" lgt_status lgt_measure(lgt_ctx *ctx, double *F, double *theta, double
 }
 
 extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *theta_t) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_measure_slices: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx) {
     lgt_set_error("lgt_measure_slices: NULL context");
     return LGT_EINVAL;
@@ -703,11 +741,41 @@ extern "C" lgt_status lgt_measure_slices(lgt_ctx *ctx, double *F_t, double *thet
   return sync_stream(ctx);
 }
 
+// the fused estimate of a slab over its owned slices (per slice as lgt_estimate;
+// F, theta: means over the owned slices, Coulomb: max theta_t)
+static lgt_status slab_estimate(lgt_ctx *c, double *F, double *theta, double *F_t, double *theta_t) {
+  const int nt = c->g.nt, L = nt - 2;
+  LGT_CUDA(launch_slice_mask(c->ws.active, nt, 2, nt, c->stream));
+  Meas m;
+  lgt_status st = estimate(c, -1.0, &m);
+  if (st != LGT_OK) return st;
+  std::vector<double> sl((size_t)nt * 2);
+  LGT_CUDA(cudaMemcpyAsync(sl.data(), c->ws.fused_slice, sizeof(double) * sl.size(), cudaMemcpyDeviceToHost,
+                           c->stream));
+  st = sync_stream(c);
+  if (st != LGT_OK) return st;
+  const bool coulomb = c->cfg.gauge == GAUGE_COULOMB;
+  const double vs = 2.0 * (double)c->g.vs_half, nd = coulomb ? 3.0 : 4.0;
+  double fs = 0.0, ts = 0.0, tmax = 0.0;
+  for (int k = 0; k < L; k++) {
+    const double ft = sl[2 * (k + 2)] / (3.0 * nd * vs), th = sl[2 * (k + 2) + 1] / (3.0 * vs);
+    if (F_t) F_t[k] = ft;
+    if (theta_t) theta_t[k] = th;
+    fs += ft;
+    ts += th;
+    tmax = th > tmax ? th : tmax;
+  }
+  if (F) *F = fs / L;
+  if (theta) *theta = coulomb ? tmax : ts / L;
+  return LGT_OK;
+}
+
 extern "C" lgt_status lgt_estimate(lgt_ctx *ctx, double *F, double *theta, double *F_t, double *theta_t) {
   if (!ctx) {
     lgt_set_error("lgt_estimate: NULL context");
     return LGT_EINVAL;
   }
+  if (ctx->slab) return slab_estimate(ctx, F, theta, F_t, theta_t);
   Meas m;
   lgt_status st = estimate(ctx, -1.0, &m);
   if (st != LGT_OK) return st;
@@ -744,6 +812,182 @@ extern "C" lgt_status lgt_inject_stream_stall(lgt_ctx *ctx, uint64_t wait_ns, ui
   return LGT_OK;
 }
 
+// ------------------------------------------------------ temporal slabs (Sec. 5)
+extern "C" lgt_status lgt_slab_create(const lgt_params *params, int32_t nt_global, int32_t t0, const double *links,
+                                      int links_on_device, void *cuda_stream, lgt_ctx **out) {
+  if (!out || !params || !links) {
+    lgt_set_error("lgt_slab_create: NULL argument");
+    return LGT_EINVAL;
+  }
+  *out = nullptr;
+  const int L = params->dims[0];
+  if (L < 2 || (L & 1) || nt_global < 2 || (nt_global & 1) || t0 < 0 || (t0 & 1) || t0 + L > nt_global) {
+    lgt_set_error("lgt_slab_create: need an even slab of dims[0] = %d >= 2 slices starting at an even t0 = %d "
+                  "within the %d slices of the lattice", L, t0, nt_global);
+    return LGT_EINVAL;
+  }
+  if (params->gauge != LGT_LANDAU && params->gauge != LGT_COULOMB) {
+    lgt_set_error("lgt_slab_create: Landau or Coulomb gauge only");
+    return LGT_EINVAL;
+  }
+  if (params->sa_sweeps != 0) {
+    lgt_set_error("lgt_slab_create: no simulated annealing on slabs");
+    return LGT_EINVAL;
+  }
+  lgt_status st = lgt_validate_params(params);
+  if (st != LGT_OK) return st;
+  lgt_params local = *params;
+  local.dims[0] = L + 2;
+  const Geom g = lgt_make_geom(local.dims);
+  const size_t slice_doubles = (size_t)g.vs_half * 2 * 4 * 18;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  double *buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&buf, slice_doubles * g.nt * sizeof(double), stream);
+  if (e == cudaSuccess) e = launch_fill_unit_aos(buf, (long long)(2 * slice_doubles / 18), stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(buf + 2 * slice_doubles, links, slice_doubles * L * sizeof(double),
+                        links_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) {
+    if (buf) cudaFreeAsync(buf, stream);
+    lgt_set_error("lgt_slab_create: staging the slab failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LGT_ENOMEM : LGT_ECUDA;
+  }
+  lgt_ctx *c = nullptr;
+  st = lgt_create(&local, buf, 1, cuda_stream, &c);
+  cudaFreeAsync(buf, stream);
+  cudaStreamSynchronize(stream);
+  if (st != LGT_OK) return st;
+  c->slab = 1;
+  c->slab_t0 = t0;
+  c->slab_nt_global = nt_global;
+  c->cfg.t_offset = t0 - 2;  // the random streams count global sites
+  // the streaming configuration orders whole slices itself: a slab uses the pipelined one
+  if (lgt_cfg_stream(c->cfg_bulk)) c->cfg_bulk = 7;
+  if (lgt_cfg_stream(c->cfg_polish)) c->cfg_polish = 0;
+  *out = c;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_slab_half_sweep(lgt_ctx *ctx, int32_t parity, int32_t first, int32_t count) {
+  if (!ctx || !ctx->slab || (parity != 0 && parity != 1)) {
+    lgt_set_error("lgt_slab_half_sweep: bad arguments (or not a slab)");
+    return LGT_EINVAL;
+  }
+  lgt_ctx *c = ctx;
+  const int L = c->g.nt - 2;
+  if (first < 0 || count < 1 || first + count > L) {
+    lgt_set_error("lgt_slab_half_sweep: slices [%d, %d) outside the %d owned slices", first, first + count, L);
+    return LGT_EINVAL;
+  }
+  const int fmt = work_fmt(c);
+  void *links = c->phase == 0 ? c->u32 : c->u64;
+  const int kind = c->phase == 0 ? 0 : 1;
+  const int lc = c->phase == 0 ? c->cfg_bulk : c->cfg_polish;
+  const int64_t done = kind == 0 ? c->sweeps_bulk : c->sweeps_fp64;
+  SweepCfg sc = c->cfg;  // the launch covers the requested slices only
+  sc.t_first = 2 + first;
+  sc.t_count = count;
+  const int bt = batch_begin(c, kind);
+  int launches = 0;
+  LGT_CUDA(launch_half_sweeps(fmt, c->g, links, nullptr, c->ws, sc, parity, 1, c->sweep_index, done,
+                              c->phase == 0 ? c->prm.reunit_every : 0, 0, lc, c->stream, nullptr, nullptr,
+                              &launches));
+  batch_end(c, bt);
+  c->last_sites = lgt_cfg_sites(lc);
+  if (parity == 1 && first + count == L) {  // a sweep ends with the odd half of the last owned slice
+    c->sweep_index++;
+    if (kind == 0) c->sweeps_bulk++;
+    else c->sweeps_fp64++;
+  }
+  c->stats.sweep_launches[kind] += 1;
+  c->stats.launches += launches;
+  c->stats.site_updates[kind] += (int64_t)c->g.vs_half * count;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_slab_boundary_bytes(lgt_ctx *ctx, size_t *bytes) {
+  if (!ctx || !ctx->slab || !bytes) {
+    lgt_set_error("lgt_slab_boundary_bytes: bad arguments (or not a slab)");
+    return LGT_EINVAL;
+  }
+  *bytes = (size_t)ctx->g.vs_half * link_bytes_per_half_site(work_fmt(ctx)) / 4;
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_slab_boundary(lgt_ctx *ctx, int32_t slice, int32_t parity, void *buf, int32_t into_slab) {
+  if (!ctx || !ctx->slab || !buf || (parity != 0 && parity != 1)) {
+    lgt_set_error("lgt_slab_boundary: bad arguments (or not a slab)");
+    return LGT_EINVAL;
+  }
+  lgt_ctx *c = ctx;
+  const int L = c->g.nt - 2;
+  if (slice < -1 || slice >= L) {
+    lgt_set_error("lgt_slab_boundary: slice %d outside [-1, %d)", slice, L);
+    return LGT_EINVAL;
+  }
+  const int fmt = work_fmt(c);
+  const size_t vh = (size_t)c->g.vh, vs = (size_t)c->g.vs_half, t = (size_t)(slice + 2);
+  char *base = (char *)(c->phase == 0 ? c->u32 : c->u64);
+  char *b = (char *)buf;
+  // the streams of (parity, mu = 0): 16-byte chunks of vh sites each
+  struct Part {
+    size_t offset, elem;  // bytes to the first chunk's stream, bytes per site in a chunk
+    int chunks;
+  } parts[2];
+  int np = 1;
+  if (fmt == FMT_F64 || fmt == FMT_PAIR) {
+    parts[0] = {(size_t)(parity * 4) * 9 * vh * 16, 16, 9};
+  } else if (fmt == FMT_F32_12) {
+    parts[0] = {(size_t)(parity * 4) * 3 * vh * 16, 16, 3};
+  } else {  // FP32-18: 4 float4 chunks, then the float2 chunk in its own region
+    parts[0] = {(size_t)(parity * 4) * 4 * vh * 16, 16, 4};
+    parts[1] = {32 * vh * 16 + (size_t)(parity * 4) * vh * 8, 8, 1};
+    np = 2;
+  }
+  size_t off = 0;
+  for (int k = 0; k < np; k++) {
+    char *stream_base = base + parts[k].offset + t * vs * parts[k].elem;
+    const size_t width = vs * parts[k].elem, pitch = vh * parts[k].elem;
+    if (into_slab)
+      LGT_CUDA(cudaMemcpy2DAsync(stream_base, pitch, b + off, width, width, parts[k].chunks,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    else
+      LGT_CUDA(cudaMemcpy2DAsync(b + off, width, stream_base, pitch, width, parts[k].chunks,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    off += width * parts[k].chunks;
+  }
+  return LGT_OK;
+}
+
+extern "C" lgt_status lgt_measure_slice_sums(lgt_ctx *ctx, double *sums) {
+  if (!ctx || !sums) {
+    lgt_set_error("lgt_measure_slice_sums: bad arguments");
+    return LGT_EINVAL;
+  }
+  lgt_ctx *c = ctx;
+  lgt_status st = anchor_materialise(c);
+  if (st != LGT_OK) return st;
+  const int bt = batch_begin(c, 2);
+  LGT_CUDA(launch_measure(work_fmt(c), c->g, c->phase == 0 ? c->u32 : c->u64, c->ws, 1, -1.0, 128, c->stream,
+                          c->prm.gauge == LGT_MAG ? 1 : 0));
+  batch_end(c, bt);
+  c->stats.measure_launches++;
+  c->stats.launches++;
+  const int first = c->slab ? 2 : 0;
+  const int n = c->g.nt - first;
+  LGT_CUDA(cudaMemcpyAsync(sums, c->ws.slice_sum + (size_t)first * MEAS_NV, sizeof(double) * MEAS_NV * n,
+                           cudaMemcpyDeviceToHost, c->stream));
+  return sync_stream(c);
+}
+
+extern "C" lgt_status lgt_slab_sync(lgt_ctx *ctx) {
+  if (!ctx) {
+    lgt_set_error("lgt_slab_sync: NULL context");
+    return LGT_EINVAL;
+  }
+  return sync_stream(ctx);
+}
+
 // --------------------------------------------------------------- promotion
 static lgt_status promote(lgt_ctx *c) {
   if (c->phase != 0) return LGT_OK;
@@ -765,6 +1009,10 @@ static lgt_status promote(lgt_ctx *c) {
 }
 
 extern "C" lgt_status lgt_promote(lgt_ctx *ctx) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_promote: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx) {
     lgt_set_error("lgt_promote: NULL context");
     return LGT_EINVAL;
@@ -949,6 +1197,10 @@ static lgt_status run_annealing(lgt_ctx *c, int64_t *remaining) {
 
 // ------------------------------------------------------------- the driver
 extern "C" lgt_status lgt_fix(lgt_ctx *ctx, lgt_result *res) {
+  if (ctx && ctx->slab) {
+    lgt_set_error("lgt_fix: a temporal slab is swept and measured through the lgt_slab_* calls");
+    return LGT_EINVAL;
+  }
   if (!ctx) {
     lgt_set_error("lgt_fix: NULL context");
     return LGT_EINVAL;
@@ -1095,11 +1347,24 @@ static lgt_status to_output(lgt_ctx *c, double *out, int out_on_device, int work
   return LGT_OK;
 }
 
+// a slab's owned slices of its working links (public layout, FP64)
+static lgt_status slab_output(lgt_ctx *c, double *out, int out_on_device) {
+  const Geom &g = c->g;
+  const size_t slice_doubles = (size_t)g.vs_half * 2 * 4 * 18;
+  if (!c->stage) LGT_CUDA(cudaMalloc(&c->stage, slice_doubles * g.nt * sizeof(double)));
+  LGT_CUDA(launch_egress(work_fmt(c), g, c->phase == 0 ? c->u32 : c->u64, c->stage, c->stream));
+  c->stats.launches++;
+  LGT_CUDA(cudaMemcpyAsync(out, c->stage + 2 * slice_doubles, slice_doubles * (g.nt - 2) * sizeof(double),
+                           out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return sync_stream(c);
+}
+
 extern "C" lgt_status lgt_get_links(lgt_ctx *ctx, double *out, int out_on_device) {
   if (!ctx || !out) {
     lgt_set_error("lgt_get_links: bad arguments");
     return LGT_EINVAL;
   }
+  if (ctx->slab) return slab_output(ctx, out, out_on_device);
   return to_output(ctx, out, out_on_device, 0);
 }
 
@@ -1108,6 +1373,7 @@ extern "C" lgt_status lgt_get_working_links(lgt_ctx *ctx, double *out, int out_o
     lgt_set_error("lgt_get_working_links: bad arguments");
     return LGT_EINVAL;
   }
+  if (ctx->slab) return slab_output(ctx, out, out_on_device);
   return to_output(ctx, out, out_on_device, 1);
 }
 

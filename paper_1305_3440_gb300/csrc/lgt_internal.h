@@ -120,6 +120,11 @@ struct SweepArgs {
   // bounded waits expire: fault injection for tests)
   unsigned long long stream_wait_ns;
   unsigned stream_skip;
+  // global timeslice of local slice 0 (a temporal slab's offset): the random
+  // streams of stochastic relaxation and annealing are counted by the global site
+  int t_offset;
+  // the slices the launch covers: t_first .. t_first + t_count - 1 (all by default)
+  int t_first, t_count;
 };
 
 // Arguments of one lattice's exact measurement.
@@ -181,6 +186,8 @@ struct SweepCfg {
   // streaming launches: wait bound (0: LGT_STREAM_WAIT_NS) and first ticket (see SweepArgs)
   unsigned long long stream_wait_ns = 0;
   unsigned stream_skip = 0;
+  int t_offset = 0;  // temporal slab: global slice of local slice 0
+  int t_first = 0, t_count = 0;  // slices a launch covers (t_count 0: all)
 };
 
 // Single-lattice half-sweep kernels, one per (format, gauge, algorithm,
@@ -308,6 +315,11 @@ cudaError_t launch_g_identity(const Geom &g, void *G, cudaStream_t st);
 // to AoS.  skip_temporal: leave mu = 0 untouched.
 cudaError_t launch_apply_G(const Geom &g, const void *G, const void *u64_in, void *u64_out, double *aos_out,
                            int skip_temporal, cudaStream_t st);
+
+// Temporal slabs: active[t] = (lo <= t < hi) for the nt slices.
+cudaError_t launch_slice_mask(uint8_t *active, int nt, int lo, int hi, cudaStream_t st);
+// n links of public AoS layout (18 doubles each) set to the unit matrix.
+cudaError_t launch_fill_unit_aos(double *aos, long long n, cudaStream_t st);
 
 // Every link of a field of format fmt set to the unit matrix.
 cudaError_t launch_fill_unit(int fmt, const Geom &g, void *soa, cudaStream_t st);

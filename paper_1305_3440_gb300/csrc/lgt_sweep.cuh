@@ -58,7 +58,8 @@ __device__ __forceinline__ SaDraw sa_draw_of(const SweepArgs &a, const Coords &c
   d.site = (uint32_t)((unsigned long long)c.x1 +
                       (unsigned long long)a.g.n1 *
                           ((unsigned long long)c.x2 +
-                           (unsigned long long)a.g.n2 * ((unsigned long long)c.x3 + (unsigned long long)a.g.n3 * c.t)));
+                           (unsigned long long)a.g.n2 *
+                               ((unsigned long long)c.x3 + (unsigned long long)a.g.n3 * (long long)(c.t + a.t_offset))));
   d.sweep = (uint32_t)a.sweep;
   return d;
 }
@@ -68,7 +69,8 @@ __device__ __forceinline__ uint4 sr_draws(const SweepArgs &a, const Coords &c) {
       (unsigned long long)c.x1 +
       (unsigned long long)a.g.n1 * ((unsigned long long)c.x2 +
                                     (unsigned long long)a.g.n2 * ((unsigned long long)c.x3 +
-                                                                  (unsigned long long)a.g.n3 * (unsigned long long)c.t));
+                                                                  (unsigned long long)a.g.n3 *
+                                                                      (unsigned long long)(c.t + a.t_offset)));
   const uint4 ctr = make_uint4((uint32_t)lex, (uint32_t)(lex >> 32), (uint32_t)a.sweep, LGT_SR_TAG);
   const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
   return philox4x32_10(ctr, key);
@@ -96,10 +98,10 @@ __device__ __forceinline__ bool sweep_reversed(const SweepArgs &a, int p) { retu
 // (slice, tile) of this block in a (tiles per slice, slices) grid
 __device__ __forceinline__ void sweep_block_tile(const SweepArgs &a, int p, int &t, int &bx) {
   if (sweep_reversed(a, p)) {
-    t = (int)gridDim.y - 1 - (int)blockIdx.y;
+    t = a.t_first + (int)gridDim.y - 1 - (int)blockIdx.y;
     bx = (int)gridDim.x - 1 - (int)blockIdx.x;
   } else {
-    t = (int)blockIdx.y;
+    t = a.t_first + (int)blockIdx.y;
     bx = (int)blockIdx.x;
   }
 }
@@ -328,14 +330,14 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
   typedef LinkIO<FMT_F32_12> IO;
   constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
   const int T = (int)blockDim.x, tid = (int)threadIdx.x, q = p ^ 1;
-  const int total = tiles_x * a.g.nt;
+  const int total = tiles_x * a.t_count;  // tiles of the launch's slices t_first ...
   const float4 *L = reinterpret_cast<const float4 *>(a.links);
   const float4 *Gs = reinterpret_cast<const float4 *>(a.G);
   const bool rev = sweep_reversed(a, p);
   auto issue = [&](int slot, int buf) {
     if (slot < total) {
       const int tile = rev ? total - 1 - slot : slot;
-      const int t = tile / tiles_x, j = (tile - t * tiles_x) * T + tid;
+      const int t = a.t_first + tile / tiles_x, j = (tile - (t - a.t_first) * tiles_x) * T + tid;
       if (!(a.active && !a.active[t]) && j < a.g.vs_half) {
         const Coords c = coords_in_slice(a.g, p, t, j);
         const int i = t * a.g.vs_half + j;
@@ -363,7 +365,7 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
     issue(slot + (int)gridDim.x, (it + 1) & 1);
     cp_async_wait<1>();  // this thread's copies of the current tile have landed
     const int tile = rev ? total - 1 - slot : slot;
-    const int t = tile / tiles_x, bx = tile - t * tiles_x;
+    const int t = a.t_first + tile / tiles_x, bx = tile - (t - a.t_first) * tiles_x;
     if (a.active && !a.active[t]) continue;  // the whole tile belongs to one slice
     const int j = bx * T + tid;
     float acc[2] = {0.0f, 0.0f};

@@ -97,6 +97,13 @@ _sigs = {
     "lgt_get_stats": ([_vp, _P(lgt_stats)], ctypes.c_int),
     "lgt_destroy": ([_vp], None),
     "lgt_inject_stream_stall": ([_vp, ctypes.c_uint64, ctypes.c_uint32], ctypes.c_int),
+    "lgt_slab_create": ([_P(lgt_params), ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int, _vp, _P(_vp)],
+                        ctypes.c_int),
+    "lgt_slab_half_sweep": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lgt_slab_boundary_bytes": ([_vp, _P(ctypes.c_size_t)], ctypes.c_int),
+    "lgt_slab_boundary": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32], ctypes.c_int),
+    "lgt_slab_sync": ([_vp], ctypes.c_int),
+    "lgt_measure_slice_sums": ([_vp, _vp], ctypes.c_int),
     "lgt_measure_noalloc": ([_P(ctypes.c_int32), _vp, _vp, _vp], ctypes.c_int),
     "lgt_server_create": ([ctypes.c_size_t, ctypes.c_int, _P(_vp)], ctypes.c_int),
     "lgt_submit": ([_vp, _P(lgt_params), _vp, _P(ctypes.c_uint64)], ctypes.c_int),
@@ -173,6 +180,42 @@ def lgt_create(params: lgt_params, links, stream=None):
     ptr, on_dev, _keep = _links_arg(links)
     out = _vp()
     _check(_lib.lgt_create(ctypes.byref(params), ptr, on_dev, _stream_arg(stream), ctypes.byref(out)))
+    return out
+
+
+def lgt_slab_create(params: lgt_params, nt_global: int, t0: int, links, stream=None):
+    """Context of a temporal slab: params.dims[0] owned slices starting at global slice t0."""
+    ptr, on_dev, _keep = _links_arg(links)
+    out = _vp()
+    _check(_lib.lgt_slab_create(ctypes.byref(params), int(nt_global), int(t0), ptr, on_dev, _stream_arg(stream),
+                                ctypes.byref(out)))
+    return out
+
+
+def lgt_slab_half_sweep(ctx, parity: int, first: int, count: int) -> None:
+    _check(_lib.lgt_slab_half_sweep(ctx, int(parity), int(first), int(count)))
+
+
+def lgt_slab_boundary_bytes(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib.lgt_slab_boundary_bytes(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def lgt_slab_boundary(ctx, slice_: int, parity: int, buf, into_slab: bool) -> None:
+    """Copy U_0 of one parity on one owned slice (-1: the halo) to / from buf, a
+    contiguous torch CUDA tensor of lgt_slab_boundary_bytes bytes."""
+    _check(_lib.lgt_slab_boundary(ctx, int(slice_), int(parity), buf.data_ptr(), 1 if into_slab else 0))
+
+
+def lgt_slab_sync(ctx) -> None:
+    _check(_lib.lgt_slab_sync(ctx))
+
+
+def lgt_measure_slice_sums(ctx, nt: int):
+    """Exact per-slice sums, shape (nt, 5) (see lgt.h); nt = the owned slices of a slab."""
+    out = np.zeros((int(nt), 5))
+    _check(_lib.lgt_measure_slice_sums(ctx, out.ctypes.data))
     return out
 
 
