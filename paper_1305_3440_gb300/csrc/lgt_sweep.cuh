@@ -636,63 +636,50 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
 }
 
 // ------------------------------------------------ maximally Abelian gauge
-// v of subgroup (I, J) for the site's links as the running g leaves them:
-// the (I, J) blocks of g U_mu(x) and U_mu(x-mu) g^dagger, formed from the
-// links (loaded again: L1/L2 hits after the first pass) and g.
-template <int FMT, typename R, int I, int J>
-__device__ __forceinline__ void mag_vector(const SweepArgs &a, int p, int i, const Coords &c, const R g[18], R v[3]) {
-  typedef LinkIO<FMT> IO;
-  const int q = p ^ 1;
-  v[0] = v[1] = v[2] = R(0);
-#pragma unroll 1
-  for (int mu = 0; mu < 4; mu++) {
-    R u[18];
-    IO::load(a.links, a.g.vh, p, mu, i, u);
-    // (g U)_ab = sum_k g_ak U_kb
-    R f[2][2][2];  // [a in (I, J)][b in (I, J)][re, im]
-#pragma unroll
-    for (int x = 0; x < 2; x++)
-#pragma unroll
-      for (int y = 0; y < 2; y++) {
-        const int ra = x ? J : I, cb = y ? J : I;
-        R re = R(0), im = R(0);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-          re += g[LGT_RE(ra, k)] * u[LGT_RE(k, cb)] - g[LGT_IM(ra, k)] * u[LGT_IM(k, cb)];
-          im += g[LGT_RE(ra, k)] * u[LGT_IM(k, cb)] + g[LGT_IM(ra, k)] * u[LGT_RE(k, cb)];
-        }
-        f[x][y][0] = re, f[x][y][1] = im;
-      }
-    mag_s<R>(f[0][0][0], f[0][0][1], f[1][0][0], f[1][0][1], R(1), v);   // s((gU)_II, (gU)_JI)
-    mag_s<R>(f[0][1][0], f[0][1][1], f[1][1][0], f[1][1][1], R(-1), v);  // - s((gU)_IJ, (gU)_JJ)
-    IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
-    // (U g^dagger)_ab = sum_k U_ak conj(g_bk)
-#pragma unroll
-    for (int x = 0; x < 2; x++)
-#pragma unroll
-      for (int y = 0; y < 2; y++) {
-        const int ra = x ? J : I, cb = y ? J : I;
-        R re = R(0), im = R(0);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-          re += u[LGT_RE(ra, k)] * g[LGT_RE(cb, k)] + u[LGT_IM(ra, k)] * g[LGT_IM(cb, k)];
-          im += u[LGT_IM(ra, k)] * g[LGT_RE(cb, k)] - u[LGT_RE(ra, k)] * g[LGT_IM(cb, k)];
-        }
-        f[x][y][0] = re, f[x][y][1] = im;
-      }
-    // s(conj B_II, conj B_IJ) - s(conj B_JI, conj B_JJ)
-    mag_s<R>(f[0][0][0], -f[0][0][1], f[0][1][0], -f[0][1][1], R(1), v);
-    mag_s<R>(f[1][0][0], -f[1][0][1], f[1][1][0], -f[1][1][1], R(-1), v);
-  }
+// Complex arithmetic of the subgroup steps (a value per (re, im) pair).
+template <typename R>
+struct Cx {
+  R re, im;
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_at(const R m[18], int a, int b) {
+  return Cx<R>{m[LGT_RE(a, b)], m[LGT_IM(a, b)]};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_mul(Cx<R> x, Cx<R> y) {
+  return Cx<R>{x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_mul_conj(Cx<R> x, Cx<R> y) {  // x conj(y)
+  return Cx<R>{x.re * y.re + x.im * y.im, x.im * y.re - x.re * y.im};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_add(Cx<R> x, Cx<R> y) {
+  return Cx<R>{x.re + y.re, x.im + y.im};
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cx_conj(Cx<R> x) {
+  return Cx<R>{x.re, -x.im};
 }
 
-// one subgroup step: the maximum of subgroup (I, J), overrelaxed or squared
-// (Sec. 3.1, 3.2), applied to g's rows I, J
-template <int FMT, typename R, int ALGO, int I, int J>
-__device__ __forceinline__ void mag_step(const SweepArgs &a, int p, int i, const Coords &c, R g[18], R omega,
-                                         uint64_t sr_thr, uint32_t draw) {
-  R v[3];
-  mag_vector<FMT, R, I, J>(a, p, i, c, g, v);
+// The 2x2 blocks a subgroup step needs: F = (g U)_{ab} and B = (U g^dagger)_{ab}
+// for a, b in (I, J), with the rows I, J of the running g given as complex
+// 3-vectors; the s-terms of the step's vector v (see mag_s above).
+template <typename R>
+__device__ __forceinline__ void mag_terms(Cx<R> f_ii, Cx<R> f_ij, Cx<R> f_ji, Cx<R> f_jj, Cx<R> b_ii, Cx<R> b_ij,
+                                          Cx<R> b_ji, Cx<R> b_jj, R v[3]) {
+  mag_s<R>(f_ii.re, f_ii.im, f_ji.re, f_ji.im, R(1), v);    // s((gU)_II, (gU)_JI)
+  mag_s<R>(f_ij.re, f_ij.im, f_jj.re, f_jj.im, R(-1), v);   // - s((gU)_IJ, (gU)_JJ)
+  mag_s<R>(b_ii.re, -b_ii.im, b_ij.re, -b_ij.im, R(1), v);  // s(conj B_II, conj B_IJ)
+  mag_s<R>(b_ji.re, -b_ji.im, b_jj.re, -b_jj.im, R(-1), v); // - s(conj B_JI, conj B_JJ)
+}
+
+// A subgroup element as the complex pair (a, b) of [[a, b], [-conj b, conj a]]
+// (a = r0 + i r3, b = r2 + i r1): the maximum of v, overrelaxed (Sec. 3.1) or
+// squared with probability p (Sec. 3.2).
+template <typename R, int ALGO>
+__device__ __forceinline__ void mag_element(const R v[3], R omega, uint64_t sr_thr, uint32_t draw, Cx<R> &ea,
+                                            Cx<R> &eb) {
   R r0, r1, r2, r3;
   mag_maximum<R>(v, r0, r1, r2, r3);
   if (ALGO == ALGO_OR) {
@@ -713,23 +700,20 @@ __device__ __forceinline__ void mag_step(const SweepArgs &a, int p, int i, const
     r3 *= two_r0;
     r0 = a0;
   }
-  // R_s = [[r0 + i r3, r2 + i r1], [-r2 + i r1, r0 - i r3]] on rows (I, J)
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const R gire = g[LGT_RE(I, k)], giim = g[LGT_IM(I, k)];
-    const R gjre = g[LGT_RE(J, k)], gjim = g[LGT_IM(J, k)];
-    g[LGT_RE(I, k)] = r0 * gire - r3 * giim + r2 * gjre - r1 * gjim;
-    g[LGT_IM(I, k)] = r0 * giim + r3 * gire + r2 * gjim + r1 * gjre;
-    g[LGT_RE(J, k)] = -r2 * gire - r1 * giim + r0 * gjre + r3 * gjim;
-    g[LGT_IM(J, k)] = -r2 * giim + r1 * gire + r0 * gjim - r3 * gjre;
-  }
+  ea = Cx<R>{r0, r3};
+  eb = Cx<R>{r2, r1};
 }
 
 // The half-sweep of the maximally Abelian gauge (one thread per site, any
-// link format; R = float for the FP32 formats, double for FP64).  The fused
-// estimate takes sum_a |U_aa|^2 over the site's 8 links (the parity-0 sums
-// give F_MAG, every link counted once) and tr Delta_MAG^2 from X(x), both
-// before the update.
+// link format; R = float for the FP32 formats, double for FP64).  The site
+// functional is quadratic in g, so K(x) does not suffice: each subgroup step
+// needs the (I, J) blocks of g U and U g^dagger of the site's 8 links under the
+// running g = R_{s-1} ... R_0.  That g is sparse in a known way -- after step
+// (0,1) row 2 is e_2, after step (0,2) row 1 still has no third entry -- so
+// the blocks are formed from the links with 2- and 3-term products instead of
+// full ones (the links are loaded again for each step: L1/L2 hits).  The first
+// pass also forms X(x) and the estimate: sum_a |U_aa|^2 over the 8 links (the
+// parity-0 sums give F_MAG, every link counted once) and tr Delta_MAG^2.
 template <int FMT, typename R, int ALGO>
 __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t, int bx) {
   typedef LinkIO<FMT> IO;
@@ -740,7 +724,11 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
     const Coords c = coords_in_slice(a.g, p, t, j);
     const int i = t * a.g.vs_half + j;
     const int q = p ^ 1;
-    R X[18];
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    const R omega = (R)a.omega;
+    // pass 1: X(x), the estimate, and step (0,1) with g = 1
+    R X[18], v[3] = {R(0), R(0), R(0)};
     mat_zero(X);
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
@@ -756,29 +744,83 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
         }
 #pragma unroll
       for (int x = 0; x < 3; x++) acc[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
-      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+      R w[18];
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
       // X -= D^dagger U: X_ab -= conj(U_aa) U_ab
 #pragma unroll
       for (int x = 0; x < 3; x++)
 #pragma unroll
         for (int y = 0; y < 3; y++) {
-          X[LGT_RE(x, y)] -= u[LGT_RE(x, x)] * u[LGT_RE(x, y)] + u[LGT_IM(x, x)] * u[LGT_IM(x, y)];
-          X[LGT_IM(x, y)] -= u[LGT_RE(x, x)] * u[LGT_IM(x, y)] - u[LGT_IM(x, x)] * u[LGT_RE(x, y)];
+          X[LGT_RE(x, y)] -= w[LGT_RE(x, x)] * w[LGT_RE(x, y)] + w[LGT_IM(x, x)] * w[LGT_IM(x, y)];
+          X[LGT_IM(x, y)] -= w[LGT_RE(x, x)] * w[LGT_IM(x, y)] - w[LGT_IM(x, x)] * w[LGT_RE(x, y)];
         }
 #pragma unroll
-      for (int x = 0; x < 3; x++) acc[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
+      for (int x = 0; x < 3; x++) acc[0] += w[LGT_RE(x, x)] * w[LGT_RE(x, x)] + w[LGT_IM(x, x)] * w[LGT_IM(x, x)];
+      mag_terms<R>(cx_at(u, 0, 0), cx_at(u, 0, 1), cx_at(u, 1, 0), cx_at(u, 1, 1), cx_at(w, 0, 0), cx_at(w, 0, 1),
+                   cx_at(w, 1, 0), cx_at(w, 1, 1), v);
     }
     R unused;
     violation_of_K(X, unused, acc[1]);  // Delta: traceless part of (X - X^dagger)/(2i)
-    uint4 draws = make_uint4(0, 0, 0, 0);
-    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    Cx<R> a0, b0;
+    mag_element<R, ALGO>(v, omega, a.sr_thr, draws.x, a0, b0);
+    // pass 2: step (0,2); rows 0 and 2 of g = R_0: (a0, b0, 0) and e_2
+    v[0] = v[1] = v[2] = R(0);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; mu++) {
+      R u[18], w[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
+      const Cx<R> f00 = cx_add(cx_mul(a0, cx_at(u, 0, 0)), cx_mul(b0, cx_at(u, 1, 0)));
+      const Cx<R> f02 = cx_add(cx_mul(a0, cx_at(u, 0, 2)), cx_mul(b0, cx_at(u, 1, 2)));
+      // (U g^dagger)_{x0} = U_x0 conj(a0) + U_x1 conj(b0), (U g^dagger)_{x2} = U_x2
+      const Cx<R> b00 = cx_add(cx_mul_conj(cx_at(w, 0, 0), a0), cx_mul_conj(cx_at(w, 0, 1), b0));
+      const Cx<R> b20 = cx_add(cx_mul_conj(cx_at(w, 2, 0), a0), cx_mul_conj(cx_at(w, 2, 1), b0));
+      mag_terms<R>(f00, f02, cx_at(u, 2, 0), cx_at(u, 2, 2), b00, cx_at(w, 0, 2), b20, cx_at(w, 2, 2), v);
+    }
+    Cx<R> a1, b1;
+    mag_element<R, ALGO>(v, omega, a.sr_thr, draws.y, a1, b1);
+    // pass 3: step (1,2); row 1 of g = (-conj b0, conj a0, 0), row 2 = (-conj b1 a0, -conj b1 b0, conj a1)
+    const Cx<R> g10 = Cx<R>{-b0.re, b0.im}, g11 = cx_conj(a0);
+    const Cx<R> nb1 = Cx<R>{-b1.re, b1.im};  // -conj b1
+    const Cx<R> g20 = cx_mul(nb1, a0), g21 = cx_mul(nb1, b0), g22 = cx_conj(a1);
+    v[0] = v[1] = v[2] = R(0);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; mu++) {
+      R u[18], w[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
+      Cx<R> f[2][2], b[2][2];
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        const int col = 1 + y;
+        f[0][y] = cx_add(cx_mul(g10, cx_at(u, 0, col)), cx_mul(g11, cx_at(u, 1, col)));
+        f[1][y] = cx_add(cx_add(cx_mul(g20, cx_at(u, 0, col)), cx_mul(g21, cx_at(u, 1, col))),
+                         cx_mul(g22, cx_at(u, 2, col)));
+        const int row = 1 + y;
+        b[y][0] = cx_add(cx_mul_conj(cx_at(w, row, 0), g10), cx_mul_conj(cx_at(w, row, 1), g11));
+        b[y][1] = cx_add(cx_add(cx_mul_conj(cx_at(w, row, 0), g20), cx_mul_conj(cx_at(w, row, 1), g21)),
+                         cx_mul_conj(cx_at(w, row, 2), g22));
+      }
+      mag_terms<R>(f[0][0], f[0][1], f[1][0], f[1][1], b[0][0], b[0][1], b[1][0], b[1][1], v);
+    }
+    Cx<R> a2, b2;
+    mag_element<R, ALGO>(v, omega, a.sr_thr, draws.z, a2, b2);
+    // g = R_2 R_1 R_0: rows 0 = a1 (a0, b0, 0) + b1 e_2 and rows 1, 2 from step (1,2)
     R g[18];
-    mat_zero(g);
-    g[LGT_RE(0, 0)] = g[LGT_RE(1, 1)] = g[LGT_RE(2, 2)] = R(1);
-    const R omega = (R)a.omega;
-    mag_step<FMT, R, ALGO, 0, 1>(a, p, i, c, g, omega, a.sr_thr, draws.x);
-    mag_step<FMT, R, ALGO, 0, 2>(a, p, i, c, g, omega, a.sr_thr, draws.y);
-    mag_step<FMT, R, ALGO, 1, 2>(a, p, i, c, g, omega, a.sr_thr, draws.z);
+    {
+      const Cx<R> r0c[3] = {cx_mul(a1, a0), cx_mul(a1, b0), b1};
+      const Cx<R> r1c[3] = {g10, g11, Cx<R>{R(0), R(0)}};
+      const Cx<R> r2c[3] = {g20, g21, g22};
+      const Cx<R> nb2 = Cx<R>{-b2.re, b2.im}, ca2 = cx_conj(a2);
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const Cx<R> n1 = cx_add(cx_mul(a2, r1c[k]), cx_mul(b2, r2c[k]));
+        const Cx<R> n2 = cx_add(cx_mul(nb2, r1c[k]), cx_mul(ca2, r2c[k]));
+        g[LGT_RE(0, k)] = r0c[k].re, g[LGT_IM(0, k)] = r0c[k].im;
+        g[LGT_RE(1, k)] = n1.re, g[LGT_IM(1, k)] = n1.im;
+        g[LGT_RE(2, k)] = n2.re, g[LGT_IM(2, k)] = n2.im;
+      }
+    }
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
       const int nb = cb_shift(a.g, c, mu, -1);
@@ -804,6 +846,7 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
   }
   fused_store<R, 1>(a, p, t, bx, acc);
 }
+
 
 // FP32 link formats, four threads per site: thread m of the site's quad owns
 // direction m (for Coulomb gauge thread 0 owns the temporal links, which the
