@@ -431,6 +431,25 @@ def run_ours(args):
                     variants[name]["F_minus_headline_F"] = rv.F - results[-1]["F"]
             finally:
                 lgt.lgt_destroy(cv)
+    # ---- SU(3) Coulomb gauge on 48^3 x 96 (96 timeslices per launch, per-slice theta_t <
+    # 1e-14, eps 0.5, seed 3; the workload fixes no omega: the measured schedule)
+    if not args.no_fp64_compare and rank == 0:
+        cdims = (96, 48, 48, 48)
+        cdev = torch.from_numpy(synth.field(cdims, 0.5, 3)).to(f"cuda:{local}")
+        pc = lgt.lgt_params_default(dims=cdims, gauge=lgt.LGT_COULOMB, bulk=lgt.LGT_FP32_12, max_sweeps=50000,
+                                    **SERVE_OMEGA)
+        cc = lgt.lgt_create(pc, cdev, stream=stream)
+        try:
+            sec, stc, rc, sc = _timed_fix(lgt, cc, cdev, stream)
+            th_t = lgt.lgt_measure_slices(cc, cdims[0])[1]
+            variants["coulomb_48x3x96"] = {
+                "seconds": sec, "status": stc, "sweeps_bulk": rc.sweeps_bulk, "sweeps_polish": rc.sweeps_fp64,
+                "F_mean": rc.F, "theta_t_max": float(th_t.max()), "slices": cdims[0],
+                "site_updates_per_s": (sc.site_updates[0] + sc.site_updates[1]) / sec,
+                "launch_config": list(sc.launch_config), "omega": "1.7 -> 1.1 below theta 1e-2"}
+        finally:
+            lgt.lgt_destroy(cc)
+        del cdev
     lgt.lgt_destroy(ctx)
     # ---- a bounded sample of the served stream (p50/p99 latency beside jobs/s)
     serve = None

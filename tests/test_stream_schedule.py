@@ -142,3 +142,88 @@ def test_a_weaker_rule_is_caught():
         except AssertionError:
             caught += 1
     assert caught > 0
+
+
+def run_stalled(nt, tiles_x, n_half, nblocks, seed, skip, wait_limit):
+    """The same protocol when the launch's first `skip` tickets are never taken (the
+    host's fault injection) and each wait gives up after `wait_limit` looks: the
+    block that gives up raises the abort flag, a block that finds the flag raised
+    when it would wait ends, and the next ticket a block looks at is not staged
+    once the flag is up.  Returns (aborted, started items)."""
+    rng = random.Random(seed)
+    total = tiles_x * nt * n_half
+    done = [0] * nt
+    finished, started = set(), set()
+    ticket = [skip]
+    abort = [False]
+    in_flight = {}
+
+    def take():
+        n = ticket[0]
+        ticket[0] += 1
+        staged = n < total and not abort[0] and ready(done, *item(n, tiles_x, nt)[:2], tiles_x, nt)
+        return n, staged
+
+    blocks = []  # [state, cur, staged, nxt, nxt_staged, waits]
+    for _ in range(nblocks):
+        n, st = take()
+        blocks.append(["start", n, st, None, None, 0])
+    steps = 0
+    while True:
+        live = [b for b in blocks if b[0] != "exit" and b[1] < total]
+        if not live:
+            break
+        b = rng.choice(live)
+        steps += 1
+        assert steps < 100 * total + 100 * nblocks * (wait_limit + 2), "the launch did not end"
+        if b[0] == "take":
+            b[3], b[4] = take()
+            b[0] = "start"
+            b[1], b[2] = b[3], b[4]
+        elif b[0] == "start":
+            h, t, _ = item(b[1], tiles_x, nt)
+            if not b[2]:  # the bounded wait
+                if abort[0]:
+                    b[0] = "exit"
+                    continue
+                if not ready(done, h, t, tiles_x, nt):
+                    b[5] += 1
+                    if b[5] > wait_limit:
+                        abort[0] = True
+                        b[0] = "exit"
+                    continue
+            b[5] = 0
+            if h > 0:  # dependencies as in the normal run
+                for d in (-1, 0, 1):
+                    tt = (t + d) % nt
+                    for x in range(tiles_x):
+                        n_prev = ((h - 1) * nt + ((tt - (h - 1)) % nt)) * tiles_x + x
+                        assert n_prev in finished
+            mine = {t, (t - 1) % nt}
+            for (h2, t2) in in_flight.values():
+                if h2 != h:
+                    assert not (mine & {t2, (t2 - 1) % nt})
+            in_flight[b[1]] = (h, t)
+            started.add(b[1])
+            b[0] = "finish"
+        else:  # finish: publish; then the next ticket
+            h, t = in_flight.pop(b[1])
+            finished.add(b[1])
+            done[t] += 1
+            b[0] = "take"
+    assert not in_flight
+    return abort[0], started
+
+
+@pytest.mark.parametrize("nt,tiles_x,n_half,nblocks,skip", [
+    (8, 1, 2, 8, 1), (8, 1, 4, 3, 3), (6, 2, 5, 12, 2), (12, 4, 8, 40, 5), (4, 3, 6, 2, 1)])
+def test_injected_stall_ends_the_launch_through_the_abort_flag(nt, tiles_x, n_half, nblocks, skip):
+    """lgt_inject_stream_stall: the skipped items never run, so the half-sweep after
+    them waits on slices that never become ready; a wait runs out, raises the
+    abort flag, and every block ends (none is left waiting), with the items that
+    did run still race-free and in dependency order."""
+    for seed in range(8):
+        aborted, started = run_stalled(nt, tiles_x, n_half, nblocks, seed, skip, wait_limit=5)
+        assert aborted
+        assert not (started & set(range(skip)))
+        assert len(started) < tiles_x * nt * n_half - skip  # work was left undone
