@@ -376,6 +376,10 @@ def run_ours(args):
                                             d["launch_config"]),
                 "kernel": f"half-sweep {dom}", "peak_source": src,
                 "bytes_per_site_update": algorithmic_bytes_per_site(dom), "units_per_launch": vol // 2}
+    if roofline["traffic"]:  # the DRAM bandwidth the kernel draws (L2 serves the rest of the algorithmic bytes)
+        avg_s = d["bytes_per_launch"] / (d["achieved_gbs"] * 1e9)
+        roofline["dram_gbs"] = roofline["traffic"] / avg_s / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / peaks["hbm_gbs"]
 
     # ---- all-FP64 time to theta < 1e-14 on the same field, for the ladder comparison
     ttt = {"mixed_s": elapsed / args.steps}
