@@ -89,6 +89,10 @@ def _load():
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                                 ctypes.c_uint64, _dp]
             L.orc_parity_violation.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_sa_half_sweep.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+            L.orc_sa_site_stats.argtypes = [_i32p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_uint64, ctypes.c_uint64, _dp, _dp]
             L.orc_set_threads.restype = None
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -260,6 +264,25 @@ def sa_sweeps(links, n, beta0, beta1, gauge=LANDAU, seed=0, sweep0=0, transform_
     _check(L.orc_sa_sweeps(d, links.ctypes.data, gauge, float(beta0), float(beta1), int(n), seed, sweep0,
                            transform_temporal), "orc_sa_sweeps")
     return links
+
+
+def sa_half_sweep(links, parity, beta, gauge=LANDAU, seed=0, sweep=0, transform_temporal=1):
+    """One simulated-annealing half-sweep in place (the heat-bath steps of sa_sweeps)."""
+    d = _dims_of(links)
+    _check(_load().orc_sa_half_sweep(d, links.ctypes.data, gauge, parity, float(beta), seed, sweep,
+                                     transform_temporal), "orc_sa_half_sweep")
+    return links
+
+
+def sa_site_stats(links, parity, beta, gauge=LANDAU, seed=0, sweep=0):
+    """(kappa, margin) per site of one parity for the annealing update (test
+    infrastructure; see the C source); NaN at the other parity."""
+    d = _dims_of(links)
+    kap = np.full(links.shape[:4], np.nan)
+    mar = np.full(links.shape[:4], np.nan)
+    _check(_load().orc_sa_site_stats(d, links.ctypes.data, gauge, parity, float(beta), seed, sweep,
+                                     kap.ctypes.data, mar.ctypes.data), "orc_sa_site_stats")
+    return kap, mar
 
 
 def kp_draws(alpha, n, seed=0):

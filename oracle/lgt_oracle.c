@@ -445,13 +445,17 @@ static void sa_uniforms(uint64_t seed, uint64_t sweep, int64_t site, int s, uint
  * exp(-alpha delta); accepting with probability sqrt(1 - delta / 2) supplies
  * the rest of sqrt(1 - x^2) = sqrt(2 delta) sqrt(1 - delta / 2), x = 1 - delta.
  * Returns 0 on success, 1 when every attempt was rejected. */
-static int kp_draw(double alpha, uint64_t seed, uint64_t sweep, int64_t site, int s, double *x) {
+static int kp_draw(double alpha, uint64_t seed, uint64_t sweep, int64_t site, int s, double *x, double *margin) {
   const double two_pi = 6.283185307179586476925286766559;
   for (uint32_t k = 0; k < SA_MAX_ATTEMPTS; k++) {
     double u[4];
     sa_uniforms(seed, sweep, site, s, k, u);
     const double c = cos(two_pi * u[1]);
     const double delta = -(log(u[0]) + c * c * log(u[2])) / alpha;
+    if (margin) {  /* how close this comparison came to its threshold, relative to delta */
+      const double m = fabs(u[3] * u[3] - (1.0 - 0.5 * delta)) / (fabs(delta) > 1.0 ? fabs(delta) : 1.0);
+      if (m < *margin) *margin = m;
+    }
     if (u[3] * u[3] <= 1.0 - 0.5 * delta) {
       *x = 1.0 - delta;
       return 0;
@@ -476,10 +480,10 @@ static void su2_mul(const double a[4], const double b[4], double r[4]) {
 
 /* heat-bath element for the block projection q at inverse temperature beta */
 static void su2_heatbath(const double q[4], double beta, uint64_t seed, uint64_t sweep, int64_t site, int s,
-                         double r[4]) {
+                         double r[4], double *margin) {
   const double norm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   double x;
-  if (!(norm > 0.0) || !(beta > 0.0) || kp_draw(2.0 * beta * norm, seed, sweep, site, s, &x)) {
+  if (!(norm > 0.0) || !(beta > 0.0) || kp_draw(2.0 * beta * norm, seed, sweep, site, s, &x, margin)) {
     r[0] = 1.0; /* no update of this subgroup */
     r[1] = r[2] = r[3] = 0.0;
     return;
@@ -509,6 +513,8 @@ typedef struct {
   uint64_t seed;     /* simulated annealing: stream of the site, sweep below */
   uint64_t sweep;
   int64_t site;
+  double *margin;    /* simulated annealing, test support (nullable): the smallest relative margin of
+                        the heat bath's accept/reject comparisons */
 } update_rule;
 
 /* Section 3: maximise f = Re tr[g K] by iterating over the three SU(2)
@@ -524,7 +530,7 @@ static su3 local_gauge_update(const su3 *K, const update_rule *rule, const uint3
     double q[4], r[4];
     su2_project(W.e[i][i], W.e[i][j], W.e[j][i], W.e[j][j], q);
     if (rule->algo == ORC_SA) {
-      su2_heatbath(q, rule->beta, rule->seed, rule->sweep, rule->site, s, r);
+      su2_heatbath(q, rule->beta, rule->seed, rule->sweep, rule->site, s, r, rule->margin);
     } else {
       su2_maximum(q, r);
       if (rule->algo == ORC_OR) {
@@ -815,6 +821,7 @@ static sweep_cfg make_cfg(int gauge, int algo, double omega, double p, uint64_t 
   c.rule.seed = seed;
   c.rule.sweep = 0;
   c.rule.site = 0;
+  c.rule.margin = NULL;
   c.seed = seed;
   c.transform_temporal = transform_temporal;
   c.site_offset = 0;
@@ -920,6 +927,7 @@ void orc_local_update(const double *K, int algo, double omega, double p, const u
   rule.seed = 0;
   rule.sweep = 0;
   rule.site = 0;
+  rule.margin = NULL;
   uint32_t u[3] = {0, 0, 0};
   if (draws) { u[0] = draws[0]; u[1] = draws[1]; u[2] = draws[2]; }
   su3 g = local_gauge_update(&k, &rule, u, W, R);
@@ -1030,6 +1038,58 @@ int orc_parity_violation(const int32_t dims[4], const double *links, int gauge, 
   return 0;
 }
 
+/* One simulated-annealing half-sweep over `parity` at inverse temperature
+ * beta (the heat-bath steps of orc_sa_sweeps; see su2_heatbath). */
+int orc_sa_half_sweep(const int32_t dims[4], double *links, int gauge, int parity, double beta, uint64_t seed,
+                      uint64_t sweep, int transform_temporal) {
+  if (check_dims(dims) || !(beta > 0.0) || gauge == ORC_MAG) return -1;
+  const lattice l = make_lattice(dims);
+  sweep_cfg cfg = make_cfg(gauge, ORC_SA, 1.0, 0.0, seed, transform_temporal);
+  cfg.rule.beta = beta;
+  half_sweep(&l, links, parity & 1, &cfg, sweep, NULL, NULL);
+  return 0;
+}
+
+/* Per site of one parity, for the annealing update at inverse temperature beta
+ * on the current links (TEST INFRASTRUCTURE for the FP32 annealing parity):
+ * kappa_out[site] = 1 / min_s |q_s| as orc_site_conditioning, and
+ * margin_out[site] = the smallest relative margin |u_3^2 - (1 - delta/2)| /
+ * max(1, |delta|) of the Kennedy-Pendleton comparisons the update evaluates:
+ * where it is within FP32 rounding, an FP32 update may take the other branch
+ * and draw a different element.  Sites of the other parity are left untouched. */
+int orc_sa_site_stats(const int32_t dims[4], const double *links, int gauge, int parity, double beta, uint64_t seed,
+                      uint64_t sweep, double *kappa_out, double *margin_out) {
+  if (check_dims(dims) || !(beta > 0.0) || gauge == ORC_MAG) return -1;
+  const lattice l = make_lattice(dims);
+  const sweep_cfg cfg = make_cfg(gauge, ORC_SA, 1.0, 0.0, seed, 1);
+  const int64_t nh = l.vol / 2;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < nh; k++) {
+    const int64_t site = parity_site(&l, parity, k);
+    update_rule rule = cfg.rule;
+    double margin = INFINITY;
+    rule.beta = beta;
+    rule.seed = seed;
+    rule.sweep = sweep;
+    rule.site = site;
+    rule.margin = &margin;
+    const uint32_t u[3] = {0, 0, 0};
+    su3 K = gather_K(&l, links, site, gauge), W[3];
+    local_gauge_update(&K, &rule, u, W, NULL);
+    double qmin = INFINITY;
+    for (int s = 0; s < 3; s++) {
+      const int i = SUBGROUP[s][0], j = SUBGROUP[s][1];
+      double q[4];
+      su2_project(W[s].e[i][i], W[s].e[i][j], W[s].e[j][i], W[s].e[j][j], q);
+      const double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+      if (nq < qmin) qmin = nq;
+    }
+    kappa_out[site] = qmin > 0.0 ? 1.0 / qmin : INFINITY;
+    margin_out[site] = margin;
+  }
+  return 0;
+}
+
 /* K(x) of the current links (18 doubles) */
 int orc_gather_K(const int32_t dims[4], const double *links, int64_t site, int gauge, double *K_out) {
   if (check_dims(dims)) return -1;
@@ -1076,7 +1136,7 @@ int orc_kp_draws(double alpha, int64_t n, uint64_t seed, double *out) {
   int fails = 0;
   for (int64_t k = 0; k < n; k++) {
     double x;
-    if (kp_draw(alpha, seed, 0, k, 0, &x)) {
+    if (kp_draw(alpha, seed, 0, k, 0, &x, NULL)) {
       out[k] = NAN;
       fails++;
     } else {
@@ -1090,7 +1150,7 @@ int orc_kp_draws(double alpha, int64_t n, uint64_t seed, double *out) {
  * would draw it for site, subgroup s, sweep). */
 void orc_su2_heatbath(const double *q, double beta, uint64_t seed, uint64_t sweep, int64_t site, int s,
                       double *r_out) {
-  su2_heatbath(q, beta, seed, sweep, site, s, r_out);
+  su2_heatbath(q, beta, seed, sweep, site, s, r_out, NULL);
 }
 
 double orc_sa_beta(double beta0, double beta1, int n, int i) { return sa_beta(beta0, beta1, n, i); }

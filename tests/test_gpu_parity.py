@@ -912,9 +912,52 @@ def test_annealing_sweeps_match_the_oracle(lgt, gauge):
         err = np.abs(V - ref)
         if bulk == lgt.LGT_FP64:
             assert err.max() < tol, err.max()
-        else:
-            assert np.mean(err < tol) > 0.995, np.mean(err < tol)
+        # (FP32: element by element in test_fp32_annealing_sweep_matches_the_oracle_but_near_thresholds)
         assert np.abs(plaquettes(Vg) - plaquettes(U)).max() < 1e-12
+
+
+@pytest.mark.parametrize("gauge", list(GAUGES))
+def test_fp32_annealing_sweep_matches_the_oracle_but_near_thresholds(lgt, gauge):
+    """One FP32 annealing sweep (beta = 2) against the oracle's, element by element.
+    The heat bath draws from the same Philox streams; FP32 rounding moves a
+    Kennedy-Pendleton comparison u^2 <= 1 - delta/2 across its threshold only where
+    the oracle's margin is within it, and there the site may draw another element
+    (and the odd sites next to such an even site see another K).  Those sites are
+    the ones whose smallest relative margin (oracle, each half on the field it
+    started from) is below 1e-4, two orders above the FP32 error of delta (~8u
+    times (1 + kappa)); their links are excused, they must be few, and every other
+    entry agrees within 1e-5."""
+    from lattice_np import link_endpoint, parity_field, shift
+    g = GAUGES[gauge]
+    dims = DIMS_RAGGED
+    U = synth.field(dims, 0.5, 51)
+    beta = 2.0
+    ref = U.copy()
+    O.sa_sweeps(ref, 1, beta, beta, gauge=g, seed=13)
+    p = lgt.lgt_params_default(dims=dims, gauge=g, bulk=lgt.LGT_FP32_12, seed=13, sa_sweeps=1, sa_beta0=beta,
+                               sa_beta1=beta, max_sweeps=1, reunit_every=0)
+    ctx = lgt.lgt_create(p, U)
+    try:
+        st, res = lgt.lgt_fix(ctx)
+        V = lgt.lgt_get_working_links(ctx, dims)
+    finally:
+        lgt.lgt_destroy(ctx)
+    assert st == lgt.LGT_ENOTCONV and res.sweeps_bulk == 1
+    _, m_even = O.sa_site_stats(U, 0, beta, gauge=g, seed=13)
+    half = U.copy()
+    O.sa_half_sweep(half, 0, beta, gauge=g, seed=13)
+    _, m_odd = O.sa_site_stats(half, 1, beta, gauge=g, seed=13)
+    par = parity_field(dims)
+    near_even = (par == 0) & (np.nan_to_num(m_even, nan=1.0) < 1e-4)
+    near_odd = (par == 1) & (np.nan_to_num(m_odd, nan=1.0) < 1e-4)
+    beside = np.zeros(dims, bool)
+    for mu in range(4):
+        beside |= shift(near_even, mu, 1) | shift(near_even, mu, -1)
+    flagged = (near_even | near_odd | ((par == 1) & beside)).astype(float)
+    excused = (link_endpoint(flagged, 0) + link_endpoint(flagged, 1)) > 0
+    err = np.abs(V - ref).max(axis=(-1, -2))
+    assert excused.mean() < 0.02, excused.mean()
+    assert err[~excused].max() < 1e-5, (err[~excused].max(), int(excused.sum()))
 
 
 def test_annealing_then_relaxation(lgt):

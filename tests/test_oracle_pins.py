@@ -880,3 +880,37 @@ def test_parity_violation_is_the_violation_of_K(gauge):
         assert np.allclose(both / (3 * vs), m["theta_t"], rtol=1e-12, atol=0)
     else:
         assert abs(both.sum() / (3 * np.prod(dims)) - m["theta"]) < 1e-12 * m["theta"]
+
+
+# ------------------------------- annealing decision margins (test support)
+def test_annealing_half_sweeps_and_decision_margins():
+    """Two annealing half-sweeps are the oracle's annealing sweep; and the
+    reported margins of the Kennedy-Pendleton comparisons mark where a decision
+    can flip.  Stepping beta by a relative h moves delta (proportional to 1/beta)
+    by h |delta|, so the comparison u^2 <= 1 - delta/2 can change side over a
+    step only where its relative margin is below h/2 on one side of the step:
+    across a fine scan every jump of a site's element (a flipped decision) sits
+    at such a margin, and there are jumps to check."""
+    dims = (4, 4, 6, 4)
+    U = synth.field(dims, 0.6, 77)
+    ref = U.copy()
+    O.sa_sweeps(ref, 1, 1.5, 1.5, seed=19)
+    h = U.copy()
+    O.sa_half_sweep(h, 0, 1.5, seed=19)
+    O.sa_half_sweep(h, 1, 1.5, seed=19)
+    assert np.array_equal(h, ref)
+    betas = np.linspace(1.0, 2.0, 401)
+    prev = prev_m = None
+    jumps = 0
+    for b0, b in zip(np.r_[np.nan, betas[:-1]], betas):
+        a = U.copy()
+        O.sa_half_sweep(a, 0, b, seed=19)
+        _, m = O.sa_site_stats(U, 0, b, seed=19)
+        if prev is not None:
+            moved = np.abs(a - prev).max(axis=(-3, -2, -1))  # per site: its forward links
+            step = (b - b0) / b0
+            jump = ~np.isnan(m) & (moved > 5e-2)
+            jumps += int(jump.sum())
+            assert np.all(np.minimum(m[jump], prev_m[jump]) <= 0.5 * step * 1.05)
+        prev, prev_m = a, m
+    assert jumps > 20
