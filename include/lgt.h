@@ -135,7 +135,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..11: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..12: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
   int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
@@ -182,9 +182,10 @@ typedef struct {
  *                         7: 128 threads, <= 255 registers, persistent blocks
  *                            (2 per SM) that stage the next site's links and G
  *                            in shared memory (cp.async) during the update;
- *   one thread per site, lean (FP32 bulk sweeps only): K(x) streamed, links
- *   loaded again for the write-back:
+ *   one thread per site, lean (FP32 bulk sweeps only): K(x) accumulated link by
+ *   link, links loaded again for the write-back:
  *                         8: 128 threads, <= 128 registers; 9: 128, <= 96;
+ *                        11: 128, <= 80 (24 warps per SM);
  *   one thread per site, streaming (FP32-12 bulk sweeps only):
  *                        10: as 7, but one launch runs up to 64 half-sweeps:
  *                            blocks take (half-sweep, slice, 8 tiles) items
@@ -192,11 +193,12 @@ typedef struct {
  *                            the previous half-sweep has finished its slice
  *                            and both neighbours (bounded waits: a wait over
  *                            2 s fails the call with LGT_ETIMEOUT).
- * A configuration that a phase's kernel lacks (4-10 after promotion; 7 and 10
+ * A configuration that a phase's kernel lacks (4-11 after promotion; 7 and 10
  * on FP32-18 links) falls back to configuration 0 for that phase.  Every
- * configuration forms K(x) and the fused estimate in the same order; results
- * differ only where the compiler fuses multiply-adds differently in the two
- * kernels (FP32 rounding; converged F within 1e-10). */
+ * configuration groups the fused estimate by the same 8 sites; results differ
+ * only in FP32 rounding (the lean configurations sum K(x) link by link, the
+ * others pairwise; and where the compiler fuses multiply-adds), converged F
+ * within 1e-10. */
 
 /* Fill *p with defaults: Landau, OR, omega 1.7, FP64, tol 1e-14,
  * theta_switch 1e-13, max_sweeps 10000, check_every 10, reunit_every 50,

@@ -213,22 +213,25 @@ struct SweepCfg {
 //   half-sweep has finished the item's slice and its two neighbours, so the
 //   pipeline does not drain between half-sweeps; staging as configuration 7:
 //    10: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
-// Every configuration forms K(x) in the same order and groups the fused
-// estimate by the same 8 sites; results differ only where the compiler fuses
-// multiply-adds differently in two kernels (FP32 rounding).  The maximally
-// Abelian gauge has kernels in configurations 0-3 only.
-constexpr int LGT_NCFG = 11;
+//   one thread per site, lean as 8 and 9, more warps per SM:
+//    11: 128 threads, <= 80 registers (6 blocks, 24 warps per SM)
+// The one-thread and four-thread layouts form K(x) in the same order, the lean
+// ones link by link; every configuration groups the fused estimate by the same
+// 8 sites; results differ only in FP32 rounding (the order of K's sums and
+// where the compiler fuses multiply-adds).  The maximally Abelian gauge has
+// kernels in configurations 0-3 only.
+constexpr int LGT_NCFG = 12;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
   return c == 1 ? 3
                 : (c == 3 ? 8
                           : (c == 4 ? 4
                                     : (c == 5 ? 2
-                                              : (c == 6 ? 6 : (c == 7 || c == 10 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : 1)))))));
+                                              : (c == 6 ? 6 : (c == 7 || c == 10 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : (c == 11 ? 6 : 1))))))));
 }
 __host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4 && c <= 6; }
 __host__ __device__ constexpr bool lgt_cfg_pipe(int c) { return c == 7; }
-__host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9; }
+__host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9 || c == 11; }
 __host__ __device__ constexpr bool lgt_cfg_stream(int c) { return c == 10; }
 // sites covered by one block (per tile for the pipelined configuration)
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }

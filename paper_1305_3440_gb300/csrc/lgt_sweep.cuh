@@ -248,30 +248,19 @@ __device__ __forceinline__ void sweep_body_f32_lean(const SweepArgs &a, int p, i
     const Coords c = coords_in_slice(a.g, p, t, j);
     const int i = t * a.g.vs_half + j;
     const int q = p ^ 1;
-    // K(x) = (k_0 + k_1) + (k_2 + k_3), as the other layouts
-    float W[18], k2[18];
+    // K(x) = sum_mu U_mu(x) + U_mu(x - mu)^dagger accumulated link by link: one
+    // link in registers at a time (the other layouts' pairwise order needs three
+    // matrices live; the sums differ only in FP32 rounding)
+    float W[18];
+    mat_zero(W);
 #pragma unroll 1
-    for (int h = 0; h < 2; h++) {
-      float ka[18], kb[18];
-#pragma unroll
-      for (int d = 0; d < 2; d++) {
-        const int mu = 2 * h + d;
-        float *k = d ? kb : ka;
-        if (mu < MU0) {
-          mat_zero(k);
-        } else {
-          float uf[18], ub[18];
-          IO::load(a.links, a.g.vh, p, mu, i, uf);
-          IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), ub);
-          k_term(k, uf, ub);
-        }
-      }
-      float *dst = h ? k2 : W;
-#pragma unroll
-      for (int e = 0; e < 18; e++) dst[e] = ka[e] + kb[e];
+    for (int mu = MU0; mu < 4; mu++) {
+      float u[18];
+      IO::load(a.links, a.g.vh, p, mu, i, u);
+      acc_add(W, u);
+      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), u);
+      acc_add_dag(W, u);
     }
-#pragma unroll
-    for (int e = 0; e < 18; e++) W[e] = W[e] + k2[e];
     violation_of_K(W, acc[0], acc[1]);
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);

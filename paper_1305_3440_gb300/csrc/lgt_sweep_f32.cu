@@ -76,6 +76,7 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 8: return pick_cfg<8>(fmt, gauge, algo);
     case 9: return pick_cfg<9>(fmt, gauge, algo);
     case 10: return pick_cfg<10>(fmt, gauge, algo);
+    case 11: return pick_cfg<11>(fmt, gauge, algo);
   }
   return nullptr;
 }

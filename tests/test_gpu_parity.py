@@ -627,18 +627,22 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
 @pytest.mark.parametrize("algo", list(ALGOS))
 def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     """Every launch configuration (one or four threads per site, every block size,
-    pipelined through shared memory, lean, streaming) forms K(x) in the same order and groups the
-    fused estimate by the same 8 sites; what remains is where the compiler fuses
-    multiply-adds in each kernel (FP32 rounding, which a nearly degenerate SU(2)
-    projection can amplify along a trajectory).  So the test compares what the
-    method fixes: one half-sweep agrees to FP32 rounding, and ladder runs
-    converge to the same F.  The ragged lattice leaves a partial block in every
+    pipelined through shared memory, lean, streaming) groups the fused estimate
+    by the same 8 sites; they differ in FP32 rounding only (the lean ones sum
+    K(x) link by link, the others pairwise, and the compiler fuses multiply-adds
+    differently in each kernel), which an ill-conditioned site update amplifies.
+    So the test compares what the method fixes: each configuration's half-sweep
+    is within the per-site FP32 bound of the oracle's, and ladder runs converge
+    to the same F.  The ragged lattice leaves a partial block in every
     configuration."""
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
-    ncfg = 11
-    ref = None
+    ncfg = 12
+    half = U.copy()
+    O.half_sweep(half, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
+    kappa = O.site_conditioning(U, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
+    bound = fp32_half_sweep_bound(kappa, 0, 16.0)
     for k in range(ncfg):
         p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, **kw)
         ctx = lgt.lgt_create(p, U)
@@ -647,10 +651,8 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
             out = lgt.lgt_get_working_links(ctx, U.shape[:4])
         finally:
             lgt.lgt_destroy(ctx)
-        if ref is None:
-            ref = out
-        err = np.abs(out - ref).max()
-        assert err < 2e-6, f"launch configuration {k}: {err} after a half-sweep"
+        ratio, n_above, n_links = check_fp32_bound(np.abs(out - half), bound)
+        assert ratio <= 1.0, f"launch configuration {k}: {ratio} of the allowed error after a half-sweep"
     ref = None
     for k in range(ncfg):
         p = lgt.lgt_params_default(dims=U.shape[:4], launch_config=k + 1, theta_tol=1e-12, max_sweeps=3000, **kw)
