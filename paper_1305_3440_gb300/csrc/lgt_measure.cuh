@@ -217,8 +217,26 @@ __device__ __forceinline__ void fused_finish_body(const FusedArgs &a, int t) {
     double v[2] = {0.0, 0.0};
     const double2 *p0 = a.warp_part + (size_t)t * a.wps;
     const double2 *p1 = a.warp_part + ((size_t)a.g.nt + t) * a.wps;
-    for (int w = threadIdx.x; w < a.nw; w += blockDim.x) {
-      const double2 x0 = p0[w], x1 = p1[w];
+    // Each thread adds the slots w, w + blockDim.x, ... in that order.  The slots
+    // sit in L2 (half of them on the other die), so the loads of eight
+    // consecutive terms are issued before any of them is added.
+    const int bd = (int)blockDim.x;
+    int w = threadIdx.x;
+    for (; w + 7 * bd < a.nw; w += 8 * bd) {
+      double2 x0[8], x1[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        x0[u] = __ldcg(p0 + w + u * bd);
+        x1[u] = __ldcg(p1 + w + u * bd);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        v[0] += x0[u].x;
+        v[1] += x0[u].y + x1[u].y;
+      }
+    }
+    for (; w < a.nw; w += bd) {
+      const double2 x0 = __ldcg(p0 + w), x1 = __ldcg(p1 + w);
       v[0] += x0.x;
       v[1] += x0.y + x1.y;
     }
@@ -235,23 +253,47 @@ __device__ __forceinline__ void fused_finish_body(const FusedArgs &a, int t) {
     am_last = atomicAdd(a.counter, 1u) == (unsigned)a.g.nt - 1;
   }
   __syncthreads();
-  if (!am_last || threadIdx.x != 0) return;
+  if (!am_last) return;
   __threadfence();
+  // The last block forms the totals in slice order.  Its threads first load
+  // the slices' sums and form each slice's F_t and theta_t side by side (one L2
+  // round trip and one FP64 division latency instead of one per slice), then
+  // thread 0 adds them in slice order: the same sums as a serial loop over the
+  // slices, bit for bit.
+  constexpr int CH = 256;
+  __shared__ double sl[4 * CH];
+  __shared__ uint8_t act[CH];
   const double vs = 2.0 * (double)a.g.vs_half, vol = 2.0 * (double)a.g.vh;
   const double nd = a.gauge == GAUGE_COULOMB ? 3.0 : 4.0;
   double fsum = 0.0, tsum = 0.0, tmax = 0.0, ftot = 0.0, ttot = 0.0;
   int nact = 0;
-  for (int tt = 0; tt < a.g.nt; tt++) {
-    const double rk = __ldcg(a.slice + 2 * tt), th2 = __ldcg(a.slice + 2 * tt + 1);
-    ftot += rk;
-    ttot += th2;
-    const double ft = rk / (3.0 * nd * vs), th = th2 / (3.0 * vs);
-    fsum += ft;
-    tsum += th;
-    tmax = th > tmax ? th : tmax;
-    if (a.coulomb_target >= 0.0) a.active[tt] = th >= a.coulomb_target ? 1 : 0;
-    nact += a.active[tt];
+  for (int t0 = 0; t0 < a.g.nt; t0 += CH) {
+    const int n = a.g.nt - t0 < CH ? a.g.nt - t0 : CH;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const double rk = __ldcg(a.slice + 2 * (t0 + k)), th2 = __ldcg(a.slice + 2 * (t0 + k) + 1);
+      const double th = th2 / (3.0 * vs);
+      sl[4 * k] = rk;
+      sl[4 * k + 1] = th2;
+      sl[4 * k + 2] = rk / (3.0 * nd * vs);
+      sl[4 * k + 3] = th;
+      if (a.coulomb_target >= 0.0) a.active[t0 + k] = th >= a.coulomb_target ? 1 : 0;
+      act[k] = a.active[t0 + k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < n; k++) {
+        ftot += sl[4 * k];
+        ttot += sl[4 * k + 1];
+        fsum += sl[4 * k + 2];
+        const double th = sl[4 * k + 3];
+        tsum += th;
+        tmax = th > tmax ? th : tmax;
+        nact += act[k];
+      }
+    }
+    __syncthreads();
   }
+  if (threadIdx.x != 0) return;
   a.totals[TOT_F_LANDAU] = ftot / (3.0 * nd * vol);
   a.totals[TOT_THETA_LANDAU] = ttot / (3.0 * vol);
   a.totals[TOT_PLAQ] = 0.0;
