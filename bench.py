@@ -579,7 +579,6 @@ def run_landau64(args):
     vol = int(np.prod(dims))
     U = synth.field(dims, 0.7, 5)
     dev = torch.from_numpy(U).cuda()
-    del U
     stream = torch.cuda.Stream()
     out = {}
     for name, kw in [("or_1.8", dict(algo=lgt.LGT_OR, omega=1.8)), ("sr_0.9", dict(algo=lgt.LGT_SR, p=0.9, seed=5))]:
@@ -603,9 +602,22 @@ def run_landau64(args):
     for name in ("or_1.8", "sr_0.9"):
         n = out[name]["sweeps_bulk"] + out[name]["sweeps_polish"]
         out[name]["fp64_estimate_s"] = n * 2 * avg
+    # the FP64 oracle on the host cores: one untimed sweep, then 5 timed OR sweeps
+    # of the same field (ω 1.8)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        O.sweeps(U, 1, omega=1.8, sweep0=0)
+        t0 = time.perf_counter()
+        O.sweeps(U, 5, omega=1.8, sweep0=1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 5 * vol / dt, "unit": "site updates/s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": f"5 FP64 OR sweeps of the 64^4 field ({dt:.1f} s)"}
+    del U
     peaks, src = measured_peaks()
     print(json.dumps({"workload": "landau64", "config": {"workload": "SU(3) Landau 64^4, eps=0.7, seed 5"},
-                      "runs": out, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}), flush=True)
+                      "runs": out, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src,
+                      "cpu_baseline": cpu}), flush=True)
 
 
 def run_mag(args):
