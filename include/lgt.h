@@ -135,7 +135,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..12: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..15: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
   int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
@@ -192,9 +192,21 @@ typedef struct {
  *                            in order from a counter and start an item once
  *                            the previous half-sweep has finished its slice
  *                            and both neighbours (bounded waits: a wait over
- *                            2 s fails the call with LGT_ETIMEOUT).
- * A configuration that a phase's kernel lacks (4-11 after promotion; 7 and 10
- * on FP32-18 links) falls back to configuration 0 for that phase.  Every
+ *                            2 s fails the call with LGT_ETIMEOUT);
+ *                        12: as 10, items of 2 tiles taken in a rolling band:
+ *                            half-sweep h starts D = ceil(N_t / 4) slices of
+ *                            work after h - 1, at a slice D - 2 further on,
+ *                            so about four half-sweeps sweep the lattice
+ *                            together two slices apart and a slice's links
+ *                            return to the next half-sweep while L2 still
+ *                            holds them (same bounded waits);
+ *   one thread per site, staged (FP32-12 bulk sweeps only): one batch of
+ *   cp.async copies brings the site's links and G into shared memory, then
+ *   the lean configurations' update runs from there:
+ *                        13: 128 threads, <= 128 registers (4 blocks per SM);
+ *                        14: 64 threads, <= 128 registers (8 blocks per SM).
+ * A configuration that a phase's kernel lacks (4-14 after promotion; 7, 10 and
+ * 12-14 on FP32-18 links) falls back to configuration 0 for that phase.  Every
  * configuration groups the fused estimate by the same 8 sites; results differ
  * only in FP32 rounding (the lean configurations sum K(x) link by link, the
  * others pairwise; and where the compiler fuses multiply-adds), converged F

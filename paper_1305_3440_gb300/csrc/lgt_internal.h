@@ -43,6 +43,7 @@ struct Workspace {
   uint8_t *active;          // [nt]
   int *err;                 // [1] bit 0: ingest check failed, bit 1: a streaming sweep's wait timed out
   unsigned *stream_ctr;     // [2 + nt] streaming sweeps: ticket, abort flag, tiles done per slice
+  unsigned *stream_order;   // [LGT_STREAM_MAX_HALF * nt] rolling-band order of configuration 12 (h << 16 | k)
 };
 
 size_t workspace_bytes(const Geom &g, int min_block);
@@ -120,6 +121,11 @@ struct SweepArgs {
   // bounded waits expire: fault injection for tests)
   unsigned long long stream_wait_ns;
   unsigned stream_skip;
+  // streaming launches: the (half-sweep h, position k) pair of each scheduled
+  // slice in ticket order (h << 16 | k; nullptr: half-sweep after half-sweep),
+  // and the start slice of half-sweep h, h * stream_shift mod nt
+  const unsigned *stream_order;
+  int stream_shift;
   // global timeslice of local slice 0 (a temporal slab's offset): the random
   // streams of stochastic relaxation and annealing are counted by the global site
   int t_offset;
@@ -215,30 +221,41 @@ struct SweepCfg {
 //    10: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
 //   one thread per site, lean as 8 and 9, more warps per SM:
 //    11: 128 threads, <= 80 registers (6 blocks, 24 warps per SM)
+//   one thread per site, streaming in a rolling band (FP32-12 only): as 10, but
+//   the launch's half-sweeps overlap in time -- half-sweep h starts D waves
+//   after h - 1, S slices further on -- so a few of them sweep the lattice
+//   together a few slices apart and each link comes back to L2-resident lines:
+//    12: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
+//   one thread per site, staged (FP32-12 only): the site's links and G copied
+//   into shared memory by one batch of cp.async, then the lean body from there:
+//    13: 128 threads, <= 128 registers, 4 blocks per SM (54 KB shared each)
+//    14:  64 threads, <= 128 registers, 8 blocks per SM (27 KB shared each)
 // The one-thread and four-thread layouts form K(x) in the same order, the lean
 // ones link by link; every configuration groups the fused estimate by the same
 // 8 sites; results differ only in FP32 rounding (the order of K's sums and
 // where the compiler fuses multiply-adds).  The maximally Abelian gauge has
 // kernels in configurations 0-3 only.
-constexpr int LGT_NCFG = 12;
-__host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : (c == 3 ? 64 : 128); }
+constexpr int LGT_NCFG = 15;
+__host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : ((c == 3 || c == 14) ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
   return c == 1 ? 3
                 : (c == 3 ? 8
                           : (c == 4 ? 4
                                     : (c == 5 ? 2
-                                              : (c == 6 ? 6 : (c == 7 || c == 10 ? 2 : (c == 8 ? 4 : (c == 9 ? 5 : (c == 11 ? 6 : 1))))))));
+                                              : (c == 6 ? 6 : (c == 7 || c == 10 || c == 12 ? 2 : (c == 8 || c == 13 ? 4 : (c == 9 ? 5 : (c == 11 ? 6 : (c == 14 ? 8 : 1)))))))));
 }
 __host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4 && c <= 6; }
 __host__ __device__ constexpr bool lgt_cfg_pipe(int c) { return c == 7; }
 __host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9 || c == 11; }
-__host__ __device__ constexpr bool lgt_cfg_stream(int c) { return c == 10; }
+__host__ __device__ constexpr bool lgt_cfg_stream(int c) { return c == 10 || c == 12; }
+__host__ __device__ constexpr bool lgt_cfg_band(int c) { return c == 12; }
+__host__ __device__ constexpr bool lgt_cfg_staged(int c) { return c == 13 || c == 14; }
 // sites covered by one block (per tile for the pipelined configuration)
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
 // whether a storage format has kernels for a configuration
 __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
   return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
-         (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c)) || fmt == FMT_F32_12);
+         (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c) || lgt_cfg_staged(c)) || fmt == FMT_F32_12);
 }
 // the maximally Abelian gauge has kernels in the one-thread-per-site configurations 0-3
 __host__ __device__ constexpr bool lgt_cfg_mag(int c) { return c >= 0 && c <= 3; }
@@ -255,6 +272,31 @@ constexpr int LGT_PIPE_SMEM_PER_THREAD = 2 * 27 * 16;
 constexpr int LGT_STREAM_MAX_HALF = 64;
 constexpr int LGT_STREAM_TILES = 8;  // tiles (of 128 sites) per scheduled item (LGT_STREAM_TILES in the environment)
 constexpr unsigned long long LGT_STREAM_WAIT_NS = 2000000000ull;
+// rolling band (configuration 12): half-sweeps active at once, the gap in
+// slices between consecutive ones, and tiles per item (LGT_STREAM_BAND="B,G"
+// and LGT_STREAM_BAND_TILES in the environment)
+constexpr int LGT_BAND_ACTIVE = 4;
+constexpr int LGT_BAND_GAP = 2;
+constexpr int LGT_BAND_TILES = 2;
+
+// Rolling-band order.  Half-sweep h of a launch of n_half visits position k
+// (slice h * S + k mod nt) at wave D h + k; tickets go wave by wave and, within
+// a wave, by increasing h.  Item (h + 1, k) needs half-sweep h at positions
+// S + k - 1 .. S + k + 1 (mod nt), whose waves are at most D h + S + k + 1 <=
+// D (h + 1) + k when 1 <= S <= D - 1 (equal only with S = D - 1, and then h + 1
+// comes later in the wave): every item's dependencies hold smaller tickets.
+// Returns the ticket slot of (h, k): the pairs of earlier waves, then those of
+// the same wave with smaller h.
+__host__ __device__ inline unsigned stream_band_rank(int h, int k, int nt, int n_half, int D) {
+  const long long w = (long long)D * h + k;
+  unsigned r = 0;
+  for (int j = 0; j < n_half; j++) {
+    const long long c = w - (long long)D * j;  // positions of half-sweep j before wave w
+    r += (unsigned)(c < 0 ? 0 : (c > nt ? nt : c));
+    if (j < h && c < nt) r++;  // half-sweep j < h is in wave w too (c > 0 here)
+  }
+  return r;
+}
 constexpr int LGT_ERR_STREAM_WAIT = 2;
 // configuration for a requested block size (lgt_params.block_size)
 inline int lgt_cfg_of_block(int block) { return block == 256 ? 2 : (block == 64 ? 3 : 0); }

@@ -5,6 +5,7 @@
 // variants, compiled in parallel), their bodies in lgt_sweep.cuh.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include "lgt_device.cuh"
@@ -34,7 +35,8 @@ size_t workspace_bytes(const Geom &g, int min_block) {
   b += sizeof(unsigned) * ((size_t)g.nt + 1);              // counters
   b += (size_t)g.nt + sizeof(int);                         // active, err
   b += sizeof(unsigned) * ((size_t)g.nt + 2);              // stream_ctr
-  return b + 16 * 20;                                      // alignment slack
+  b += sizeof(unsigned) * LGT_STREAM_MAX_HALF * (size_t)g.nt;  // stream_order
+  return b + 16 * 21;                                      // alignment slack
 }
 
 static char *align16(char *p) { return (char *)(((uintptr_t)p + 15) & ~(uintptr_t)15); }
@@ -69,6 +71,8 @@ void workspace_carve(void *base, const Geom &g, int min_block, Workspace *w) {
   p = align16(p + sizeof(int));
   w->stream_ctr = (unsigned *)p;
   p = align16(p + sizeof(unsigned) * ((size_t)g.nt + 2));
+  w->stream_order = (unsigned *)p;
+  p = align16(p + sizeof(unsigned) * LGT_STREAM_MAX_HALF * (size_t)g.nt);
   w->active = (uint8_t *)p;
 }
 
@@ -108,6 +112,8 @@ void fill_sweep_args(SweepArgs *a, const Geom &g, void *links, void *G, const Wo
   a->snake = snake;
   a->stream_wait_ns = c.stream_wait_ns ? c.stream_wait_ns : LGT_STREAM_WAIT_NS;
   a->stream_skip = c.stream_skip;
+  a->stream_order = nullptr;  // half-sweep after half-sweep
+  a->stream_shift = 1;
   a->t_offset = c.t_offset;
   a->t_first = c.t_first;
   a->t_count = c.t_count > 0 ? c.t_count : g.nt;
@@ -179,7 +185,16 @@ static cudaError_t launch_sweep_kernel(sweep_fn fn, int cfg, const Geom &g, Swee
     // could only be placed as they exit: measured a little slower, left plain)
     return launch_fn(fn, dim3(blocks), block, smem, st, a, parity & 1, false);
   }
-  return launch_fn(fn, dim3(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), a.t_count), block, 0, st, a, parity & 1, pdl);
+  int smem = 0;
+  if (lgt_cfg_staged(cfg)) {  // one tile per block, its sites' operands staged in shared memory
+    smem = LGT_PIPE_SMEM_PER_THREAD / 2 * block;
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_fn(fn, dim3(ceil_div(g.vs_half, lgt_cfg_sites(cfg)), a.t_count), block, smem, st, a, parity & 1, pdl);
 }
 
 static sweep_fn pick_sweep(int fmt, const SweepCfg &c, int cfg) {
@@ -207,6 +222,34 @@ cudaError_t launch_half_sweep(int fmt, const Geom &g, void *links, void *G, cons
   return half_sweep(fmt, g, links, G, w, c, parity, sweep, reunit, use_mask, cfg, st, aux, loop, reunit_every, false);
 }
 
+// The rolling band's table: slot stream_band_rank(h, k) holds (h, k).
+__global__ void k_stream_order(unsigned *order, int nt, int n_half, int D) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nt * n_half) return;
+  const int h = idx / nt, k = idx - h * nt;
+  order[stream_band_rank(h, k, nt, n_half, D)] = ((unsigned)h << 16) | (unsigned)k;
+}
+
+// Shape of the rolling band on nt slices: about B half-sweeps at once (D =
+// ceil(nt / B) waves apart), G slices apart (S = D - G); B and G from
+// LGT_STREAM_BAND="B,G" when set, read at each launch.
+static void band_shape(int nt, int *D, int *S) {
+  int B = LGT_BAND_ACTIVE, G = LGT_BAND_GAP;
+  if (const char *v = getenv("LGT_STREAM_BAND")) {
+    int b = 0, gap = 0;
+    if (sscanf(v, "%d,%d", &b, &gap) == 2 && b >= 1 && b <= 64 && gap >= 1 && gap <= 64) B = b, G = gap;
+  }
+  int d = ceil_div(nt, B);
+  if (d < G + 1) d = G + 1;  // 1 <= S <= D - 1
+  *D = d;
+  *S = d - G;
+}
+static int band_tiles() {
+  const char *v = getenv("LGT_STREAM_BAND_TILES");
+  const int n = v ? atoi(v) : 0;
+  return n >= 1 && n <= 64 ? n : LGT_BAND_TILES;
+}
+
 cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, const Workspace &w, const SweepCfg &c,
                                int p0, int n_half, unsigned long long sweep0, long long count_base, int reunit_every,
                                int use_mask, int cfg, cudaStream_t st, const void *aux, const LoopState *loop,
@@ -231,6 +274,9 @@ cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, con
   }
   sweep_fn fn = pick_sweep(fmt, c, cfg);
   if (!fn || !lgt_cfg_supported_gauge(fmt, c.gauge, cfg)) return cudaErrorInvalidValue;
+  int band_d = 0, band_s = 1, band_n = 0;  // rolling band: wave stagger, slice shift, table built for band_n
+  const bool band = lgt_cfg_band(cfg) && g.nt <= 0xffff;  // the table packs k in 16 bits (else configuration 10's order)
+  if (band) band_shape(g.nt, &band_d, &band_s);
   // launches of at most LGT_STREAM_MAX_HALF half-sweeps (and 2^30 tiles: the
   // ticket and slice counters are 32-bit)
   const long long tiles_half = (long long)ceil_div(g.vs_half, lgt_cfg_threads(cfg)) * g.nt;
@@ -248,6 +294,18 @@ cudaError_t launch_half_sweeps(int fmt, const Geom &g, void *links, void *G, con
     a.reunit_every = reunit_every;
     a.count_base = loop ? 0 : count_base + s0;
     a.n_half = n;
+    if (band) {
+      a.stream_tiles = band_tiles();
+      a.stream_shift = band_s;
+      a.stream_order = w.stream_order;
+      if (n != band_n) {  // the table of this launch's n half-sweeps (stream-ordered after the last reader)
+        const int pairs = n * g.nt;
+        k_stream_order<<<ceil_div(pairs, 256), 256, 0, st>>>(w.stream_order, g.nt, n, band_d);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        band_n = n;
+      }
+    }
     cudaError_t e = launch_sweep_kernel(fn, cfg, g, a, p, st);
     if (e != cudaSuccess) return e;
     if (launches) ++*launches;

@@ -392,17 +392,116 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
 }
 
 
+// FP32-12, staged: one batch of cp.async copies brings the site's links (the 8
+// of K(x), plus the temporal pair of a Coulomb update that transforms U_0) and
+// G(x) into the thread's own shared-memory slots, so the site waits for memory
+// once instead of once per direction and once more per reload; the update then
+// runs as the lean body's (K summed link by link, same arithmetic), reading its
+// operands from shared memory.  Slots [chunk][thread] as in the pipelined
+// layout: a thread reads back only what it staged, so no block barrier is
+// needed; 432 B per thread bound the blocks per SM (4 of 128 threads).
+template <int GAUGE, int ALGO>
+__device__ __forceinline__ void sweep_body_f32_staged(const SweepArgs &a, int p, int t, int bx) {
+  extern __shared__ float4 lgt_stage[];  // [LGT_PIPE_CHUNKS][blockDim.x]
+  typedef LinkIO<FMT_F32_12> IO;
+  if (a.active && !a.active[t]) return;  // whole block belongs to one slice
+  const int T = (int)blockDim.x, tid = (int)threadIdx.x;
+  const int j = bx * T + tid;
+  float acc[2] = {0.0f, 0.0f};
+  if (j < a.g.vs_half) {
+    constexpr int MU0 = GAUGE == GAUGE_COULOMB ? 1 : 0;
+    const int mu_lo = (GAUGE == GAUGE_COULOMB && a.transform_temporal) ? 0 : MU0;
+    const Coords c = coords_in_slice(a.g, p, t, j);
+    const int i = t * a.g.vs_half + j;
+    const int q = p ^ 1;
+    const float4 *L = reinterpret_cast<const float4 *>(a.links);
+    const float4 *Gs = reinterpret_cast<const float4 *>(a.G);
+    float4 *slot = lgt_stage + tid;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+      if (mu < mu_lo) continue;
+      const int nb = cb_shift(a.g, c, mu, -1);
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        cp_async16(slot + (mu * 6 + k) * T, L + (size_t)((p * 4 + mu) * 3 + k) * a.g.vh + i);
+        cp_async16(slot + (mu * 6 + 3 + k) * T, L + (size_t)((q * 4 + mu) * 3 + k) * a.g.vh + nb);
+      }
+    }
+    if (Gs) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) cp_async16(slot + (24 + k) * T, Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();  // this thread's copies have landed
+    // rows 0, 1 of the staged matrix at chunk c0 (row 2 zero)
+    auto staged = [&](int c0, float m[18]) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const float4 v = slot[(c0 + k) * T];
+        m[4 * k] = v.x, m[4 * k + 1] = v.y, m[4 * k + 2] = v.z, m[4 * k + 3] = v.w;
+      }
+#pragma unroll
+      for (int e = 12; e < 18; e++) m[e] = 0.0f;
+    };
+    float W[18];
+    mat_zero(W);
+#pragma unroll 1
+    for (int mu = MU0; mu < 4; mu++) {
+      float u[18];
+      staged(mu * 6, u);
+      rebuild_row2(u);
+      acc_add(W, u);
+      staged(mu * 6 + 3, u);
+      rebuild_row2(u);
+      acc_add_dag(W, u);
+    }
+    violation_of_K(W, acc[0], acc[1]);
+    uint4 draws = make_uint4(0, 0, 0, 0);
+    if (ALGO == ALGO_SR) draws = sr_draws(a, c);
+    float gm[18];
+    local_update<float, ALGO>(W, gm, (float)a.omega, a.sr_thr, draws);
+#pragma unroll 1
+    for (int mu = mu_lo; mu < 4; mu++) {
+      const int nb = cb_shift(a.g, c, mu, -1);
+      float u[18], r[18];
+      staged(mu * 6, u);
+      rebuild_row2(u);
+      mat_mul(gm, u, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, p, mu, i, r);
+      staged(mu * 6 + 3, u);  // rows 0, 1 of U g^dagger need rows 0, 1 of U only
+      mat_mul_dag(u, gm, r);
+      if (a.reunit) reunitarise(r);
+      IO::store(a.links, a.g.vh, q, mu, nb, r);
+    }
+    if (Gs) {
+      float gx[18], r[18];
+      staged(24, gx);
+      rebuild_row2(gx);
+      mat_mul(gm, gx, r);
+      if (a.reunit) reunitarise(r);
+      GIO::store(a.G, a.g.vh, p, i, r);
+    }
+  }
+  fused_store<float, 1>(a, p, t, bx, acc);
+}
+
+
 // ---------------------------------------------------------------- streaming
 // Several half-sweeps in one persistent launch.  Item n of the launch is
-// (half-sweep h, position k, group bx of up to stream_tiles tiles) with
-// n = (h * nt + k) * items_x + bx;
-// half-sweep h visits slice t = (h + k) mod nt at position k.  A site of
-// slice t touches links stored in slices t and t - 1 only (the temporal
-// backward link), so half-sweep h may update slice t once half-sweep h - 1 has
-// finished slices t - 1, t and t + 1; with the slice order shifted by one per
-// half-sweep, those are the first three positions of half-sweep h - 1 after
-// k, long finished when item (h, k) comes up, and the pipeline streams across
-// half-sweep boundaries.  done[t] counts the finished items of slice t over the
+// (half-sweep h, position k, group bx of up to stream_tiles tiles); half-sweep
+// h visits slice t = (h S + k) mod nt at position k.  A site of slice t touches
+// links stored in slices t and t - 1 only (the temporal backward link), so
+// half-sweep h may update slice t once half-sweep h - 1 has finished slices
+// t - 1, t and t + 1.  Configuration 10 takes the half-sweeps one after the
+// other (n = (h nt + k) items_x + bx, S = 1): the slices item (h, k) needs are
+// the first positions of half-sweep h - 1 after k, long finished when it comes
+// up, and the pipeline streams across half-sweep boundaries.  Configuration 12
+// takes them in a rolling band (stream_band_rank: half-sweep h starts D waves
+// after h - 1 and S = D - G slices further on), so about nt / D half-sweeps
+// sweep the lattice together, G slices apart, and a slice's links come back to
+// the next half-sweep a few slices of work after the last one wrote them, from
+// L2; only the S slices each half-sweep skips at its start wait for its end.  done[t] counts the finished items of slice t over the
 // launch: it reaches h * items_x only when every item of slice t in half-sweeps
 // before h has finished, because each such item waited for the ones before it.
 // Blocks take items from a ticket counter, in order, and wait only for items
@@ -432,14 +531,23 @@ __device__ __forceinline__ void lgt_red_release_add(unsigned *p, unsigned v) {
 struct StreamItem {
   int h, t, bx;
 };
-__device__ __forceinline__ StreamItem stream_item(unsigned n, int items_x, int nt) {
+// item n: slot n / items_x of the launch's order -- (h, k) = (slot / nt, slot
+// mod nt) half-sweep after half-sweep, or the rolling band's table -- and group
+// n mod items_x of slice h * shift + k (mod nt)
+__device__ __forceinline__ StreamItem stream_item(unsigned n, int items_x, int nt, const unsigned *order, int shift) {
   StreamItem it;
-  const unsigned per_half = (unsigned)items_x * (unsigned)nt;
-  it.h = (int)(n / per_half);
-  const unsigned r = n - (unsigned)it.h * per_half;
-  const int k = (int)(r / (unsigned)items_x);
-  it.bx = (int)(r - (unsigned)k * (unsigned)items_x);
-  it.t = (it.h % nt + k) % nt;
+  const unsigned slot = n / (unsigned)items_x;
+  it.bx = (int)(n - slot * (unsigned)items_x);
+  int k;
+  if (order) {
+    const unsigned e = __ldg(order + slot);
+    it.h = (int)(e >> 16);
+    k = (int)(e & 0xffffu);
+  } else {
+    it.h = (int)(slot / (unsigned)nt);
+    k = (int)(slot - (unsigned)it.h * (unsigned)nt);
+  }
+  it.t = (int)(((long long)it.h * shift + k) % nt);
   return it;
 }
 // whether half-sweep it.h - 1 has finished slices t - 1, t, t + 1 (one look)
@@ -518,7 +626,7 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
     if (tid == 0) {
       int ready = 0;
       if (n < total && !lgt_ld_acquire(ctr + 1)) {
-        ready = stream_ready(ctr + 2, stream_item(n, items_x, nt), items_x, nt) ? 1 : 0;
+        ready = stream_ready(ctr + 2, stream_item(n, items_x, nt, in.stream_order, in.stream_shift), items_x, nt) ? 1 : 0;
       }
       s_next = n;
       s_ready = ready;
@@ -529,13 +637,13 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
   unsigned cur = s_next;
   int staged = s_ready, buf = 0;  // staged: the current tile's loads are issued
   if (cur < total && staged) {
-    const StreamItem it = stream_item(cur, items_x, nt);
+    const StreamItem it = stream_item(cur, items_x, nt, in.stream_order, in.stream_shift);
     issue(it, it.bx * per_item, 0);
   }
   cp_async_commit();
   bool abort = false;
   while (cur < total && !abort) {
-    const StreamItem it = stream_item(cur, items_x, nt);  // it.bx: the item's index in its slice
+    const StreamItem it = stream_item(cur, items_x, nt, in.stream_order, in.stream_shift);  // it.bx: the item's index in its slice
     const int first = it.bx * per_item;
     const int ntl = tiles_x - first < per_item ? tiles_x - first : per_item;
     const int p = (p0 + it.h) & 1;
@@ -571,7 +679,7 @@ __device__ __forceinline__ void sweep_body_f32_stream(const SweepArgs &in, int p
         nxt = s_next;
         nxt_ready = s_ready;
         if (nxt < total && nxt_ready) {
-          const StreamItem in2 = stream_item(nxt, items_x, nt);
+          const StreamItem in2 = stream_item(nxt, items_x, nt, in.stream_order, in.stream_shift);
           issue(in2, in2.bx * per_item, buf ^ 1);
         }
       }

@@ -1,7 +1,7 @@
 // lgt_sweep_f32.cu -- FP32 bulk half-sweep kernels (FP32-18 and FP32-12 link
 // storage), one instantiation per gauge, algorithm and launch configuration
-// (one or four threads per site; pipelined through shared memory; streaming
-// several half-sweeps per launch); the maximally Abelian gauge in the
+// (one or four threads per site; pipelined or staged through shared memory;
+// streaming several half-sweeps per launch); the maximally Abelian gauge in the
 // one-thread-per-site configurations 0-3.
 #include "lgt_sweep.cuh"
 
@@ -23,6 +23,10 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
   }
   int t, bx;
   sweep_block_tile(a, p, t, bx);
+  if constexpr (lgt_cfg_staged(CFG)) {
+    if constexpr (FMT == FMT_F32_12 && GAUGE != GAUGE_MAG) sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, bx);
+    return;
+  }
   if constexpr (GAUGE == GAUGE_MAG) {
     sweep_body_mag<FMT, float, ALGO>(a, p, t, bx);
   } else if constexpr (lgt_cfg_quad(CFG)) {
@@ -77,6 +81,9 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 9: return pick_cfg<9>(fmt, gauge, algo);
     case 10: return pick_cfg<10>(fmt, gauge, algo);
     case 11: return pick_cfg<11>(fmt, gauge, algo);
+    case 12: return pick_cfg<12>(fmt, gauge, algo);
+    case 13: return pick_cfg<13>(fmt, gauge, algo);
+    case 14: return pick_cfg<14>(fmt, gauge, algo);
   }
   return nullptr;
 }

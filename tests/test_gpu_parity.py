@@ -638,7 +638,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
-    ncfg = 12
+    ncfg = 15
     half = U.copy()
     O.half_sweep(half, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
     kappa = O.site_conditioning(U, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
@@ -662,7 +662,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
             cfgs = lgt.lgt_get_stats(ctx).launch_config
         finally:
             lgt.lgt_destroy(ctx)
-        supported = k not in (7, 10) or bulk == "fp32_12"  # the staged layouts hold 12-real links only
+        supported = k not in (7, 10, 12, 13, 14) or bulk == "fp32_12"  # the staged layouts hold 12-real links only
         assert st == lgt.LGT_OK and cfgs[0] == (k if supported else 0) and res.theta < 1e-12
         if ref is None:
             ref = res.F
@@ -686,7 +686,7 @@ def test_streaming_sweeps_match_the_pipelined_kernel(lgt, gauge, algo):
     kw = dict(dims=dims, bulk=lgt.LGT_FP32_12, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=9,
               reunit_every=3)
     out = {}
-    for k in (0, 7, 10):
+    for k in (0, 7, 10, 12):
         ctx = lgt.lgt_create(lgt.lgt_params_default(launch_config=k + 1, **kw), U)
         try:
             lgt.lgt_half_sweep(ctx, 1)
@@ -698,8 +698,38 @@ def test_streaming_sweeps_match_the_pipelined_kernel(lgt, gauge, algo):
             lgt.lgt_destroy(ctx)
         assert st.launch_config[0] == k and sb == 41 and st.sweep_launches[0] == 81
     assert np.array_equal(out[10], out[7])
+    assert np.array_equal(out[12], out[7])
     assert np.abs(out[10] - out[0]).max() < 1e-4
     assert max(unitarity_error(out[10])) < 1e-5
+
+
+@pytest.mark.parametrize("band,tiles", [("2,1", "1"), ("3,3", "3"), ("6,2", "2"), ("1,5", "4"), ("12,1", "1")])
+def test_rolling_band_shapes_match_the_pipelined_kernel(lgt, band, tiles, monkeypatch):
+    """Configuration 12 with other band shapes (LGT_STREAM_BAND="B,G": about B
+    half-sweeps at once, G slices apart; D = max(ceil(nt / B), G + 1) waves of
+    stagger, S = D - G) and item sizes: 30 sweeps (60 half-sweeps, one launch)
+    of stochastic relaxation from a rough field give the pipelined kernel's
+    links bit for bit, and so does a launch of 3 half-sweeps.  14 slices of a
+    ragged 6x10x14 volume."""
+    dims = (14, 6, 10, 14)
+    U = synth.field(dims, 0.5, 24)
+    kw = dict(dims=dims, bulk=lgt.LGT_FP32_12, algo=lgt.LGT_SR, p=0.8, seed=11, reunit_every=4)
+    monkeypatch.setenv("LGT_STREAM_BAND", band)
+    monkeypatch.setenv("LGT_STREAM_BAND_TILES", tiles)
+    out = {}
+    for k in (7, 12):
+        ctx = lgt.lgt_create(lgt.lgt_params_default(launch_config=k + 1, **kw), U)
+        try:
+            lgt.lgt_sweep(ctx, 30)
+            lgt.lgt_half_sweep(ctx, 0)
+            lgt.lgt_sweep(ctx, 1)
+            lgt.lgt_half_sweep(ctx, 1)
+            out[k] = lgt.lgt_get_working_links(ctx, dims)
+            st = lgt.lgt_get_stats(ctx)
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st.launch_config[0] == k and st.sweep_launches[0] == 64
+    assert np.array_equal(out[12], out[7])
 
 
 @pytest.mark.parametrize("bulk", ["fp64", "fp32_12"])

@@ -1,10 +1,13 @@
 """The streaming sweep kernel's schedule, checked on the host.
 
-The kernel (launch configuration 10) runs n_half half-sweeps in one launch.
-Item n is (half-sweep h, position k, group bx of a slice's tiles), with
-n = (h * nt + k) * items_x + bx (items_x is called tiles_x below: the model
-does not look inside an item), and half-sweep h visits slice t = (h + k) mod nt
-at position k.  A block takes tickets in order; it looks once, without
+The kernel (launch configurations 10 and 12) runs n_half half-sweeps in one
+launch.  Item n is (half-sweep h, position k, group bx of a slice's tiles),
+and half-sweep h visits slice t = (h S + k) mod nt at position k.
+Configuration 10 numbers the items half-sweep after half-sweep,
+n = (h * nt + k) * items_x + bx with S = 1 (items_x is called tiles_x below:
+the model does not look inside an item); configuration 12 numbers the (h, k)
+pairs in a rolling band, wave D h + k first and h second (the kernel's
+stream_band_rank, restated here), with 1 <= S <= D - 1.  A block takes tickets in order; it looks once, without
 waiting, whether its next item's slices are ready (the previous half-sweep has
 finished slices t - 1, t, t + 1: done[t'] >= h * items_x) and stages it if so;
 otherwise it waits for them only after finishing its current item.  This model replays that protocol with random
@@ -20,7 +23,46 @@ import random
 import pytest
 
 
+def band_rank(h, k, nt, n_half, D):
+    """Slot of (h, k) in the rolling band: pairs of earlier waves (wave D j + k'),
+    then those of the same wave with smaller h."""
+    w = D * h + k
+    r = 0
+    for j in range(n_half):
+        c = w - D * j
+        r += min(max(c, 0), nt)
+        if j < h and c < nt:
+            r += 1
+    return r
+
+
+class Order:
+    """Ticket <-> (h, slice, group) of one launch: half-sweep after half-sweep
+    (D None, S 1: configuration 10) or the rolling band (D, S: configuration 12)."""
+
+    def __init__(self, nt, tiles_x, n_half, D=None, S=1):
+        self.nt, self.tiles_x, self.n_half, self.S = nt, tiles_x, n_half, S
+        if D is None:
+            self.pairs = [(h, k) for h in range(n_half) for k in range(nt)]
+        else:
+            self.pairs = [None] * (nt * n_half)
+            for h in range(n_half):
+                for k in range(nt):
+                    self.pairs[band_rank(h, k, nt, n_half, D)] = (h, k)
+        self.slot = {}
+        for i, (h, k) in enumerate(self.pairs):
+            self.slot[(h, (h * S + k) % nt)] = i
+
+    def item(self, n):
+        h, k = self.pairs[n // self.tiles_x]
+        return h, (h * self.S + k) % self.nt, n % self.tiles_x
+
+    def ticket(self, h, t, bx):
+        return self.slot[(h, t)] * self.tiles_x + bx
+
+
 def item(n, tiles_x, nt):
+    """Configuration 10's numbering in closed form."""
     per_half = tiles_x * nt
     h = n // per_half
     r = n - h * per_half
@@ -35,9 +77,11 @@ def ready(done, h, t, tiles_x, nt):
     return all(done[(t + d) % nt] >= need for d in (-1, 0, 1))
 
 
-def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
+def run(nt, tiles_x, n_half, nblocks, seed, ready=ready, order=None):
     """Replays the blocks' protocol; returns the number of waits that found the
-    slices not ready.  `ready` is the dependency rule (the kernel's by default)."""
+    slices not ready.  `ready` is the dependency rule (the kernel's by default);
+    `order` the launch's numbering (configuration 10's by default)."""
+    order = order or Order(nt, tiles_x, n_half)
     rng = random.Random(seed)
     total = tiles_x * nt * n_half
     done = [0] * nt
@@ -49,7 +93,7 @@ def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
     def take():
         n = ticket[0]
         ticket[0] += 1
-        staged = n < total and ready(done, *item(n, tiles_x, nt)[:2], tiles_x, nt)
+        staged = n < total and ready(done, *order.item(n)[:2], tiles_x, nt)
         return n, staged
 
     # a block: [state, cur, cur_staged, nxt, nxt_staged]
@@ -65,7 +109,7 @@ def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
         movable = []
         for b in live:
             if b[0] == "start" and not b[2]:
-                h, t, _ = item(b[1], tiles_x, nt)
+                h, t, _ = order.item(b[1])
                 if not ready(done, h, t, tiles_x, nt):
                     continue  # waiting
             movable.append(b)
@@ -77,7 +121,7 @@ def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
             b[3], b[4] = take()
             b[0] = "start"
         elif b[0] == "start":
-            h, t, bx = item(b[1], tiles_x, nt)
+            h, t, bx = order.item(b[1])
             if not b[2]:
                 waits += 1
             # an item starts only after the previous half-sweep finished t - 1, t, t + 1
@@ -85,8 +129,8 @@ def run(nt, tiles_x, n_half, nblocks, seed, ready=ready):
                 for d in (-1, 0, 1):
                     tt = (t + d) % nt
                     for x in range(tiles_x):
-                        n_prev = ((h - 1) * nt + ((tt - (h - 1)) % nt)) * tiles_x + x
-                        assert n_prev in finished
+                        n_prev = order.ticket(h - 1, tt, x)
+                        assert n_prev < b[1] and n_prev in finished
             # no two items in flight touch the same links
             mine = {t, (t - 1) % nt}
             for (h2, t2) in in_flight.values():
@@ -227,3 +271,70 @@ def test_injected_stall_ends_the_launch_through_the_abort_flag(nt, tiles_x, n_ha
         assert aborted
         assert not (started & set(range(skip)))
         assert len(started) < tiles_x * nt * n_half - skip  # work was left undone
+
+
+def test_band_order_with_whole_lattice_stagger_is_configuration_10s():
+    """D = nt, S = 1 makes every wave hold one pair: the band's numbering is then
+    configuration 10's, half-sweep after half-sweep."""
+    nt, tiles_x, n_half = 6, 3, 5
+    band = Order(nt, tiles_x, n_half, D=nt, S=1)
+    assert [band.item(n) for n in range(nt * tiles_x * n_half)] == \
+           [item(n, tiles_x, nt) for n in range(nt * tiles_x * n_half)]
+
+
+@pytest.mark.parametrize("nt,n_half,D", [(2, 3, 2), (4, 7, 2), (6, 5, 3), (8, 9, 4), (32, 20, 8), (12, 4, 20)])
+def test_band_ranks_are_a_permutation_in_wave_order(nt, n_half, D):
+    """stream_band_rank numbers every (h, k) once, waves D h + k in increasing
+    order and, within a wave, half-sweeps in increasing order."""
+    ranks = {(h, k): band_rank(h, k, nt, n_half, D) for h in range(n_half) for k in range(nt)}
+    assert sorted(ranks.values()) == list(range(nt * n_half))
+    by_rank = sorted(ranks, key=ranks.get)
+    assert by_rank == sorted(ranks, key=lambda hk: (D * hk[0] + hk[1], hk[0]))
+
+
+def test_band_dependencies_hold_smaller_tickets():
+    """Every S in 1 .. D - 1, for small lattices and any stagger (also D > nt):
+    the three items of half-sweep h - 1 that item (h, slice t) waits for come
+    earlier in the launch's order -- the property the deadlock argument needs."""
+    for nt in (2, 4, 6, 10):
+        for n_half in (1, 2, 5, 9):
+            for D in range(2, 2 * nt + 2):
+                for S in range(1, D):
+                    o = Order(nt, 1, n_half, D=D, S=S)
+                    for n in range(nt * n_half):
+                        h, t, _ = o.item(n)
+                        if h:
+                            assert all(o.ticket(h - 1, (t + d) % nt, 0) < n for d in (-1, 0, 1)), (nt, n_half, D, S)
+
+
+@pytest.mark.parametrize("nt,tiles_x,n_half,D,S,nblocks", [
+    (4, 2, 6, 2, 1, 5), (6, 3, 7, 3, 1, 8), (6, 2, 9, 3, 2, 4), (8, 2, 10, 4, 2, 12), (10, 1, 12, 5, 3, 20),
+    (12, 4, 8, 4, 3, 30), (32, 2, 8, 8, 6, 64), (8, 3, 5, 11, 4, 9)])
+def test_band_schedule_is_race_free_and_terminates(nt, tiles_x, n_half, D, S, nblocks):
+    """The rolling band under the blocks' protocol: every item once, dependencies
+    finished first, no two in-flight items on the same links, no deadlock."""
+    for seed in range(4):
+        run(nt, tiles_x, n_half, nblocks, seed, order=Order(nt, tiles_x, n_half, D=D, S=S))
+
+
+def test_band_brings_slices_back_soon():
+    """What the band is for (32 slices, 20 half-sweeps, D 8, S 6: about four
+    half-sweeps at once, two slices apart): half-sweep h returns to a slice at
+    most (D - S) waves of at most ceil(nt / D) + 1 pairs after half-sweep h - 1
+    left it (10 slices of work),
+    except for the S slices h skips at its start; configuration 10's order
+    returns after nt - 1 slices of work or more."""
+    nt, n_half, D, S = 32, 20, 8, 6
+    band = Order(nt, 1, n_half, D=D, S=S)
+    near = far = 0
+    for h in range(1, n_half):
+        for t in range(nt):
+            gap = band.ticket(h, t, 0) - band.ticket(h - 1, t, 0)
+            assert gap > 0
+            if gap <= (D - S) * (-(-nt // D) + 1):
+                near += 1
+            else:
+                far += 1
+    assert far == (n_half - 1) * S and near == (n_half - 1) * (nt - S)
+    seq = Order(nt, 1, n_half)
+    assert all(seq.ticket(h, t, 0) - seq.ticket(h - 1, t, 0) >= nt - 1 for h in range(1, n_half) for t in range(nt))
