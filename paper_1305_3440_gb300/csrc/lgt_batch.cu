@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(256) k_measure_batch(const BatchMeas *jobs, in
   measure_body<FMT>(J.a, t, p, rem - p * J.nbx, J.nbx);
 }
 
-// FP32 bulk sweeps of the batch: the lean one-thread layout (K streamed, links
-// reloaded for the write-back; <= 128 registers, 4 blocks of 128 threads per
-// SM), as launch configuration 8 of the single-lattice kernels.
+// FP32-18 bulk sweeps of the batch: the lean one-thread layout (K streamed,
+// links reloaded for the write-back; <= 128 registers, 4 blocks of 128 threads
+// per SM), as launch configuration 8 of the single-lattice kernels.
 template <int FMT, int GAUGE, int ALGO>
 __global__ void __launch_bounds__(128, 4) k_sweep_batch_lean(const BatchSweep *jobs, int n, int p, int s) {
   const int b = batch_block(jobs, p);
@@ -73,7 +73,39 @@ __global__ void __launch_bounds__(128, 4) k_sweep_batch_lean(const BatchSweep *j
   sweep_body_f32_lean<FMT, GAUGE, ALGO>(a, p, t, local - t * J.nbx);
 }
 
+// FP32-12 bulk sweeps of the batch: the staged one-thread layout (each site's
+// links and G copied into shared memory by one batch of cp.async, then the
+// lean update from there; 4 blocks of 128 threads per SM), as launch
+// configuration 13 of the single-lattice kernels.
+template <int GAUGE, int ALGO>
+__global__ void __launch_bounds__(128, 4) k_sweep_batch_staged(const BatchSweep *jobs, int n, int p, int s) {
+  const int b = batch_block(jobs, p);
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, b);
+  const BatchSweep &J = jobs[k];
+  SweepArgs a = J.a;
+  a.sweep += (unsigned long long)s;
+  a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
+  const int local = b - J.block_begin;
+  const int t = local / J.nbx;
+  sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, local - t * J.nbx);
+}
+
 typedef void (*batch_fn)(const BatchSweep *, int, int, int);
+
+// the staged kernel's shared memory (27 chunks of 16 B per thread), opted in once per kernel
+static cudaError_t staged_smem(batch_fn fn, int block, int *smem) {
+  *smem = LGT_PIPE_SMEM_PER_THREAD / 2 * block;
+  cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+static batch_fn pick_batch_staged(int gauge, int algo) {
+  if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_batch_staged<GAUGE_LANDAU, ALGO_SR> : k_sweep_batch_staged<GAUGE_LANDAU, ALGO_OR>;
+  return algo == ALGO_SR ? k_sweep_batch_staged<GAUGE_COULOMB, ALGO_SR> : k_sweep_batch_staged<GAUGE_COULOMB, ALGO_OR>;
+}
 
 template <int FMT>
 static batch_fn pick_batch_lean(int gauge, int algo) {
@@ -91,13 +123,20 @@ cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSwe
                                     int parity, int s, int block, cudaStream_t st) {
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
   batch_fn fn = nullptr;
+  int smem = 0;
   if (fmt == FMT_F64) fn = pick_batch_fmt<FMT_F64>(gauge, algo);
   else if (fmt == FMT_F32_18) fn = block == 128 ? pick_batch_lean<FMT_F32_18>(gauge, algo) : pick_batch_fmt<FMT_F32_18>(gauge, algo);
+  else if (fmt == FMT_F32_12 && block == 128 && (gauge == GAUGE_LANDAU || gauge == GAUGE_COULOMB) &&
+           (algo == ALGO_OR || algo == ALGO_SR)) {
+    fn = pick_batch_staged(gauge, algo);
+    cudaError_t e = staged_smem(fn, block, &smem);
+    if (e != cudaSuccess) return e;
+  }
   else if (fmt == FMT_F32_12) fn = block == 128 ? pick_batch_lean<FMT_F32_12>(gauge, algo) : pick_batch_fmt<FMT_F32_12>(gauge, algo);
   else if (fmt == FMT_PAIR) fn = pick_batch_fmt<FMT_PAIR>(gauge, algo);
   else if (fmt == FMT_ANCHOR) fn = pick_batch_fmt<FMT_ANCHOR>(gauge, algo);
   if (!fn) return cudaErrorInvalidValue;
-  fn<<<total_blocks, block, 0, st>>>(jobs, n, parity & 1, s);
+  fn<<<total_blocks, block, smem, st>>>(jobs, n, parity & 1, s);
   return cudaGetLastError();
 }
 
