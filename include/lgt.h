@@ -83,7 +83,8 @@ typedef enum {
  * subgroup in closed form (of the circle of maximisers, the element nearest
  * the identity), then overrelaxation or stochastic relaxation as for Landau
  * gauge.  lgt_result.F / theta and lgt_measure report F_MAG / theta_MAG.
- * Launch configurations 0-3 only (others fall back to 0); after promotion it
+ * Launch configurations 0-3, and 13-14 on FP32-12 links (others fall back to
+ * 0); after promotion it
  * polishes in FP64 whatever `polish` says; no simulated annealing; not
  * served (lgt_submit: LGT_EINVAL). */
 typedef enum { LGT_LANDAU = 0, LGT_COULOMB = 1, LGT_MAG = 2 } lgt_gauge;

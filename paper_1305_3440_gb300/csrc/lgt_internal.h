@@ -234,7 +234,7 @@ struct SweepCfg {
 // ones link by link; every configuration groups the fused estimate by the same
 // 8 sites; results differ only in FP32 rounding (the order of K's sums and
 // where the compiler fuses multiply-adds).  The maximally Abelian gauge has
-// kernels in configurations 0-3 only.
+// kernels in configurations 0-3, 13 and 14.
 constexpr int LGT_NCFG = 15;
 __host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : ((c == 3 || c == 14) ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
@@ -257,8 +257,9 @@ __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
   return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
          (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c) || lgt_cfg_staged(c)) || fmt == FMT_F32_12);
 }
-// the maximally Abelian gauge has kernels in the one-thread-per-site configurations 0-3
-__host__ __device__ constexpr bool lgt_cfg_mag(int c) { return c >= 0 && c <= 3; }
+// the maximally Abelian gauge has kernels in the one-thread-per-site
+// configurations 0-3 and, on FP32-12 links, the staged ones
+__host__ __device__ constexpr bool lgt_cfg_mag(int c) { return (c >= 0 && c <= 3) || c == 13 || c == 14; }
 // whether a (format, gauge) pair has kernels for a configuration
 __host__ __device__ constexpr bool lgt_cfg_supported_gauge(int fmt, int gauge, int c) {
   return lgt_cfg_supported(fmt, c) &&

@@ -808,12 +808,17 @@ __device__ __forceinline__ void mag_element(const R v[3], R omega, uint64_t sr_t
 // running g = R_{s-1} ... R_0.  That g is sparse in a known way -- after step
 // (0,1) row 2 is e_2, after step (0,2) row 1 still has no third entry -- so
 // the blocks are formed from the links with 2- and 3-term products instead of
-// full ones (the links are loaded again for each step: L1/L2 hits).  The first
-// pass also forms X(x) and the estimate: sum_a |U_aa|^2 over the 8 links (the
-// parity-0 sums give F_MAG, every link counted once) and tr Delta_MAG^2.
-template <int FMT, typename R, int ALGO>
+// full ones (the links are loaded again for each step: L1/L2 hits, or, with
+// STAGED (FP32-12, launch configurations 13 and 14), from the thread's
+// shared-memory slots, filled by one batch of cp.async copies as in the staged
+// relaxation body).  The first pass also forms X(x) and the estimate:
+// sum_a |U_aa|^2 over the 8 links (the parity-0 sums give F_MAG, every link
+// counted once) and tr Delta_MAG^2.
+template <int FMT, typename R, int ALGO, bool STAGED = false>
 __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t, int bx) {
   typedef LinkIO<FMT> IO;
+  static_assert(!STAGED || FMT == FMT_F32_12, "the staged layout holds 12-real FP32 links");
+  extern __shared__ float4 lgt_stage[];  // STAGED: [LGT_PIPE_CHUNKS][blockDim.x]
   if (a.active && !a.active[t]) return;
   const int j = bx * blockDim.x + threadIdx.x;
   R acc[2] = {R(0), R(0)};
@@ -821,6 +826,47 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
     const Coords c = coords_in_slice(a.g, p, t, j);
     const int i = t * a.g.vs_half + j;
     const int q = p ^ 1;
+    const int T = (int)blockDim.x;
+    float4 *slot = lgt_stage + threadIdx.x;
+    if constexpr (STAGED) {  // the site's 8 links and G, one wait for memory
+      const float4 *L = reinterpret_cast<const float4 *>(a.links);
+      const float4 *Gs = reinterpret_cast<const float4 *>(a.G);
+#pragma unroll
+      for (int mu = 0; mu < 4; mu++) {
+        const int nb = cb_shift(a.g, c, mu, -1);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          cp_async16(slot + (mu * 6 + k) * T, L + (size_t)((p * 4 + mu) * 3 + k) * a.g.vh + i);
+          cp_async16(slot + (mu * 6 + 3 + k) * T, L + (size_t)((q * 4 + mu) * 3 + k) * a.g.vh + nb);
+        }
+      }
+      if (Gs) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) cp_async16(slot + (24 + k) * T, Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
+    // the matrix at staged chunk c0 (row 2 rebuilt)
+    auto staged = [&](int c0, R m[18]) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const float4 v4 = slot[(c0 + k) * T];
+        m[4 * k] = v4.x, m[4 * k + 1] = v4.y, m[4 * k + 2] = v4.z, m[4 * k + 3] = v4.w;
+      }
+#pragma unroll
+      for (int e = 12; e < 18; e++) m[e] = R(0);
+      rebuild_row2(m);
+    };
+    // U_mu(x) and U_mu(x - mu)
+    auto load_fwd = [&](int mu, R m[18]) {
+      if constexpr (STAGED) staged(mu * 6, m);
+      else IO::load(a.links, a.g.vh, p, mu, i, m);
+    };
+    auto load_bwd = [&](int mu, R m[18]) {
+      if constexpr (STAGED) staged(mu * 6 + 3, m);
+      else IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), m);
+    };
     uint4 draws = make_uint4(0, 0, 0, 0);
     if (ALGO == ALGO_SR) draws = sr_draws(a, c);
     const R omega = (R)a.omega;
@@ -830,7 +876,7 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
       R u[18];
-      IO::load(a.links, a.g.vh, p, mu, i, u);
+      load_fwd(mu, u);
       // X += U D^dagger: X_ab += U_ab conj(U_bb)
 #pragma unroll
       for (int x = 0; x < 3; x++)
@@ -842,7 +888,7 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
 #pragma unroll
       for (int x = 0; x < 3; x++) acc[0] += u[LGT_RE(x, x)] * u[LGT_RE(x, x)] + u[LGT_IM(x, x)] * u[LGT_IM(x, x)];
       R w[18];
-      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
+      load_bwd(mu, w);
       // X -= D^dagger U: X_ab -= conj(U_aa) U_ab
 #pragma unroll
       for (int x = 0; x < 3; x++)
@@ -865,8 +911,8 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
       R u[18], w[18];
-      IO::load(a.links, a.g.vh, p, mu, i, u);
-      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
+      load_fwd(mu, u);
+      load_bwd(mu, w);
       const Cx<R> f00 = cx_add(cx_mul(a0, cx_at(u, 0, 0)), cx_mul(b0, cx_at(u, 1, 0)));
       const Cx<R> f02 = cx_add(cx_mul(a0, cx_at(u, 0, 2)), cx_mul(b0, cx_at(u, 1, 2)));
       // (U g^dagger)_{x0} = U_x0 conj(a0) + U_x1 conj(b0), (U g^dagger)_{x2} = U_x2
@@ -884,8 +930,8 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
 #pragma unroll 1
     for (int mu = 0; mu < 4; mu++) {
       R u[18], w[18];
-      IO::load(a.links, a.g.vh, p, mu, i, u);
-      IO::load(a.links, a.g.vh, q, mu, cb_shift(a.g, c, mu, -1), w);
+      load_fwd(mu, u);
+      load_bwd(mu, w);
       Cx<R> f[2][2], b[2][2];
 #pragma unroll
       for (int y = 0; y < 2; y++) {
@@ -922,11 +968,11 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
     for (int mu = 0; mu < 4; mu++) {
       const int nb = cb_shift(a.g, c, mu, -1);
       R u[18], r[18];
-      IO::load(a.links, a.g.vh, p, mu, i, u);
+      load_fwd(mu, u);
       mat_mul(g, u, r);
       if (a.reunit) reunitarise(r);
       IO::store(a.links, a.g.vh, p, mu, i, r);
-      IO::load(a.links, a.g.vh, q, mu, nb, u);
+      load_bwd(mu, u);
       mat_mul_dag(u, g, r);
       if (a.reunit) reunitarise(r);
       IO::store(a.links, a.g.vh, q, mu, nb, r);
@@ -934,7 +980,8 @@ __device__ __forceinline__ void sweep_body_mag(const SweepArgs &a, int p, int t,
     if constexpr (sizeof(R) == sizeof(float)) {
       if (a.G) {
         float gx[18], r[18];
-        GIO::load(a.G, a.g.vh, p, i, gx);
+        if constexpr (STAGED) staged(24, gx);
+        else GIO::load(a.G, a.g.vh, p, i, gx);
         mat_mul(g, gx, r);
         if (a.reunit) reunitarise(r);
         GIO::store(a.G, a.g.vh, p, i, r);

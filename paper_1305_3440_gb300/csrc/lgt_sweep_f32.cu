@@ -2,7 +2,7 @@
 // storage), one instantiation per gauge, algorithm and launch configuration
 // (one or four threads per site; pipelined or staged through shared memory;
 // streaming several half-sweeps per launch); the maximally Abelian gauge in the
-// one-thread-per-site configurations 0-3.
+// one-thread-per-site configurations 0-3 and the staged ones (13, 14).
 #include "lgt_sweep.cuh"
 
 namespace lgt {
@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
   int t, bx;
   sweep_block_tile(a, p, t, bx);
   if constexpr (lgt_cfg_staged(CFG)) {
-    if constexpr (FMT == FMT_F32_12 && GAUGE != GAUGE_MAG) sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, bx);
+    if constexpr (FMT == FMT_F32_12 && GAUGE == GAUGE_MAG) sweep_body_mag<FMT, float, ALGO, true>(a, p, t, bx);
+    else if constexpr (FMT == FMT_F32_12) sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, bx);
     return;
   }
   if constexpr (GAUGE == GAUGE_MAG) {
