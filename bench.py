@@ -164,6 +164,12 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        watts = []
+        for r in rows:
+            try:
+                watts.append(float(r[3]))
+            except ValueError:
+                pass
         reasons = set()
         for r in rows:
             for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
@@ -171,7 +177,8 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "sm_mhz_min": min(sm) if sm else None,
+                "power_w_max": max(watts) if watts else None}
 
 
 def algorithmic_bytes_per_site(kind: str) -> int:
@@ -328,7 +335,10 @@ def run_ours(args):
         # profilers started with "collect from cudaProfilerStart" see the timed steps only
         torch.cuda.profiler.start()
         ev0.record(stream)
+        step_ev = []
         for _ in range(args.steps):
+            step_ev.append(torch.cuda.Event(enable_timing=True))
+            step_ev[-1].record(stream)
             res = step(dev_in, dev_out)
             st = lgt.lgt_get_stats(ctx)
             stats_kernel["bulk_ms"] += st.sweep_ms[0]
@@ -346,6 +356,8 @@ def run_ours(args):
         torch.cuda.profiler.stop()
     clocks = clk.summary()
     elapsed = ev0.elapsed_time(ev1) / 1e3
+    step_ev.append(ev1)
+    step_ms = [round(step_ev[k].elapsed_time(step_ev[k + 1]), 2) for k in range(args.steps)]
     barrier()
     t_max, upd = aggregate_over_ranks(elapsed, float(sweeps * vol), device=f"cuda:{local}")
     value = upd / t_max
@@ -357,15 +369,22 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e_sweeps = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        res = step(host_in.numpy(), host_out.numpy())
-        e_sweeps += res.sweeps_bulk + res.sweeps_fp64
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local) as e_clk:
+        e0.record(stream)
+        e_ev = []
+        for _ in range(args.steps):
+            e_ev.append(torch.cuda.Event(enable_timing=True))
+            e_ev[-1].record(stream)
+            res = step(host_in.numpy(), host_out.numpy())
+            e_sweeps += res.sweeps_bulk + res.sweeps_fp64
+        e1.record(stream)
+        torch.cuda.synchronize()
     e_elapsed = e0.elapsed_time(e1) / 1e3
+    e_ev.append(e1)
     e2e = {"value": e_sweeps * vol * world / e_elapsed, "unit": "site updates/s",
-           "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16)}
+           "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16),
+           "step_ms": [round(e_ev[k].elapsed_time(e_ev[k + 1]), 2) for k in range(args.steps)],
+           "clocks": e_clk.summary()}
     assert np.array_equal(host_out.numpy(), dev_out.cpu().numpy())
 
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
@@ -424,6 +443,9 @@ def run_ours(args):
         runs = [("device_loop", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_12, omega=OMEGA)),
                 ("fp32_18_bulk", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_18, omega=OMEGA)),
                 ("sr_p0.8", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_12, algo=lgt.LGT_SR, p=0.8, seed=SEED)),
+                # the same stochastic relaxation, polished by overrelaxation after promotion
+                ("sr_p0.8_or_polish", DIMS, dev_in, dict(bulk=lgt.LGT_FP32_12, algo=lgt.LGT_SR, p=0.8, seed=SEED,
+                                                         polish_algo=lgt.LGT_POLISH_OR)),
                 # an omega schedule, not the workload's fixed omega: 1.7 until the sweeps'
                 # estimate of theta drops below 1e-2, then 1.1
                 ("omega_schedule_1.7_to_1.1", DIMS, dev_in,
@@ -491,6 +513,7 @@ def run_ours(args):
                            "omega_polish": p.omega_polish,
                            "theta_tol": TOL, "l2": "inputs larger than L2 (604 MB FP64 + 201 MB FP32 links)",
                            "parallelism": f"replicas x{world}"},
+                "step_ms": step_ms,
                 "sweeps_per_step": {"bulk_fp32": last["sweeps_bulk"], "polish": last["sweeps_fp64"]},
                 "result": {"F": last["F"], "theta": last["theta"], "plaquette": last["plaquette"]},
                 "time_to_theta_1e-14": ttt, "other_runs": variants, "kernels": kernels, "roofline": roofline,
@@ -581,7 +604,8 @@ def run_landau64(args):
     dev = torch.from_numpy(U).cuda()
     stream = torch.cuda.Stream()
     out = {}
-    for name, kw in [("or_1.8", dict(algo=lgt.LGT_OR, omega=1.8)), ("sr_0.9", dict(algo=lgt.LGT_SR, p=0.9, seed=5))]:
+    for name, kw in [("or_1.8", dict(algo=lgt.LGT_OR, omega=1.8)), ("sr_0.9", dict(algo=lgt.LGT_SR, p=0.9, seed=5)),
+                     ("sr_0.9_or_polish", dict(algo=lgt.LGT_SR, p=0.9, seed=5, polish_algo=lgt.LGT_POLISH_OR))]:
         p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, max_sweeps=100000, **kw)
         ctx = lgt.lgt_create(p, dev, stream=stream)
         t, st, res, stats = _timed_fix(lgt, ctx, dev, stream)
@@ -599,7 +623,7 @@ def run_landau64(args):
     avg = (s1.sweep_ms[1] - s0.sweep_ms[1]) / 1e3 / (s1.sweep_launches[1] - s0.sweep_launches[1])
     out["fp64_rate"] = {"avg_launch_us": avg * 1e6, "site_updates_per_s": (vol // 2) / avg,
                         "achieved_gbs": 2304 * (vol // 2) / avg / 1e9}
-    for name in ("or_1.8", "sr_0.9"):
+    for name in ("or_1.8", "sr_0.9", "sr_0.9_or_polish"):
         n = out[name]["sweeps_bulk"] + out[name]["sweeps_polish"]
         out[name]["fp64_estimate_s"] = n * 2 * avg
     # the FP64 oracle on the host cores: one untimed sweep, then 5 timed OR sweeps

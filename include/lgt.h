@@ -89,6 +89,8 @@ typedef enum {
  * served (lgt_submit: LGT_EINVAL). */
 typedef enum { LGT_LANDAU = 0, LGT_COULOMB = 1, LGT_MAG = 2 } lgt_gauge;
 typedef enum { LGT_OR = 0, LGT_SR = 1 } lgt_algo; /* Sec. 3.1 / Sec. 3.2 */
+/* lgt_params.polish_algo: the relaxation of the sweeps after promotion */
+typedef enum { LGT_POLISH_SAME = 0, LGT_POLISH_OR = 1 } lgt_polish_algo;
 typedef enum {
   LGT_FP64 = 0,    /* all sweeps in FP64 */
   LGT_FP32_18 = 1, /* bulk sweeps on FP32 links (18 reals), then FP64 polish */
@@ -140,7 +142,11 @@ typedef struct {
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
   int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
-  int32_t reserved;           /* must be 0 */
+  int32_t polish_algo;        /* relaxation after promotion: LGT_POLISH_SAME (0, default) keeps
+                                 algo; LGT_POLISH_OR (1) switches a stochastic-relaxation job to
+                                 overrelaxation at omega_polish (0: omega) once its field is
+                                 promoted -- the ladder's last decade, where Sec. 3.2's squared
+                                 steps converge slowly */
   double sa_beta0, sa_beta1;  /* inverse temperature of the first and the last annealing sweep,
                                  0 < sa_beta0 <= sa_beta1 (geometric in between) */
   double omega_late;          /* omega schedule (OR): the relaxation sweeps before promotion (all

@@ -81,7 +81,7 @@ extern "C" lgt_status lgt_params_default(lgt_params *p) {
   p->polish = LGT_POLISH_ANCHOR;
   p->launch_config = 0;
   p->sa_sweeps = 0;
-  p->reserved = 0;
+  p->polish_algo = LGT_POLISH_SAME;
   p->sa_beta0 = 1.0;
   p->sa_beta1 = 100.0;
   p->omega_polish = 1.3;
@@ -125,7 +125,8 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("omega = %g outside [1, 2)", p->omega);
     return LGT_EINVAL;
   }
-  if (p->algo == LGT_OR && p->omega_polish != 0.0 && !(p->omega_polish >= 1.0 && p->omega_polish < 2.0)) {
+  if ((p->algo == LGT_OR || p->polish_algo == LGT_POLISH_OR) && p->omega_polish != 0.0 &&
+      !(p->omega_polish >= 1.0 && p->omega_polish < 2.0)) {
     lgt_set_error("omega_polish = %g outside [1, 2) (0: same as omega)", p->omega_polish);
     return LGT_EINVAL;
   }
@@ -162,8 +163,13 @@ lgt_status lgt_validate_params(const lgt_params *p) {
     lgt_set_error("sa_sweeps >= 0 and 0 < sa_beta0 <= sa_beta1 (finite) required");
     return LGT_EINVAL;
   }
-  if (p->reserved != 0) {
-    lgt_set_error("reserved must be 0");
+  if (p->polish_algo != LGT_POLISH_SAME && p->polish_algo != LGT_POLISH_OR) {
+    lgt_set_error("polish_algo %d unknown", p->polish_algo);
+    return LGT_EINVAL;
+  }
+  if (p->polish_algo == LGT_POLISH_OR && p->algo == LGT_SR && p->omega_polish == 0.0 &&
+      !(p->omega >= 1.0 && p->omega < 2.0)) {
+    lgt_set_error("polish_algo = LGT_POLISH_OR needs omega_polish or omega in [1, 2)");
     return LGT_EINVAL;
   }
   if (p->launch_config < 0 || p->launch_config > LGT_NCFG) {
@@ -381,6 +387,7 @@ static lgt_status load_field(lgt_ctx *c, const double *links, int links_on_devic
   c->sa_pending = c->prm.sa_sweeps > 0;
   c->active_slices = g.nt;
   c->cfg.omega = c->prm.omega;  // omega_late may take over (omega schedule), omega_polish at promotion
+  c->cfg.algo = c->prm.algo == LGT_SR ? ALGO_SR : ALGO_OR;  // polish_algo may switch it at promotion
   c->omega_switched = 0;
   c->sweeps_bulk = c->sweeps_fp64 = 0;
   c->sweep_index = c->prm.sweep_offset;
@@ -994,6 +1001,7 @@ static lgt_status promote(lgt_ctx *c) {
   LGT_CUDA(launch_apply_G(c->g, c->G, c->u64, c->u64, nullptr, skip_temporal(c), c->stream));
   c->stats.launches++;
   c->phase = 1;
+  if (c->prm.polish_algo == LGT_POLISH_OR) c->cfg.algo = ALGO_OR;  // the sweeps after promotion overrelax
   if (c->prm.omega_polish != 0.0) c->cfg.omega = c->prm.omega_polish;
   if (c->prm.polish == LGT_POLISH_PAIR) {
     LGT_CUDA(launch_convert_pair(c->g, c->u64, 1, c->stream));

@@ -520,6 +520,7 @@ cudaError_t collect(lgt_server *s, Job *j) {
 cudaError_t promote_job(lgt_server *s, Job *j) {
   cudaError_t e = launch_apply_G(j->g, j->G, j->u64, j->u64, nullptr, j->skip_temporal(), s->stream);
   j->phase = 1;
+  if (j->prm.polish_algo == LGT_POLISH_OR) j->cfg.algo = ALGO_OR;  // the sweeps after promotion overrelax
   if (j->prm.omega_polish != 0.0) j->cfg.omega = j->prm.omega_polish;
   if (e == cudaSuccess && j->prm.polish == LGT_POLISH_PAIR) {
     e = launch_convert_pair(j->g, j->u64, 1, s->stream);

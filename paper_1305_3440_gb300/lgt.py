@@ -26,6 +26,7 @@ LGT_LANDAU, LGT_COULOMB, LGT_MAG = 0, 1, 2
 LGT_OR, LGT_SR = 0, 1
 LGT_FP64, LGT_FP32_18, LGT_FP32_12 = 0, 1, 2
 LGT_POLISH_PAIR, LGT_POLISH_FP64, LGT_POLISH_ANCHOR = 0, 1, 2
+LGT_POLISH_SAME, LGT_POLISH_OR = 0, 1  # lgt_params.polish_algo
 
 STATUS_NAMES = {0: "LGT_OK", 1: "LGT_EINVAL", 2: "LGT_ENOMEM", 3: "LGT_ECUDA", 4: "LGT_ENOTCONV",
                 5: "LGT_EAGAIN", 6: "LGT_ETIMEOUT", 7: "LGT_EBUSY", 8: "LGT_ECANCELLED", 9: "LGT_ENOTFOUND"}
@@ -39,7 +40,7 @@ class lgt_params(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("reunit_every", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("polish", ctypes.c_int32), ("launch_config", ctypes.c_int32), ("omega_polish", ctypes.c_double),
-                ("sa_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sa_beta0", ctypes.c_double),
+                ("sa_sweeps", ctypes.c_int32), ("polish_algo", ctypes.c_int32), ("sa_beta0", ctypes.c_double),
                 ("sa_beta1", ctypes.c_double), ("omega_late", ctypes.c_double), ("theta_omega", ctypes.c_double)]
 
 

@@ -622,6 +622,77 @@ def test_omega_polish_drives_the_sweeps_after_promotion(lgt, near_fixed_8):
     assert np.abs(got - ref17).max() > 1e-11
 
 
+@pytest.mark.parametrize("polish", ["pair", "anchor"])
+def test_polish_algo_switches_stochastic_relaxation_to_overrelaxation(lgt, near_fixed_8, polish):
+    """polish_algo = LGT_POLISH_OR: a stochastic-relaxation job's sweeps after
+    promotion are the oracle's overrelaxation sweeps at omega_polish (Sec. 3.1);
+    with the default LGT_POLISH_SAME they stay the oracle's stochastic-relaxation
+    sweeps (Sec. 3.2, same random stream).  8^4 field near the maximum (theta ~
+    1e-12), two sweeps after promotion, to the polish tolerance."""
+    U = near_fixed_8[(O.LANDAU, 1e-12)]
+    kw = dict(algo=lgt.LGT_SR, p=0.8, seed=5)
+    out = {}
+    for pa in (lgt.LGT_POLISH_OR, lgt.LGT_POLISH_SAME):
+        ctx = promoted_ctx(lgt, U, polish=polish, omega_polish=1.3, polish_algo=pa, **kw)
+        try:
+            lgt.lgt_sweep(ctx, 2)
+            out[pa] = lgt.lgt_get_links(ctx, U.shape[:4])
+        finally:
+            lgt.lgt_destroy(ctx)
+    tol = 1e-12  # the polish kernels' FP32 rotation angles at theta ~ 1e-12 (test above)
+    ref_or = U.copy()
+    O.sweeps(ref_or, 2, omega=1.3)
+    assert np.abs(out[lgt.LGT_POLISH_OR] - ref_or).max() < tol
+    ref_sr = U.copy()
+    O.sweeps(ref_sr, 2, algo=O.SR, p=0.8, seed=5)
+    assert np.abs(out[lgt.LGT_POLISH_SAME] - ref_sr).max() < tol
+    assert np.abs(out[lgt.LGT_POLISH_OR] - ref_sr).max() > 10 * tol
+
+
+def test_polish_algo_fix_reaches_the_stochastic_relaxation_maximum(lgt):
+    """A stochastic-relaxation fix (FP32-12 bulk, p 0.8) polished by overrelaxation
+    ends at the oracle's stochastic-relaxation F to 1e-10 with theta certified,
+    in fewer polish sweeps than the same job polished by stochastic relaxation;
+    served, it converges the same way."""
+    dims = (8, 8, 8, 8)
+    U = synth.field(dims, 0.3, 9)
+    ref = U.copy()
+    r = O.fix(ref, algo=O.SR, p=0.8, seed=5, tol=1e-14, max_sweeps=6000)
+    assert r["converged"]
+    res = {}
+    links = {}
+    for pa in (lgt.LGT_POLISH_OR, lgt.LGT_POLISH_SAME):
+        p = lgt.lgt_params_default(dims=dims, algo=lgt.LGT_SR, p=0.8, seed=5, bulk=lgt.LGT_FP32_12,
+                                   max_sweeps=6000, polish_algo=pa)
+        ctx = lgt.lgt_create(p, U)
+        try:
+            st, res[pa] = lgt.lgt_fix(ctx)
+            links[pa] = lgt.lgt_get_links(ctx, dims)
+        finally:
+            lgt.lgt_destroy(ctx)
+        assert st == lgt.LGT_OK and res[pa].theta < 1e-14
+        assert abs(res[pa].F - r["F"]) < 1e-10, (pa, res[pa].F, r["F"])
+    m = O.measure(links[lgt.LGT_POLISH_OR])
+    assert m["theta"] < 1e-14
+    assert res[lgt.LGT_POLISH_OR].sweeps_fp64 < res[lgt.LGT_POLISH_SAME].sweeps_fp64
+    p = lgt.lgt_params_default(dims=dims, algo=lgt.LGT_SR, p=0.8, seed=5, bulk=lgt.LGT_FP32_12,
+                               max_sweeps=6000, polish_algo=lgt.LGT_POLISH_OR)
+    srv = lgt.lgt_server_create(1 << 30)
+    try:
+        jid = lgt.lgt_submit(srv, p, U)
+        out = np.empty_like(U)
+        while True:
+            st, sres = lgt.lgt_poll(srv, jid, out)
+            if st != lgt.LGT_EAGAIN:
+                break
+            time.sleep(0.01)
+    finally:
+        lgt.lgt_server_destroy(srv)
+    assert st == lgt.LGT_OK and sres.theta < 1e-14 and abs(sres.F - r["F"]) < 1e-10
+    assert sres.sweeps_fp64 < res[lgt.LGT_POLISH_SAME].sweeps_fp64
+    assert O.measure(out)["theta"] < 1e-14
+
+
 @pytest.mark.parametrize("bulk", ["fp32_18", "fp32_12"])
 @pytest.mark.parametrize("gauge", list(GAUGES))
 @pytest.mark.parametrize("algo", list(ALGOS))
