@@ -138,7 +138,7 @@ typedef struct {
                                  site (0: autotuned over block sizes, register budgets and site
                                  layouts) */
   int32_t polish;             /* lgt_polish (FP64 phase after an FP32 bulk phase) */
-  int32_t launch_config;      /* 0: as block_size says; k = 1..15: launch configuration k-1 of the
+  int32_t launch_config;      /* 0: as block_size says; k = 1..16: launch configuration k-1 of the
                                  sweep kernels (overrides block_size; see below) */
   double omega_polish;        /* OR parameter of the sweeps after promotion, [1, 2); 0: omega */
   int32_t sa_sweeps;          /* simulated-annealing sweeps lgt_fix runs first (0: none) */
@@ -211,9 +211,12 @@ typedef struct {
  *   cp.async copies brings the site's links and G into shared memory, then
  *   the lean configurations' update runs from there:
  *                        13: 128 threads, <= 128 registers (4 blocks per SM);
- *                        14: 64 threads, <= 128 registers (8 blocks per SM).
- * A configuration that a phase's kernel lacks (4-14 after promotion; 7, 10 and
- * 12-14 on FP32-18 links) falls back to configuration 0 for that phase.  Every
+ *                        14: 64 threads, <= 128 registers (8 blocks per SM);
+ *                        15: 64 threads, <= 112 registers (9 blocks per SM),
+ *                            the links staged and G loaded into registers.
+ * A configuration that a phase's kernel lacks (4-15 after promotion; 7, 10 and
+ * 12-15 on FP32-18 links; all but 0-3, 13 and 14 in the maximally Abelian
+ * gauge) falls back to configuration 0 for that phase.  Every
  * configuration groups the fused estimate by the same 8 sites; results differ
  * only in FP32 rounding (the lean configurations sum K(x) link by link, the
  * others pairwise; and where the compiler fuses multiply-adds), converged F

@@ -230,26 +230,30 @@ struct SweepCfg {
 //   into shared memory by one batch of cp.async, then the lean body from there:
 //    13: 128 threads, <= 128 registers, 4 blocks per SM (54 KB shared each)
 //    14:  64 threads, <= 128 registers, 8 blocks per SM (27 KB shared each)
+//    15:  64 threads, <= 112 registers, 9 blocks per SM: the links only in
+//         shared memory (24 KB), G loaded into registers beside the copies
 // The one-thread and four-thread layouts form K(x) in the same order, the lean
 // ones link by link; every configuration groups the fused estimate by the same
 // 8 sites; results differ only in FP32 rounding (the order of K's sums and
 // where the compiler fuses multiply-adds).  The maximally Abelian gauge has
 // kernels in configurations 0-3, 13 and 14.
-constexpr int LGT_NCFG = 15;
-__host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : ((c == 3 || c == 14) ? 64 : 128); }
+constexpr int LGT_NCFG = 16;
+__host__ __device__ constexpr int lgt_cfg_threads(int c) { return (c == 2 || c == 5) ? 256 : ((c == 3 || c == 14 || c == 15) ? 64 : 128); }
 __host__ __device__ constexpr int lgt_cfg_minblocks(int c) {
   return c == 1 ? 3
                 : (c == 3 ? 8
                           : (c == 4 ? 4
                                     : (c == 5 ? 2
-                                              : (c == 6 ? 6 : (c == 7 || c == 10 || c == 12 ? 2 : (c == 8 || c == 13 ? 4 : (c == 9 ? 5 : (c == 11 ? 6 : (c == 14 ? 8 : 1)))))))));
+                                              : (c == 6 ? 6 : (c == 7 || c == 10 || c == 12 ? 2 : (c == 8 || c == 13 ? 4 : (c == 9 ? 5 : (c == 11 ? 6 : (c == 14 ? 8 : (c == 15 ? 9 : 1))))))))));
 }
 __host__ __device__ constexpr bool lgt_cfg_quad(int c) { return c >= 4 && c <= 6; }
 __host__ __device__ constexpr bool lgt_cfg_pipe(int c) { return c == 7; }
 __host__ __device__ constexpr bool lgt_cfg_lean(int c) { return c == 8 || c == 9 || c == 11; }
 __host__ __device__ constexpr bool lgt_cfg_stream(int c) { return c == 10 || c == 12; }
 __host__ __device__ constexpr bool lgt_cfg_band(int c) { return c == 12; }
-__host__ __device__ constexpr bool lgt_cfg_staged(int c) { return c == 13 || c == 14; }
+__host__ __device__ constexpr bool lgt_cfg_staged(int c) { return c == 13 || c == 14 || c == 15; }
+// 16-byte chunks a staged configuration keeps per thread: 8 links x 3, and G x 3 unless 15
+__host__ __device__ constexpr int lgt_cfg_stage_chunks(int c) { return c == 15 ? 24 : 27; }
 // sites covered by one block (per tile for the pipelined configuration)
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
 // whether a storage format has kernels for a configuration

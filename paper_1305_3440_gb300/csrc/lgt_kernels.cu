@@ -187,7 +187,7 @@ static cudaError_t launch_sweep_kernel(sweep_fn fn, int cfg, const Geom &g, Swee
   }
   int smem = 0;
   if (lgt_cfg_staged(cfg)) {  // one tile per block, its sites' operands staged in shared memory
-    smem = LGT_PIPE_SMEM_PER_THREAD / 2 * block;
+    smem = 16 * lgt_cfg_stage_chunks(cfg) * block;
     cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -399,8 +399,11 @@ __device__ __forceinline__ void sweep_body_f32_pipe(const SweepArgs &a, int p, i
 // runs as the lean body's (K summed link by link, same arithmetic), reading its
 // operands from shared memory.  Slots [chunk][thread] as in the pipelined
 // layout: a thread reads back only what it staged, so no block barrier is
-// needed; 432 B per thread bound the blocks per SM (4 of 128 threads).
-template <int GAUGE, int ALGO>
+// needed; 432 B per thread bound the blocks per SM (4 of 128 threads).  With
+// STAGE_G false only the links are staged (384 B per thread, 9 blocks of 64
+// threads per SM) and G(x) comes into registers by plain loads issued beside
+// the copies.
+template <int GAUGE, int ALGO, bool STAGE_G = true>
 __device__ __forceinline__ void sweep_body_f32_staged(const SweepArgs &a, int p, int t, int bx) {
   extern __shared__ float4 lgt_stage[];  // [LGT_PIPE_CHUNKS][blockDim.x]
   typedef LinkIO<FMT_F32_12> IO;
@@ -427,9 +430,13 @@ __device__ __forceinline__ void sweep_body_f32_staged(const SweepArgs &a, int p,
         cp_async16(slot + (mu * 6 + 3 + k) * T, L + (size_t)((q * 4 + mu) * 3 + k) * a.g.vh + nb);
       }
     }
+    float4 gq[3];  // !STAGE_G: rows 0, 1 of G(x), in flight beside the copies
     if (Gs) {
 #pragma unroll
-      for (int k = 0; k < 3; k++) cp_async16(slot + (24 + k) * T, Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+      for (int k = 0; k < 3; k++) {
+        if constexpr (STAGE_G) cp_async16(slot + (24 + k) * T, Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+        else gq[k] = __ldg(Gs + (size_t)(p * 3 + k) * a.g.vh + i);
+      }
     }
     cp_async_commit();
     cp_async_wait<0>();  // this thread's copies have landed
@@ -476,7 +483,16 @@ __device__ __forceinline__ void sweep_body_f32_staged(const SweepArgs &a, int p,
     }
     if (Gs) {
       float gx[18], r[18];
-      staged(24, gx);
+      if constexpr (STAGE_G) {
+        staged(24, gx);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          gx[4 * k] = gq[k].x, gx[4 * k + 1] = gq[k].y, gx[4 * k + 2] = gq[k].z, gx[4 * k + 3] = gq[k].w;
+        }
+#pragma unroll
+        for (int e = 12; e < 18; e++) gx[e] = 0.0f;
+      }
       rebuild_row2(gx);
       mat_mul(gm, gx, r);
       if (a.reunit) reunitarise(r);

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
   sweep_block_tile(a, p, t, bx);
   if constexpr (lgt_cfg_staged(CFG)) {
     if constexpr (FMT == FMT_F32_12 && GAUGE == GAUGE_MAG) sweep_body_mag<FMT, float, ALGO, true>(a, p, t, bx);
-    else if constexpr (FMT == FMT_F32_12) sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, bx);
+    else if constexpr (FMT == FMT_F32_12) sweep_body_f32_staged<GAUGE, ALGO, lgt_cfg_stage_chunks(CFG) == 27>(a, p, t, bx);
     return;
   }
   if constexpr (GAUGE == GAUGE_MAG) {
@@ -85,6 +85,7 @@ sweep_fn pick_sweep_f32(int fmt, int gauge, int algo, int cfg) {
     case 12: return pick_cfg<12>(fmt, gauge, algo);
     case 13: return pick_cfg<13>(fmt, gauge, algo);
     case 14: return pick_cfg<14>(fmt, gauge, algo);
+    case 15: return pick_cfg<15>(fmt, gauge, algo);
   }
   return nullptr;
 }

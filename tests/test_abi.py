@@ -67,7 +67,7 @@ def test_defaults(lgt):
 @pytest.mark.parametrize("field,value", [("dims", (8, 8, 8, 7)), ("dims", (0, 8, 8, 8)),
                                          ("omega", 2.0), ("omega", 0.9), ("check_every", 0),
                                          ("block_size", 96), ("theta_tol", 0.0), ("bulk", 7),
-                                         ("launch_config", 16), ("launch_config", -1), ("sa_sweeps", -1),
+                                         ("launch_config", 17), ("launch_config", -1), ("sa_sweeps", -1),
                                          ("polish_algo", 2), ("polish_algo", -1), ("omega_late", 2.0), ("omega_late", 0.5),
                                          ("theta_omega", -1.0)])
 def test_bad_params_rejected_before_any_device_work(lgt, field, value):

@@ -709,7 +709,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
     U = synth.field(DIMS_RAGGED, 0.5, 21)
     kw = dict(bulk=getattr(lgt, "LGT_" + bulk.upper()), gauge=GAUGES[gauge], algo=ALGOS[algo], p=0.8, seed=5,
               reunit_every=2)
-    ncfg = 15
+    ncfg = 16
     half = U.copy()
     O.half_sweep(half, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
     kappa = O.site_conditioning(U, 0, gauge=GAUGES[gauge], algo=ALGOS[algo], omega=1.7, p=0.8, seed=5)
@@ -733,7 +733,7 @@ def test_launch_configurations_agree(lgt, bulk, gauge, algo):
             cfgs = lgt.lgt_get_stats(ctx).launch_config
         finally:
             lgt.lgt_destroy(ctx)
-        supported = k not in (7, 10, 12, 13, 14) or bulk == "fp32_12"  # the staged layouts hold 12-real links only
+        supported = k not in (7, 10, 12, 13, 14, 15) or bulk == "fp32_12"  # the staged layouts hold 12-real links only
         assert st == lgt.LGT_OK and cfgs[0] == (k if supported else 0) and res.theta < 1e-12
         if ref is None:
             ref = res.F
