@@ -368,6 +368,19 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the host link on this machine: one timed copy each way of the step's buffers
+    # (outside the timed region; the same transfers lgt_load / lgt_get_links make)
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(stream)
+    with torch.cuda.stream(stream):
+        dev_out.copy_(host_in, non_blocking=True)
+        c1.record(stream)
+        host_out.copy_(dev_out, non_blocking=True)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    copy_gbs = {"h2d": round(host_in.numel() * 16 / c0.elapsed_time(c1) / 1e6, 1),
+                "d2h": round(host_out.numel() * 16 / c1.elapsed_time(c2) / 1e6, 1)}
+    lgt.lgt_get_links(ctx, out=dev_out)
     e_sweeps = 0
     with ClockSampler(local) as e_clk:
         e0.record(stream)
@@ -384,7 +397,7 @@ def run_ours(args):
     e2e = {"value": e_sweeps * vol * world / e_elapsed, "unit": "site updates/s",
            "h2d_bytes_per_step": int(host_in.numel() * 16), "d2h_bytes_per_step": int(host_out.numel() * 16),
            "step_ms": [round(e_ev[k].elapsed_time(e_ev[k + 1]), 2) for k in range(args.steps)],
-           "clocks": e_clk.summary()}
+           "clocks": e_clk.summary(), "pinned_copy_gbs": copy_gbs}
     assert np.array_equal(host_out.numpy(), dev_out.cpu().numpy())
 
     # ---- roofline of the dominant kernel (live CUDA events on the launching stream)
