@@ -43,7 +43,7 @@ def _slabs(lgt, p, U, n, stream, split=False):
 
 @pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("n", [1, 2, 4])
-@pytest.mark.parametrize("bulk,cfg", [("fp64", 1), ("fp32_12", 9), ("fp32_18", 8)])
+@pytest.mark.parametrize("bulk,cfg", [("fp64", 1), ("fp32_12", 9), ("fp32_12", 15), ("fp32_12", 16), ("fp32_18", 8)])
 @pytest.mark.parametrize("gauge,algo", [("landau", "or"), ("landau", "sr"), ("coulomb", "or")])
 def test_gpu_slabs_reproduce_the_whole_lattice(lgt, split, n, bulk, cfg, gauge, algo):
     import torch
