@@ -744,9 +744,30 @@ def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstan
         return lgt.lgt_params_default(dims=sp["dims"], gauge=sp["gauge"], theta_tol=sp["tol"],
                                       bulk=lgt.LGT_FP32_12, max_sweeps=100000, **SERVE_OMEGA)
 
+    # The clients' inputs.  Made before timing when they fit in a modest share of
+    # host memory; otherwise a producer thread makes them during the run on all but
+    # three cores, so that the server's worker thread (which issues the GPU's ticks)
+    # and the polling thread are never starved by the generator.
+    n_bytes = sum(int(np.prod(sp["dims"])) * 4 * 9 * 16 for sp in specs)
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        avail = 0
+    made = {}
+    gen_threads = max(1, (os.cpu_count() or 4) - 3)
+    if n_bytes <= min(48 << 30, avail // 3):
+        for j, sp in enumerate(specs):
+            made[j] = synth.field(sp["dims"], sp["eps"], sp["seed"])
+        inputs = f"made before timing ({n_bytes / 2**30:.1f} GB)"
+    else:
+        inputs = f"made during the run by a producer thread on {gen_threads} cores"
+
     def producer(qu, subset):
-        for sp in subset:
-            qu.put((sp, synth.field(sp["dims"], sp["eps"], sp["seed"])))
+        for j, sp in enumerate(subset):
+            U = made.get(j)
+            if U is None:
+                U = synth.field(sp["dims"], sp["eps"], sp["seed"], threads=gen_threads)
+            qu.put((sp, U))
         qu.put(None)
 
     def drain(srv, pending, done):
@@ -804,7 +825,8 @@ def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstan
             "offered_rate_jobs_per_s": rate, "jobs_per_s": len(specs) / wall,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
             "closed_loop_p50_s": float(np.percentile([d[1] for d in done_c], 50)),
-            "all_converged": all(d[2] == lgt.LGT_OK for d in done + done_c), "per_size": breakdown}
+            "all_converged": all(d[2] == lgt.LGT_OK for d in done + done_c), "inputs": inputs,
+            "per_size": breakdown}
 
 
 SERVE_WORKLOAD = ("dims in {16^4, 24^4, 32^4, 16^3x32, 32^3x64, 48^4}, Landau/Coulomb 50/50, tol 1e-12/1e-14, "

@@ -45,6 +45,9 @@ def _load():
             lib.lgtgen_field.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
                                          ctypes.c_uint64, ctypes.c_void_p]
             lib.lgtgen_field.restype = ctypes.c_int
+            lib.lgtgen_field_threads.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_double,
+                                                 ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
+            lib.lgtgen_field_threads.restype = ctypes.c_int
             lib.lgtgen_haar.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
             lib.lgtgen_haar.restype = ctypes.c_int
             lib.lgtgen_philox.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -53,15 +56,16 @@ def _load():
     return _lib
 
 
-def field(dims, eps: float, seed: int) -> np.ndarray:
+def field(dims, eps: float, seed: int, threads: int = 0) -> np.ndarray:
     """Synthetic links for ``dims = (N_t, N_3, N_2, N_1)`` as complex128 of shape
-    ``(N_t, N_3, N_2, N_1, 4, 3, 3)`` (C-contiguous)."""
+    ``(N_t, N_3, N_2, N_1, 4, 3, 3)`` (C-contiguous), generated on ``threads``
+    OpenMP threads (0: the default team; the values do not depend on it)."""
     dims = tuple(int(d) for d in dims)
     if len(dims) != 4 or min(dims) < 1:
         raise ValueError(f"bad dims {dims}")
     out = np.empty(dims + (4, 3, 3), dtype=np.complex128)
     d = (ctypes.c_int32 * 4)(*dims)
-    rc = _load().lgtgen_field(d, float(eps), int(seed) & (2**64 - 1), out.ctypes.data)
+    rc = _load().lgtgen_field_threads(d, float(eps), int(seed) & (2**64 - 1), out.ctypes.data, int(threads))
     if rc != 0:
         raise RuntimeError(f"lgtgen_field failed ({rc})")
     return out

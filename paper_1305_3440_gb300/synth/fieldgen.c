@@ -245,17 +245,20 @@ static int64_t gen_shift(const int32_t dims[4], int64_t site, int mu) {
   return x1 + n1 * (x2 + n2 * (x3 + n3 * t));
 }
 
-/* Public entry: fill out[V*4*9*2] (AoS complex128) with the synthetic field.
+/* Public entry: fill out[V*4*9*2] (AoS complex128) with the synthetic field,
+ * on nthreads OpenMP threads (0: the default team).  Every element comes from
+ * its own counter, so the result does not depend on the thread count.
  * Returns 0 on success, -1 on bad dims, -2 if scratch could not be allocated. */
-int lgtgen_field(const int32_t dims[4], double eps, uint64_t seed, double *out) {
+int lgtgen_field_threads(const int32_t dims[4], double eps, uint64_t seed, double *out, int nthreads) {
   for (int d = 0; d < 4; d++)
     if (dims[d] < 1) return -1;
   const int64_t vol = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
   mat3 *h = (mat3 *)malloc(sizeof(mat3) * (size_t)vol);
   if (!h) return -2;
-#pragma omp parallel for schedule(static)
+  const int team = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(team)
   for (int64_t s = 0; s < vol; s++) h[s] = gen_haar(seed, (uint64_t)s);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) num_threads(team)
   for (int64_t s = 0; s < vol; s++) {
     for (int mu = 0; mu < 4; mu++) {
       mat3 u = gen_link(seed, (uint64_t)s, mu, eps);
@@ -272,6 +275,10 @@ int lgtgen_field(const int32_t dims[4], double eps, uint64_t seed, double *out) 
   }
   free(h);
   return 0;
+}
+
+int lgtgen_field(const int32_t dims[4], double eps, uint64_t seed, double *out) {
+  return lgtgen_field_threads(dims, eps, seed, out, 0);
 }
 
 /* Haar samples alone (for the generator's own distribution tests). */
