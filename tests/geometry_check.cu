@@ -2,11 +2,16 @@
 // run by test_geometry_host.py; no GPU needed): for every site of every parity
 // and slice, coords_in_slice / cb_index agree, the parity is right, and every
 // neighbour index cb_shift(+-mu) is in range and lands on the coordinates
-// x +- mu-hat (periodic), and back.
+// x +- mu-hat (periodic), and back.  Also the rolling-band order of the
+// streaming configuration 12 (stream_band_rank): a permutation of the
+// (half-sweep, position) pairs in which every item's three dependencies come
+// earlier.
 #include <cstdio>
 #include <cstdlib>
+#include <vector>
 
 #include "lgt_device.cuh"
+#include "lgt_internal.h"
 
 using namespace lgt;
 
@@ -42,7 +47,40 @@ static int check(int nt, int n3, int n2, int n1) {
   return 0;
 }
 
+// every (h, k) ranked once; item (h, slice t) after half-sweep h - 1's items on
+// slices t - 1, t, t + 1 (half-sweep h visits slice (h S + k) mod nt at position k)
+static int check_band(int nt, int n_half, int D, int S) {
+  std::vector<int> seen(nt * n_half, 0);
+  std::vector<unsigned> rank_of(nt * n_half);
+  for (int h = 0; h < n_half; h++)
+    for (int k = 0; k < nt; k++) {
+      const unsigned r = stream_band_rank(h, k, nt, n_half, D);
+      if (r >= (unsigned)(nt * n_half) || seen[r]++) return 7;
+      rank_of[h * nt + k] = r;
+    }
+  for (int h = 1; h < n_half; h++)
+    for (int k = 0; k < nt; k++) {
+      const int t = (int)(((long long)h * S + k) % nt);
+      for (int d = -1; d <= 1; d++) {
+        const int tt = ((t + d) % nt + nt) % nt;
+        const int kp = (int)((((long long)tt - (long long)(h - 1) * S) % nt + nt) % nt);  // position of h - 1 on tt
+        if (rank_of[(h - 1) * nt + kp] >= rank_of[h * nt + k]) return 8;
+      }
+    }
+  return 0;
+}
+
 int main() {
+  for (int nt : {2, 4, 6, 12, 32, 96})
+    for (int n_half : {1, 2, 5, 20, 64})
+      for (int D = 2; D <= nt + 3; D++)
+        for (int S = 1; S < D; S++) {
+          const int r = check_band(nt, n_half, D, S);
+          if (r) {
+            printf("FAIL band nt %d n_half %d D %d S %d: check %d\n", nt, n_half, D, S, r);
+            return 1;
+          }
+        }
   const int dims[][4] = {{2, 2, 2, 2}, {4, 6, 10, 14}, {6, 2, 4, 2}, {8, 8, 8, 8}, {2, 4, 2, 6}, {16, 4, 6, 8}, {4, 2, 2, 32}};
   for (const auto &d : dims) {
     const int r = check(d[0], d[1], d[2], d[3]);
