@@ -368,7 +368,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # the host link on this machine: one timed copy each way of the step's buffers
+    # the host link of this machine: one timed copy each way of the step's buffers
     # (outside the timed region; the same transfers lgt_load / lgt_get_links make)
     c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     c0.record(stream)

@@ -1,7 +1,7 @@
 """The kernels' index arithmetic (parity-split site index, coordinates and the
 neighbour shifts) checked exhaustively on the host for ragged and degenerate
 extents: every neighbour index in range and pointing at x +- mu-hat.  This
-stands in for a device-side bounds checker (no sanitizer runs on this pool).
+stands in for a device-side bounds checker, which these tests do not run.
 The same program checks the C++ rolling-band order of the streaming launches
 (a permutation, dependencies first) for every valid stagger and shift."""
 import os
