@@ -914,3 +914,14 @@ def test_annealing_half_sweeps_and_decision_margins():
             assert np.all(np.minimum(m[jump], prev_m[jump]) <= 0.5 * step * 1.05)
         prev, prev_m = a, m
     assert jumps > 20
+
+
+def test_generator_values_do_not_depend_on_its_thread_count():
+    """The served-stream client makes inputs on fewer cores than the default team;
+    every element of a field comes from its own counter, so the field is the same
+    bit for bit on 1, 3 or all threads (ragged extents, Haar and link draws)."""
+    dims = (4, 6, 2, 8)
+    ref = synth.field(dims, 0.45, 77)
+    for n in (1, 3):
+        assert np.array_equal(synth.field(dims, 0.45, 77, threads=n), ref)
+    assert not np.array_equal(synth.field(dims, 0.45, 78), ref)
