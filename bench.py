@@ -774,7 +774,9 @@ def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstan
         for j in list(pending):
             st, res = lgt.lgt_poll(srv, j)
             if st != lgt.LGT_EAGAIN:
-                done.append((pending.pop(j), res.seconds, st))
+                sp = pending.pop(j)
+                upd = (res.sweeps_bulk + res.sweeps_fp64) * int(np.prod(sp["dims"]))
+                done.append((sp, res.seconds, st, upd))
 
     def run_stream(subset, rate, max_out):
         srv = lgt.lgt_server_create(150 << 30, 0)
@@ -816,7 +818,7 @@ def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstan
     wall, done = run_stream(specs, rate, 0)
     lat = np.array([d[1] for d in done])
     per_size = {}
-    for sp, sec, _ in done:
+    for sp, sec, _, _ in done:
         key = "x".join(str(v) for v in sp["dims"][::-1]) + (" coulomb" if sp["gauge"] else " landau")
         per_size.setdefault(key, []).append(sec)
     breakdown = {k: {"jobs": len(v), "p50_s": float(np.percentile(v, 50)), "p99_s": float(np.percentile(v, 99)),
@@ -826,6 +828,9 @@ def serve_stream(lgt, specs, gaps, cap_jobs: int, load: float = 0.8, max_outstan
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
             "closed_loop_p50_s": float(np.percentile([d[1] for d in done_c], 50)),
             "all_converged": all(d[2] == lgt.LGT_OK for d in done + done_c), "inputs": inputs,
+            # site updates the closed loop delivered per second of wall time (sweeps x volume
+            # of every job), to set beside a single context's rate
+            "closed_loop_site_updates_per_s": sum(d[3] for d in done_c) / wall_c,
             "per_size": breakdown}
 
 
