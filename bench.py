@@ -870,7 +870,7 @@ def run_slab(args):
     n_sweeps = 100
     L = 32
     dims = (L * world, 32, 32, 32)
-    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, omega=1.7, launch_config=9)
+    p = lgt.lgt_params_default(dims=dims, bulk=lgt.LGT_FP32_12, omega=1.7, launch_config=16)  # staged configuration 15
     out = {}
 
     def timed(fn):
