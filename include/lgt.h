@@ -214,7 +214,9 @@ typedef struct {
  *                        14: 64 threads, <= 128 registers (8 blocks per SM);
  *                        15: 64 threads, <= 112 registers (9 blocks per SM),
  *                            the links staged and G loaded into registers.
- * A configuration that a phase's kernel lacks (4-15 after promotion; 7, 10 and
+ * The anchored polish (the default after promotion) runs in 0-3 and in 11
+ * (<= 80 registers, 24 warps per SM).  A configuration that a phase's kernel
+ * lacks (4-15 after promotion, except 11 for the anchored polish; 7, 10 and
  * 12-15 on FP32-18 links; all but 0-3, 13 and 14 in the maximally Abelian
  * gauge) falls back to configuration 0 for that phase.  Every
  * configuration groups the fused estimate by the same 8 sites; results differ

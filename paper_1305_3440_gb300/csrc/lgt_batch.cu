@@ -90,7 +90,28 @@ __global__ void __launch_bounds__(128, 4) k_sweep_batch_staged(const BatchSweep 
   sweep_body_f32_staged<GAUGE, ALGO>(a, p, t, local - t * J.nbx);
 }
 
+// Anchored polish sweeps of the batch at <= 80 registers (6 blocks of 128
+// threads = 24 warps per SM, as launch configuration 11 of the single-lattice
+// polish kernels): the update is issue-bound, so the extra warps pay.
+template <int GAUGE, int ALGO>
+__global__ void __launch_bounds__(128, 6) k_sweep_batch_anchor(const BatchSweep *jobs, int n, int p, int s) {
+  const int b = batch_block(jobs, p);
+  const int k = batch_row(&jobs[0].block_begin, (int)sizeof(BatchSweep), n, b);
+  const BatchSweep &J = jobs[k];
+  SweepArgs a = J.a;
+  a.sweep += (unsigned long long)s;
+  a.reunit = a.reunit_every > 0 && ((a.count_base + s + 1) % a.reunit_every) == 0;
+  const int local = b - J.block_begin;
+  const int t = local / J.nbx;
+  sweep_body_anchor<GAUGE, ALGO>(a, p, t, local - t * J.nbx, J.nbx);
+}
+
 typedef void (*batch_fn)(const BatchSweep *, int, int, int);
+
+static batch_fn pick_batch_anchor(int gauge, int algo) {
+  if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_batch_anchor<GAUGE_LANDAU, ALGO_SR> : k_sweep_batch_anchor<GAUGE_LANDAU, ALGO_OR>;
+  return algo == ALGO_SR ? k_sweep_batch_anchor<GAUGE_COULOMB, ALGO_SR> : k_sweep_batch_anchor<GAUGE_COULOMB, ALGO_OR>;
+}
 
 // the staged kernel's shared memory (27 chunks of 16 B per thread), opted in once per kernel
 static cudaError_t staged_smem(batch_fn fn, int block, int *smem) {
@@ -134,6 +155,9 @@ cudaError_t launch_half_sweep_batch(int fmt, int gauge, int algo, const BatchSwe
   }
   else if (fmt == FMT_F32_12) fn = block == 128 ? pick_batch_lean<FMT_F32_12>(gauge, algo) : pick_batch_fmt<FMT_F32_12>(gauge, algo);
   else if (fmt == FMT_PAIR) fn = pick_batch_fmt<FMT_PAIR>(gauge, algo);
+  else if (fmt == FMT_ANCHOR && block == 128 && (gauge == GAUGE_LANDAU || gauge == GAUGE_COULOMB) &&
+           (algo == ALGO_OR || algo == ALGO_SR))
+    fn = pick_batch_anchor(gauge, algo);
   else if (fmt == FMT_ANCHOR) fn = pick_batch_fmt<FMT_ANCHOR>(gauge, algo);
   if (!fn) return cudaErrorInvalidValue;
   fn<<<total_blocks, block, smem, st>>>(jobs, n, parity & 1, s);

@@ -220,7 +220,8 @@ struct SweepCfg {
 //   pipeline does not drain between half-sweeps; staging as configuration 7:
 //    10: 128 threads, <= 255 registers, 2 blocks per SM (108 KB shared each)
 //   one thread per site, lean as 8 and 9, more warps per SM:
-//    11: 128 threads, <= 80 registers (6 blocks, 24 warps per SM)
+//    11: 128 threads, <= 80 registers (6 blocks, 24 warps per SM); also the
+//        anchored polish's update at that budget (no spills)
 //   one thread per site, streaming in a rolling band (FP32-12 only): as 10, but
 //   the launch's half-sweeps overlap in time -- half-sweep h starts D waves
 //   after h - 1, S slices further on -- so a few of them sweep the lattice
@@ -258,7 +259,8 @@ __host__ __device__ constexpr int lgt_cfg_stage_chunks(int c) { return c == 15 ?
 __host__ __device__ constexpr int lgt_cfg_sites(int c) { return lgt_cfg_quad(c) ? lgt_cfg_threads(c) / 4 : lgt_cfg_threads(c); }
 // whether a storage format has kernels for a configuration
 __host__ __device__ constexpr bool lgt_cfg_supported(int fmt, int c) {
-  return c >= 0 && c < LGT_NCFG && (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12) &&
+  return c >= 0 && c < LGT_NCFG &&
+         (!(lgt_cfg_quad(c) || lgt_cfg_lean(c)) || fmt == FMT_F32_18 || fmt == FMT_F32_12 || (fmt == FMT_ANCHOR && c == 11)) &&
          (!(lgt_cfg_pipe(c) || lgt_cfg_stream(c) || lgt_cfg_staged(c)) || fmt == FMT_F32_12);
 }
 // the maximally Abelian gauge has kernels in the one-thread-per-site

@@ -38,6 +38,11 @@ __global__ void __launch_bounds__(lgt_cfg_threads(CFG), lgt_cfg_minblocks(CFG)) 
 
 template <int CFG>
 static sweep_fn pick_cfg(int fmt, int gauge, int algo) {
+  if constexpr (CFG == 11) {  // 24 warps per SM at <= 80 registers: the anchored polish only
+    if (fmt != FMT_ANCHOR || algo == ALGO_SA || gauge == GAUGE_MAG) return nullptr;
+    if (gauge == GAUGE_LANDAU) return algo == ALGO_SR ? k_sweep_anchor<GAUGE_LANDAU, ALGO_SR, CFG> : k_sweep_anchor<GAUGE_LANDAU, ALGO_OR, CFG>;
+    return algo == ALGO_SR ? k_sweep_anchor<GAUGE_COULOMB, ALGO_SR, CFG> : k_sweep_anchor<GAUGE_COULOMB, ALGO_OR, CFG>;
+  }
   if (gauge == GAUGE_MAG) {  // maximally Abelian gauge: FP64 only here, configurations 0-3
     if constexpr (lgt_cfg_mag(CFG)) {
       if (fmt == FMT_F64 && algo == ALGO_OR) return k_sweep_f64<GAUGE_MAG, ALGO_OR, CFG>;
@@ -72,6 +77,7 @@ sweep_fn pick_sweep_hi(int fmt, int gauge, int algo, int cfg) {
     case 1: return pick_cfg<1>(fmt, gauge, algo);
     case 2: return pick_cfg<2>(fmt, gauge, algo);
     case 3: return pick_cfg<3>(fmt, gauge, algo);
+    case 11: return pick_cfg<11>(fmt, gauge, algo);
   }
   return nullptr;
 }
